@@ -1,0 +1,244 @@
+/*
+ * ifnso.h - C ABI of the GB300 (sm_103a) implementation of IFNSO,
+ * Iteration-Free Newton-Schulz Orthogonalization (arXiv 2602.02500), and of
+ * the Newton-Schulz iteration it is compared with.
+ *
+ * Conventions for every entry point
+ *  - Matrices are row-major.  "Device pointer" means memory of the current
+ *    CUDA device; "host pointer" means ordinary host memory.
+ *  - Calls that take a cudaStream_t only enqueue work on that stream and
+ *    return without synchronising, unless stated otherwise.  Host-detectable
+ *    errors return a status at once and enqueue nothing; the message is
+ *    available from ifnso_last_error() in the calling thread.
+ *  - No C++ exception crosses this interface.  The caller owns every buffer
+ *    it passes; a plan owns only its own metadata.
+ *  - Conditions detected on the device (zero input, non-finite values,
+ *    a pipeline wait that ran out of time) are recorded per matrix in the
+ *    workspace and read back with ifnso_device_status().
+ */
+#ifndef IFNSO_H
+#define IFNSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ifnso_stream_t; /* the same handle as cudaStream_t */
+
+typedef enum {
+  IFNSO_OK = 0,
+  IFNSO_ERR_INVALID_ARG = 1,    /* a size, pointer, alignment or option is not accepted */
+  IFNSO_ERR_UNSUPPORTED = 2,    /* a valid request this build does not implement */
+  IFNSO_ERR_OOM = 3,            /* a host allocation of plan metadata failed */
+  IFNSO_ERR_CUDA = 4,           /* a CUDA runtime/driver call failed (message has the CUDA error) */
+  IFNSO_ERR_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up (see ifnso_device_status) */
+  IFNSO_ERR_WORKSPACE = 6       /* workspace missing, misaligned or smaller than required */
+} ifnso_status;
+
+typedef enum {
+  IFNSO_F32 = 0,  /* FP32 storage and FP32 arithmetic (SIMT FP32 kernels) */
+  IFNSO_BF16 = 1  /* BF16 storage, tensor-core products with FP32 accumulation */
+} ifnso_dtype;
+
+/* Options set with ifnso_plan_set(). */
+typedef enum {
+  /* Operand precision of the squaring chain and of the final product (BF16 plans).
+   *   IFNSO_PREC_PLAIN: one FP16 operand per D_l, one BF16 operand for P.
+   *   IFNSO_PREC_SPLIT: D_l = hi + lo (two FP16 parts, three products per
+   *                     squaring), P = hi + lo (two BF16 parts, two products).
+   *   IFNSO_PREC_AUTO (default): SPLIT when L > 6, PLAIN otherwise. */
+  IFNSO_OPT_PRECISION = 1,
+  /* Input scaling.  IFNSO_SCALE_GRAM (default): X = A / ||A A^T||_F^(1/2)
+   * (Eq. new_scale_formula, Sec. 2; o = ||T_0||_F in Algorithm 1).
+   * IFNSO_SCALE_FROB: X = A / ||A||_F (Eq. constraint, Sec. 1). */
+  IFNSO_OPT_SCALE = 2,
+  /* Upper bound on the CTAs of each persistent launch (0 = one per SM). */
+  IFNSO_OPT_MAX_CTAS = 3,
+  /* Testing aid: stop after this stage (0 = Gram only, 1 = Gram and the
+   * D_1 / P initialisation, 2 + j = after squaring pass j+1).  -1 (default)
+   * runs everything.  Intermediate buffers are read with ifnso_workspace_view(). */
+  IFNSO_OPT_STOP_AFTER = 4
+} ifnso_option;
+
+enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2 };
+enum { IFNSO_SCALE_GRAM = 0, IFNSO_SCALE_FROB = 1 };
+
+/* Per-matrix device status bits (ifnso_device_status). */
+enum {
+  IFNSO_DEV_ZERO_INPUT = 1,   /* ||A A^T||_F = 0: the output is all zeros */
+  IFNSO_DEV_NONFINITE = 2,    /* the norm scalar is not finite: the output is not meaningful */
+  IFNSO_DEV_TIMEOUT = 4       /* a pipeline wait of a kernel ran out of time */
+};
+
+typedef struct ifnso_plan ifnso_plan;
+
+/* A batch of independent matrices (one Muon step's gradient list, say).
+ * Matrix i is rows[i] x cols[i], row-major with leading dimension ld[i]
+ * elements, at device pointer in[i] (256-byte alignment recommended, 16 bytes
+ * required; BF16: ld[i] a multiple of 8; F32: any ld >= cols).  The three
+ * shape arrays and the pointer array are host arrays of `count` entries.
+ * ld may be NULL (ld[i] = cols[i]).  A matrix with rows > cols is processed
+ * as its transpose (Eq. 1, Sec. 1) and its result is returned in its own
+ * shape. */
+typedef struct {
+  int32_t count;
+  const void* const* in;
+  const int64_t* rows;
+  const int64_t* cols;
+  const int64_t* ld;
+} ifnso_batch_desc;
+
+/* Coefficients of Y = sum_{l=0}^{L} w_l (I - X X^T)^{n_l} X over the plan's
+ * exponents n = (0, 1, 2, 4, ..., 2^(L-1)) (Eq. generalized_matrix_formula and
+ * the exponential selection of Sec. 2.2).  K = L + 1 slots; slot 0 is the
+ * identity weight and is forced to 1 (y -> 1 as x -> 1, Eq. our_scalar_formula).
+ * Exactly one of `host` (FP64, K values shared by every matrix) and `device`
+ * (FP32, count x K values, one row per matrix) is non-NULL.  The identity
+ * weight of the equivalent D-basis form, 1 + sum w_l, is formed in FP64 on the
+ * device. */
+typedef struct {
+  int32_t K;
+  const double* host;
+  const float* device;
+} ifnso_coeffs;
+
+/* ---------------------------------------------------------------------------
+ * Plans
+ * ------------------------------------------------------------------------- */
+
+/* Create a plan for matrices whose oriented shape (h <= w after Eq. 1) is at
+ * most h x w, stored as `dtype`.  `exponents` (host, K entries) must be
+ * 0, 1, 2, 4, ..., 2^(K-2): the exponential term selection of Sec. 2.2, the
+ * only exponents the repeated squaring of Sec. 2.4 produces; K >= 2, K <= 31.
+ * On success *plan owns host metadata only (no device memory). */
+ifnso_status ifnso_plan_create(ifnso_plan** plan, int64_t h, int64_t w, ifnso_dtype dtype,
+                               const int32_t* exponents, int32_t K);
+
+/* Set an ifnso_option; see the enum for values. */
+ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value);
+
+/* Read back an option (after AUTO resolution for IFNSO_OPT_PRECISION). */
+ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t* value);
+
+ifnso_status ifnso_plan_destroy(ifnso_plan* plan);
+
+/* Bytes of device workspace ifnso_orthogonalize needs for this batch
+ * (0 on error, with ifnso_last_error set).  Per matrix of oriented shape
+ * h x w, with hp = h rounded up to 256: about 12 hp^2 bytes (SPLIT) or
+ * 8 hp^2 (PLAIN) for BF16, 12 hp^2 for F32, plus metadata. */
+size_t ifnso_workspace_bytes(const ifnso_plan* plan, const ifnso_batch_desc* batch);
+
+/* ---------------------------------------------------------------------------
+ * The hot path: Algorithm 1 (Sec. 2.4) for a whole batch
+ * ------------------------------------------------------------------------- */
+
+/* For every matrix M_i of the batch: A = M_i or M_i^T (h <= w); T_0 = A A^T;
+ * o = ||T_0||_F; T_1 = I - T_0/o; T_l = T_{l-1}^2 (l = 2..L);
+ * Y' = I + sum_l w_l T_l; Y = Y' A / sqrt(o) (Algorithm 1), computed in the
+ * algebraically equal form D_1 = T_0/o, D_{l+1} = 2 D_l - D_l^2,
+ * Y' = (1 + sum w_l) I - sum w_l D_l.  out[i] (device, rows[i] x cols[i],
+ * row-major, leading dimension cols[i], 16-byte aligned, the input's dtype) receives Y in M_i's
+ * shape; it must not overlap in[i] or the workspace.  `workspace` (device,
+ * 1024-byte aligned, ifnso_workspace_bytes bytes) is scratch owned by the
+ * caller; it must not be used by another call that runs concurrently.  The
+ * call is asynchronous on `stream` and may be captured in a CUDA graph once
+ * it has run outside capture with the same batch, outputs and workspace (the
+ * first call uploads the launch metadata). */
+ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch,
+                                 const ifnso_coeffs* coeffs, void* const* out,
+                                 void* workspace, size_t workspace_bytes, ifnso_stream_t stream);
+
+/* The comparison baseline, Newton-Schulz: X_0 = A/||A||_F (Eq. constraint),
+ * then `steps` times X <- sum_n poly[n] (X X^T)^n X (Eq. general_eq_matrix):
+ * degree 3 takes poly = (a, b) (the classical iteration is (1.5, -0.5),
+ * Eq. one_iteration_matrix); degree 5 takes poly = (a, b, c) (Muon:
+ * (3.4445, -4.7750, 2.0315), Eq. iteration_jordan).  Every product runs on
+ * tensor cores for BF16 plans (BF16 storage of X, X X^T and the polynomial
+ * in X X^T, FP32 accumulation) and in FP32 for F32 plans.  The plan's
+ * exponents are ignored.  Same batch, output and stream rules as
+ * ifnso_orthogonalize; workspace size from ns_workspace_bytes. */
+ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const double* poly,
+                        int32_t degree, int32_t steps, void* const* out, void* workspace,
+                        size_t workspace_bytes, ifnso_stream_t stream);
+
+size_t ns_workspace_bytes(const ifnso_plan* plan, const ifnso_batch_desc* batch);
+
+/* Synchronise `stream`, then copy the per-matrix device status words of the
+ * last call that used `workspace` into per_matrix[0..count) (host), and the
+ * per-matrix FP64 scalars into o_out / trace_out (host, count entries each,
+ * either may be NULL): o = ||T_0||_F (or ||A||_F^2 under IFNSO_SCALE_FROB and
+ * for ns_iterate) and tr(T_0) = ||A||_F^2.  Returns IFNSO_ERR_DEVICE_TIMEOUT
+ * if any matrix has IFNSO_DEV_TIMEOUT set. */
+ifnso_status ifnso_device_status(const ifnso_plan* plan, const void* workspace, int32_t count,
+                                 int32_t* per_matrix, double* o_out, double* trace_out,
+                                 ifnso_stream_t stream);
+
+/* Testing aid: device pointer and leading dimension (elements) of an h_pad x
+ * h_pad intermediate of matrix `index` in a workspace used by
+ * ifnso_orthogonalize.  which: 0 = T_0 then P (FP32), 1/2 = D buffer 0 hi/lo
+ * (FP16, or FP32 for F32 plans), 3/4 = D buffer 1 hi/lo. */
+ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch,
+                                  void* workspace, int32_t index, int32_t which, void** ptr,
+                                  int64_t* ld);
+
+/* ---------------------------------------------------------------------------
+ * Split-K Frobenius norm
+ * ------------------------------------------------------------------------- */
+
+/* norm2_out[i] (device, FP64, count entries) = ||M_i||_F^2, reduced as FP32
+ * partial sums of squares per CTA and an FP64 final accumulation (the scaling
+ * of Eq. constraint, Sec. 1).  dtype is that of the matrices.  Asynchronous. */
+ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dtype,
+                                   double* norm2_out, ifnso_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Coefficient learning (Algorithm 1, "Coefficient learning"; Sec. 2.3, 3.1.1)
+ * ------------------------------------------------------------------------- */
+
+/* Learn w_1..w_{L-1} on the GPU in FP64 by minimising sum_j (f(x_j) - 1)^2
+ * with f of Eq. overall_polynomial (w_L from Eq. b_approximation), using Adam
+ * (moments from zero, bias corrections by running products of the betas 0.9
+ * and 0.999, eps 1e-8) with learning rate lr * gamma^floor(t / step_size) at
+ * iteration t, for `iters` iterations of `samples` points of (0, 1) each.
+ * Sample j of iteration t is the FP64 uniform built from Philox4x32-10 words
+ * 0 and 1 at counter (j, t, 0, 0), key (seed, 0x4C45524E):
+ * ((w0 >> 5) 2^26 + (w1 >> 6) + 0.5) 2^-53.  Writes w_1..w_L to w_out (host,
+ * L doubles).  Synchronous.  1 <= L <= 30, 1 <= samples <= 4096. */
+ifnso_status ifnso_learn_coefficients(int32_t L, int32_t iters, int32_t samples, double lr,
+                                      int32_t step_size, double gamma, uint32_t seed,
+                                      double* w_out);
+
+/* ---------------------------------------------------------------------------
+ * Synthetic inputs (benchmark and test data; not part of the method)
+ * ------------------------------------------------------------------------- */
+
+/* Fill out (device, BF16, rows x cols, leading dimension ld) with the
+ * rank-32 signal plus noise matrix of seed `seed`: element (i, j) is
+ * fl(fl(fl(alpha * S_ij) + N_ij) * beta) rounded to nearest even BF16, where
+ * S = L R^T with L_ir / R_jr the byte sums of Philox4x32-10 word 0 at counter
+ * (i, r, 0, 0) / (j, r, 0, 0), keys (seed, 0x4C524B31) / (seed, 0x4C524B32),
+ * minus 510, and N_ij = the four 16-bit halves of words 0 and 1 at counter
+ * (j, i, 0, 0), key (seed, 0x4E4F4953), summed, minus 131070.  Asynchronous. */
+ifnso_status ifnso_synth_lowrank_bf16(void* out, int64_t rows, int64_t cols, int64_t ld,
+                                      uint32_t seed, float alpha, float beta,
+                                      ifnso_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Errors and build information
+ * ------------------------------------------------------------------------- */
+
+/* Message of the last error in the calling thread ("" if none). */
+const char* ifnso_last_error(void);
+
+/* Number of kernel launches enqueued by this library since the process
+ * started (counting every launch of every entry point). */
+uint64_t ifnso_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFNSO_H */

@@ -1,0 +1,1142 @@
+// Host side of the IFNSO library: plans, workspace layout, TMA descriptors,
+// the launch metadata of a batch and the pass sequence of Algorithm 1
+// (Sec. 2.4) and of the Newton-Schulz baseline (Sec. 1).  Every step of the
+// computation runs in this library's kernels; the host only validates,
+// lays out and enqueues.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ifnso.h"
+
+using namespace ifnso;
+
+struct ifnso_plan {
+  int64_t h = 0, w = 0;
+  int dtype = IFNSO_BF16;
+  int L = 0;
+  int precision = IFNSO_PREC_AUTO;
+  int scale = IFNSO_SCALE_GRAM;
+  int max_ctas = 0;
+  int stop_after = -1;
+  int num_sms = 0;
+  // metadata of the last batch (pinned host copy, uploaded into the workspace)
+  uint64_t sig = 0;
+  bool sig_valid = false;
+  void* meta_host = nullptr;
+  size_t meta_cap = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
+
+ifnso_status fail(ifnso_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+ifnso_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(IFNSO_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define IFNSO_CUDA(call, what)                 \
+  do {                                         \
+    cudaError_t e__ = (call);                  \
+    if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+  } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// 2D tiled tensor map, 128-byte swizzle, zero fill outside the tensor.
+// inner/outer: extents in elements, ld: row pitch in elements.
+bool encode2d(CUtensorMap* map, CUtensorMapDataType dt, const void* ptr, uint64_t inner,
+              uint64_t outer, uint64_t ld, uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// K-major operand view: rows of `outer`, contiguous K of `inner` (box 64 x 128).
+bool map_k(CUtensorMap* m, CUtensorMapDataType dt, const void* p, int64_t inner, int64_t outer, int64_t ld) {
+  return encode2d(m, dt, p, inner, outer, ld, 64, 128);
+}
+// MN-major operand view: contiguous MN of `inner`, K rows of `outer` (box 64 x 64).
+bool map_mn(CUtensorMap* m, CUtensorMapDataType dt, const void* p, int64_t inner, int64_t outer, int64_t ld) {
+  return encode2d(m, dt, p, inner, outer, ld, 64, 64);
+}
+
+struct Shape {
+  int64_t rows, cols, ld;
+  int64_t h, w, hpad;
+  int trans;
+};
+
+// ------------------------------------------------------------------ layout
+// Workspace = [metadata | scalars | per-matrix buffers].  Offsets in bytes.
+struct Layout {
+  int count = 0;
+  int L = 0;
+  int split = 0;
+  int f32 = 0;
+  int ns = 0;        // Newton-Schulz layout
+  int steps = 0;
+  std::vector<Shape> shp;
+  // metadata
+  size_t off_mats = 0, off_probs = 0, off_items_sym = 0, off_items_app = 0, off_coef = 0;
+  size_t n_probs = 0, n_sym = 0, n_app = 0;
+  size_t prob_bytes = 0;
+  size_t meta_bytes = 0;
+  size_t off_scal = 0;
+  std::vector<size_t> off_buf;  // per matrix
+  size_t total = 0;
+  // problem slots
+  size_t pi_gram = 0, pi_sqr = 0, pi_apply = 0;  // IFNSO: gram[count], sqr[2][count], apply[count]
+  size_t pi_ns_gram = 0, pi_ns_sqr = 0, pi_ns_apply = 0;  // NS: gram[steps][count], sqr[count], apply[steps][count]
+};
+
+size_t a64(size_t v) { return (v + 127) & ~size_t(127); }  // 128: the alignment of CUtensorMap
+size_t a1k(size_t v) { return (v + 1023) & ~size_t(1023); }
+
+ifnso_status read_batch(const ifnso_plan* plan, const ifnso_batch_desc* b, std::vector<Shape>& shp) {
+  if (!b || b->count < 0 || (b->count > 0 && (!b->in || !b->rows || !b->cols)))
+    return fail(IFNSO_ERR_INVALID_ARG, "batch descriptor is NULL or incomplete");
+  if (b->count > 65535) return fail(IFNSO_ERR_INVALID_ARG, "batch count %d exceeds 65535", b->count);
+  const int esz = plan->dtype == IFNSO_BF16 ? 2 : 4;
+  shp.resize(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    Shape s;
+    s.rows = b->rows[i];
+    s.cols = b->cols[i];
+    s.ld = b->ld ? b->ld[i] : s.cols;
+    if (s.rows <= 0 || s.cols <= 0) return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: empty shape %lldx%lld", i, (long long)s.rows, (long long)s.cols);
+    if (s.ld < s.cols) return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: ld %lld < cols %lld", i, (long long)s.ld, (long long)s.cols);
+    if (!b->in[i]) return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: NULL input", i);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(b->in[i]);
+    if (a % 16 != 0) return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: input not 16-byte aligned", i);
+    if (plan->dtype == IFNSO_BF16 && (s.ld * esz) % 16 != 0)
+      return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: BF16 leading dimension %lld not a multiple of 8", i, (long long)s.ld);
+    s.trans = s.rows > s.cols ? 1 : 0;
+    s.h = s.trans ? s.cols : s.rows;
+    s.w = s.trans ? s.rows : s.cols;
+    if (s.h > plan->h || s.w > plan->w)
+      return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: oriented shape %lldx%lld exceeds the plan's %lldx%lld", i,
+                  (long long)s.h, (long long)s.w, (long long)plan->h, (long long)plan->w);
+    s.hpad = round_up(s.h, HPAD);
+    if (s.hpad / 128 > 65535 || (s.w + 255) / 256 > 65535)
+      return fail(IFNSO_ERR_INVALID_ARG, "matrix %d too large", i);
+    shp[i] = s;
+  }
+  return IFNSO_OK;
+}
+
+int resolved_split(const ifnso_plan* p) {
+  if (p->dtype != IFNSO_BF16) return 0;
+  if (p->precision == IFNSO_PREC_SPLIT) return 1;
+  if (p->precision == IFNSO_PREC_PLAIN) return 0;
+  return p->L > 6 ? 1 : 0;
+}
+
+void sym_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
+  // heavy matrices first (longer K first for the Gram; equal for squarings)
+  std::vector<int> order(shp.size());
+  for (size_t i = 0; i < shp.size(); ++i) order[i] = static_cast<int>(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return shp[a].hpad * shp[a].w > shp[b].hpad * shp[b].w;
+  });
+  for (int m : order) {
+    const int nb = static_cast<int>(shp[m].hpad / 256);
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J)
+        for (int half = 0; half < 2; ++half)
+          items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * I + half),
+                                   static_cast<uint16_t>(J), static_cast<uint16_t>(I == J ? 1 : 0)});
+  }
+}
+
+void app_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
+  std::vector<int> order(shp.size());
+  for (size_t i = 0; i < shp.size(); ++i) order[i] = static_cast<int>(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return shp[a].hpad * shp[a].w > shp[b].hpad * shp[b].w;
+  });
+  for (int m : order) {
+    const int tms = static_cast<int>((shp[m].h + BM - 1) / BM);
+    const int tns = static_cast<int>((shp[m].w + BN - 1) / BN);
+    for (int tn = 0; tn < tns; ++tn)
+      for (int tm = 0; tm < tms; ++tm)
+        items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(tm),
+                                 static_cast<uint16_t>(tn), 0});
+  }
+}
+
+Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns, int steps, int K) {
+  Layout ly;
+  ly.count = static_cast<int>(shp.size());
+  ly.L = plan->L;
+  ly.split = ns ? 0 : resolved_split(plan);
+  ly.f32 = plan->dtype == IFNSO_F32;
+  ly.ns = ns;
+  ly.steps = steps;
+  ly.shp = shp;
+  const size_t n = shp.size();
+  ly.prob_bytes = ly.f32 ? sizeof(SgProblem) : sizeof(TcProblem);
+  if (!ns) {
+    ly.pi_gram = 0;
+    ly.pi_sqr = n;
+    ly.pi_apply = 3 * n;
+    ly.n_probs = 4 * n;
+  } else {
+    ly.pi_ns_gram = 0;
+    ly.pi_ns_sqr = steps * n;
+    ly.pi_ns_apply = steps * n + n;
+    ly.n_probs = (2 * steps + 1) * n;
+  }
+  if (!ly.f32) {
+    std::vector<WorkItem> a, b;
+    sym_items(shp, a);
+    app_items(shp, b);
+    ly.n_sym = a.size();
+    ly.n_app = b.size();
+  }
+  size_t off = 0;
+  ly.off_mats = off;
+  off = a64(off + n * sizeof(MatInfo));
+  ly.off_probs = off;
+  off = a64(off + ly.n_probs * ly.prob_bytes);
+  ly.off_items_sym = off;
+  off = a64(off + ly.n_sym * sizeof(WorkItem));
+  ly.off_items_app = off;
+  off = a64(off + ly.n_app * sizeof(WorkItem));
+  ly.off_coef = off;
+  off = a64(off + sizeof(double) * (K > 0 ? K : 1));
+  ly.meta_bytes = off;
+  off = a1k(off);
+  ly.off_scal = off;
+  off = a1k(off + n * sizeof(MatScalars));
+  ly.off_buf.resize(n);
+  const size_t e = ly.f32 ? 4 : 2;
+  for (size_t i = 0; i < n; ++i) {
+    ly.off_buf[i] = off;
+    const size_t hp2 = static_cast<size_t>(shp[i].hpad) * shp[i].hpad;
+    if (!ns) {
+      off = a1k(off + hp2 * 4);  // T_0 / P (FP32)
+      if (ly.f32) {
+        off = a1k(off + hp2 * 4);  // D buffer 0
+        off = a1k(off + hp2 * 4);  // D buffer 1
+      } else {
+        for (int b = 0; b < 4; ++b)
+          if (ly.split || (b & 1) == 0) off = a1k(off + hp2 * 2);
+      }
+    } else {
+      const size_t xld = static_cast<size_t>(round_up(shp[i].cols, 8));
+      off = a1k(off + hp2 * e);                     // S
+      off = a1k(off + hp2 * e);                     // B
+      off = a1k(off + shp[i].rows * xld * e);       // X buffer 0
+      off = a1k(off + shp[i].rows * xld * e);       // X buffer 1
+    }
+  }
+  ly.total = off;
+  return ly;
+}
+
+// Fill MatInfo buffer pointers for matrix i.
+MatInfo mat_info(const Layout& ly, const ifnso_batch_desc* b, void* const* out, uint8_t* ws, int i) {
+  const Shape& s = ly.shp[i];
+  MatInfo mi;
+  memset(&mi, 0, sizeof(mi));
+  mi.in = b->in[i];
+  mi.out = out ? out[i] : nullptr;
+  mi.rows = s.rows;
+  mi.cols = s.cols;
+  mi.ld = s.ld;
+  mi.h = static_cast<int32_t>(s.h);
+  mi.w = static_cast<int32_t>(s.w);
+  mi.hpad = static_cast<int32_t>(s.hpad);
+  mi.trans = s.trans;
+  const size_t hp2 = static_cast<size_t>(s.hpad) * s.hpad;
+  uint8_t* p = ws + ly.off_buf[i];
+  const size_t e = ly.f32 ? 4 : 2;
+  if (!ly.ns) {
+    mi.gp = reinterpret_cast<float*>(p);
+    p += a1k(hp2 * 4);
+    if (ly.f32) {
+      mi.d[0] = p;
+      p += a1k(hp2 * 4);
+      mi.d[2] = p;
+    } else {
+      for (int bb = 0; bb < 4; ++bb) {
+        if (ly.split || (bb & 1) == 0) {
+          mi.d[bb] = p;
+          p += a1k(hp2 * 2);
+        }
+      }
+    }
+  } else {
+    const size_t xld = static_cast<size_t>(round_up(s.cols, 8));
+    mi.s = p;
+    p += a1k(hp2 * e);
+    mi.b = p;
+    p += a1k(hp2 * e);
+    mi.x[0] = p;
+    p += a1k(s.rows * xld * e);
+    mi.x[1] = p;
+    mi.xld = static_cast<int64_t>(xld);
+  }
+  return mi;
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const uint8_t* c = static_cast<const uint8_t*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t batch_sig(const ifnso_plan* plan, const ifnso_batch_desc* b, void* const* out, const void* ws,
+                   const ifnso_coeffs* cf, const double* poly, int degree, int steps, int kind) {
+  uint64_t h = 1469598103934665603ull;
+  int opts[6] = {plan->L, resolved_split(plan), plan->scale, plan->dtype, kind, steps};
+  h = fnv(h, opts, sizeof(opts));
+  h = fnv(h, &ws, sizeof(ws));
+  h = fnv(h, &b->count, sizeof(b->count));
+  for (int i = 0; i < b->count; ++i) {
+    h = fnv(h, &b->in[i], sizeof(void*));
+    if (out) h = fnv(h, &out[i], sizeof(void*));
+    h = fnv(h, &b->rows[i], 8);
+    h = fnv(h, &b->cols[i], 8);
+    int64_t ld = b->ld ? b->ld[i] : b->cols[i];
+    h = fnv(h, &ld, 8);
+  }
+  if (cf) {
+    h = fnv(h, &cf->K, sizeof(cf->K));
+    h = fnv(h, &cf->device, sizeof(void*));
+    if (cf->host) h = fnv(h, cf->host, sizeof(double) * cf->K);
+  }
+  if (poly) h = fnv(h, poly, sizeof(double) * (degree == 5 ? 3 : 2));
+  return h;
+}
+
+ifnso_status ensure_meta_host(ifnso_plan* plan, size_t bytes, cudaStream_t stream) {
+  if (plan->meta_cap >= bytes) {
+    // the previous upload may still read the pinned buffer
+    IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    return IFNSO_OK;
+  }
+  if (plan->meta_host) {
+    IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+    cudaFreeHost(plan->meta_host);
+    plan->meta_host = nullptr;
+    plan->meta_cap = 0;
+  }
+  IFNSO_CUDA(cudaMallocHost(&plan->meta_host, bytes), "cudaMallocHost (plan metadata)");
+  plan->meta_cap = bytes;
+  return IFNSO_OK;
+}
+
+int grid_for(const ifnso_plan* plan, size_t items) {
+  int g = plan->num_sms;
+  if (plan->max_ctas > 0 && plan->max_ctas < g) g = plan->max_ctas;
+  if (static_cast<size_t>(g) > items) g = static_cast<int>(items);
+  return g < 1 ? 1 : g;
+}
+
+ifnso_status check_ws(const Layout& ly, void* ws, size_t ws_bytes) {
+  if (!ws) return fail(IFNSO_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 1024 != 0) return fail(IFNSO_ERR_WORKSPACE, "workspace is not 1024-byte aligned");
+  if (ws_bytes < ly.total)
+    return fail(IFNSO_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, ly.total);
+  return IFNSO_OK;
+}
+
+CUtensorMapDataType bf16_t() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+CUtensorMapDataType f16_t() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+
+// ---------------------------------------------------------------- IFNSO metadata
+ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void* const* out, uint8_t* ws,
+                              const double* host_coef, int K, uint8_t* meta) {
+  memset(meta, 0, ly.meta_bytes);
+  const int n = ly.count;
+  MatInfo* mats = reinterpret_cast<MatInfo*>(meta + ly.off_mats);
+  for (int i = 0; i < n; ++i) mats[i] = mat_info(ly, b, out, ws, i);
+  if (host_coef) {
+    double* c = reinterpret_cast<double*>(meta + ly.off_coef);
+    for (int k = 0; k < K; ++k) c[k] = host_coef[k];
+  }
+  if (ly.f32) {
+    SgProblem* pr = reinterpret_cast<SgProblem*>(meta + ly.off_probs);
+    for (int i = 0; i < n; ++i) {
+      const Shape& s = ly.shp[i];
+      const MatInfo& mi = mats[i];
+      const float* in = static_cast<const float*>(mi.in);
+      const int64_t hp = s.hpad;
+      // Gram: A(i,k) = in[i ld + k] (wide) or in[k ld + i] (tall)
+      SgProblem g{};
+      g.A = g.B = in;
+      g.sa0 = g.sb0 = s.trans ? 1 : s.ld;
+      g.sa1 = g.sb1 = s.trans ? s.ld : 1;
+      g.a_rows = g.b_rows = static_cast<int32_t>(s.h);
+      g.M = g.N = static_cast<int32_t>(hp);
+      g.K = static_cast<int32_t>(s.w);
+      g.mat = i;
+      g.ld_aux = hp;
+      g.pacc = mi.gp;
+      pr[ly.pi_gram + i] = g;
+      for (int par = 0; par < 2; ++par) {
+        const float* src = static_cast<const float*>(mi.d[par ? 2 : 0]);
+        float* dst = static_cast<float*>(mi.d[par ? 0 : 2]);
+        SgProblem q{};
+        q.A = q.B = src;
+        q.sa0 = q.sb0 = hp;
+        q.sa1 = q.sb1 = 1;
+        q.a_rows = q.b_rows = static_cast<int32_t>(hp);
+        q.M = q.N = q.K = static_cast<int32_t>(hp);
+        q.mat = i;
+        q.ld_aux = q.ld_out = hp;
+        q.aux0 = src;
+        q.out0 = dst;
+        q.pacc = mi.gp;
+        pr[ly.pi_sqr + par * n + i] = q;
+      }
+      SgProblem a{};
+      a.A = mi.gp;  // P (FP32, symmetric)
+      a.sa0 = hp;
+      a.sa1 = 1;
+      a.a_rows = static_cast<int32_t>(s.h);
+      a.B = in;
+      if (!s.trans) {  // B(n, k) = A[k][n]
+        a.sb0 = 1;
+        a.sb1 = s.ld;
+      } else {  // B(n, k) = M[n][k]
+        a.sb0 = s.ld;
+        a.sb1 = 1;
+      }
+      a.b_rows = static_cast<int32_t>(s.w);
+      a.M = static_cast<int32_t>(s.h);
+      a.N = static_cast<int32_t>(s.w);
+      a.K = static_cast<int32_t>(s.h);
+      a.mat = i;
+      a.out_trans = s.trans;
+      a.rows_out = static_cast<int32_t>(s.rows);
+      a.cols_out = static_cast<int32_t>(s.cols);
+      a.ld_out = s.cols;
+      a.out0 = static_cast<float*>(mi.out);
+      pr[ly.pi_apply + i] = a;
+    }
+    return IFNSO_OK;
+  }
+  TcProblem* pr = reinterpret_cast<TcProblem*>(meta + ly.off_probs);
+  for (int i = 0; i < n; ++i) {
+    const Shape& s = ly.shp[i];
+    const MatInfo& mi = mats[i];
+    const int64_t hp = s.hpad;
+    // Gram T_0 = A A^T: both operands are the input, K-major when A = M,
+    // MN-major when A = M^T (the tall input is read through its own layout).
+    TcProblem& g = pr[ly.pi_gram + i];
+    bool ok;
+    if (!s.trans) ok = map_k(&g.mapA[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+    else ok = map_mn(&g.mapA[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+    if (!ok) return fail(IFNSO_ERR_CUDA, "cuTensorMapEncodeTiled failed (matrix %d, input)", i);
+    g.mapB[0] = g.mapA[0];
+    g.a_mn = g.b_mn = s.trans;
+    g.n_kb = static_cast<int32_t>((s.w + BK - 1) / BK);
+    g.mat = i;
+    g.ld_aux = hp;
+    g.pacc = mi.gp;
+    // squarings: src buffer parity par -> dst 1 - par
+    for (int par = 0; par < 2; ++par) {
+      TcProblem& q = pr[ly.pi_sqr + par * n + i];
+      const void* shi = mi.d[2 * par];
+      const void* slo = mi.d[2 * par + 1];
+      if (!map_k(&q.mapA[0], f16_t(), shi, hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (D hi)");
+      q.mapB[0] = q.mapA[0];
+      if (ly.split) {
+        if (!map_k(&q.mapA[1], f16_t(), slo, hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (D lo)");
+        q.mapB[1] = q.mapA[1];
+      }
+      q.n_kb = static_cast<int32_t>(hp / BK);
+      q.mat = i;
+      q.ld_aux = q.ld_out = hp;
+      q.aux0 = shi;
+      q.aux1 = ly.split ? slo : nullptr;
+      q.out0 = mi.d[2 * (1 - par)];
+      q.out1 = ly.split ? mi.d[2 * (1 - par) + 1] : nullptr;
+      q.pacc = mi.gp;
+    }
+    // apply: A operand P (BF16 hi/lo in D buffer (L-1) % 2), B operand the input
+    TcProblem& a = pr[ly.pi_apply + i];
+    const int fb = (ly.L - 1) % 2;
+    if (!map_k(&a.mapA[0], bf16_t(), mi.d[2 * fb], hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (P hi)");
+    if (ly.split && !map_k(&a.mapA[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp))
+      return fail(IFNSO_ERR_CUDA, "tensor map (P lo)");
+    if (!s.trans) {
+      // Y = P A: B(n, k) = A[k][n], contiguous along n
+      ok = map_mn(&a.mapB[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+      a.b_mn = 1;
+      a.out_trans = 0;
+    } else {
+      // out = M P: computed as (P M^T)^T, B(n, k) = M[n][k], tile stored transposed
+      ok = map_k(&a.mapB[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+      a.b_mn = 0;
+      a.out_trans = 1;
+    }
+    if (!ok) return fail(IFNSO_ERR_CUDA, "tensor map (apply input)");
+    a.a_mn = 0;
+    a.n_kb = static_cast<int32_t>(hp / BK);
+    a.mat = i;
+    a.rows_out = static_cast<int32_t>(s.rows);
+    a.cols_out = static_cast<int32_t>(s.cols);
+    a.ld_out = s.cols;
+    a.out0 = mi.out;
+  }
+  std::vector<WorkItem> sy, ap;
+  sym_items(ly.shp, sy);
+  app_items(ly.shp, ap);
+  memcpy(meta + ly.off_items_sym, sy.data(), sy.size() * sizeof(WorkItem));
+  memcpy(meta + ly.off_items_app, ap.data(), ap.size() * sizeof(WorkItem));
+  return IFNSO_OK;
+}
+
+// ---------------------------------------------------------------- NS metadata
+ifnso_status build_ns_meta(const Layout& ly, const ifnso_batch_desc* b, void* const* out, uint8_t* ws,
+                           uint8_t* meta) {
+  memset(meta, 0, ly.meta_bytes);
+  const int n = ly.count;
+  const int steps = ly.steps;
+  MatInfo* mats = reinterpret_cast<MatInfo*>(meta + ly.off_mats);
+  for (int i = 0; i < n; ++i) mats[i] = mat_info(ly, b, out, ws, i);
+  auto xcur = [&](int i, int st) -> const void* { return st == 0 ? mats[i].in : mats[i].x[(st - 1) % 2]; };
+  auto xcur_ld = [&](int i, int st) -> int64_t { return st == 0 ? ly.shp[i].ld : mats[i].xld; };
+  auto xnext = [&](int i, int st) -> void* { return st == steps - 1 ? mats[i].out : mats[i].x[st % 2]; };
+  auto xnext_ld = [&](int i, int st) -> int64_t { return st == steps - 1 ? ly.shp[i].cols : mats[i].xld; };
+  if (ly.f32) {
+    SgProblem* pr = reinterpret_cast<SgProblem*>(meta + ly.off_probs);
+    for (int i = 0; i < n; ++i) {
+      const Shape& s = ly.shp[i];
+      const MatInfo& mi = mats[i];
+      const int64_t hp = s.hpad;
+      for (int st = 0; st < steps; ++st) {
+        const float* X = static_cast<const float*>(xcur(i, st));
+        const int64_t xl = xcur_ld(i, st);
+        SgProblem g{};
+        g.A = g.B = X;
+        g.sa0 = g.sb0 = s.trans ? 1 : xl;
+        g.sa1 = g.sb1 = s.trans ? xl : 1;
+        g.a_rows = g.b_rows = static_cast<int32_t>(s.h);
+        g.M = g.N = static_cast<int32_t>(hp);
+        g.K = static_cast<int32_t>(s.w);
+        g.mat = i;
+        g.ld_out = hp;
+        g.out0 = static_cast<float*>(mi.s);
+        pr[ly.pi_ns_gram + st * n + i] = g;
+        SgProblem a{};
+        a.A = static_cast<const float*>(mi.b);  // B or S (set at launch through pi)
+        a.sa0 = hp;
+        a.sa1 = 1;
+        a.a_rows = static_cast<int32_t>(s.h);
+        a.B = X;
+        if (!s.trans) {
+          a.sb0 = 1;
+          a.sb1 = xl;
+        } else {
+          a.sb0 = xl;
+          a.sb1 = 1;
+        }
+        a.b_rows = static_cast<int32_t>(s.w);
+        a.M = static_cast<int32_t>(s.h);
+        a.N = static_cast<int32_t>(s.w);
+        a.K = static_cast<int32_t>(s.h);
+        a.mat = i;
+        a.out_trans = s.trans;
+        a.rows_out = static_cast<int32_t>(s.rows);
+        a.cols_out = static_cast<int32_t>(s.cols);
+        a.ld_out = xnext_ld(i, st);
+        a.out0 = static_cast<float*>(xnext(i, st));
+        a.aux0 = X;
+        a.ld_aux = xl;
+        pr[ly.pi_ns_apply + st * n + i] = a;
+      }
+      SgProblem q{};
+      q.A = q.B = static_cast<const float*>(mi.s);
+      q.sa0 = q.sb0 = hp;
+      q.sa1 = q.sb1 = 1;
+      q.a_rows = q.b_rows = static_cast<int32_t>(hp);
+      q.M = q.N = q.K = static_cast<int32_t>(hp);
+      q.mat = i;
+      q.ld_aux = q.ld_out = hp;
+      q.aux0 = static_cast<const float*>(mi.s);
+      q.out0 = static_cast<float*>(mi.b);
+      pr[ly.pi_ns_sqr + i] = q;
+    }
+    return IFNSO_OK;
+  }
+  TcProblem* pr = reinterpret_cast<TcProblem*>(meta + ly.off_probs);
+  for (int i = 0; i < n; ++i) {
+    const Shape& s = ly.shp[i];
+    const MatInfo& mi = mats[i];
+    const int64_t hp = s.hpad;
+    for (int st = 0; st < steps; ++st) {
+      const void* X = xcur(i, st);
+      const int64_t xl = xcur_ld(i, st);
+      TcProblem& g = pr[ly.pi_ns_gram + st * n + i];
+      bool ok = !s.trans ? map_k(&g.mapA[0], bf16_t(), X, s.cols, s.rows, xl)
+                         : map_mn(&g.mapA[0], bf16_t(), X, s.cols, s.rows, xl);
+      if (!ok) return fail(IFNSO_ERR_CUDA, "tensor map (NS X)");
+      g.mapB[0] = g.mapA[0];
+      g.a_mn = g.b_mn = s.trans;
+      g.n_kb = static_cast<int32_t>((s.w + BK - 1) / BK);
+      g.mat = i;
+      g.ld_out = hp;
+      g.out0 = mi.s;
+      TcProblem& a = pr[ly.pi_ns_apply + st * n + i];
+      // A operand (B or S) filled below per degree; B operand X
+      if (!s.trans) {
+        ok = map_mn(&a.mapB[0], bf16_t(), X, s.cols, s.rows, xl);
+        a.b_mn = 1;
+        a.out_trans = 0;
+      } else {
+        ok = map_k(&a.mapB[0], bf16_t(), X, s.cols, s.rows, xl);
+        a.b_mn = 0;
+        a.out_trans = 1;
+      }
+      if (!ok) return fail(IFNSO_ERR_CUDA, "tensor map (NS apply X)");
+      a.n_kb = static_cast<int32_t>(hp / BK);
+      a.mat = i;
+      a.rows_out = static_cast<int32_t>(s.rows);
+      a.cols_out = static_cast<int32_t>(s.cols);
+      a.ld_out = xnext_ld(i, st);
+      a.out0 = xnext(i, st);
+      a.aux0 = X;
+      a.ld_aux = xl;
+    }
+    TcProblem& q = pr[ly.pi_ns_sqr + i];
+    if (!map_k(&q.mapA[0], bf16_t(), mi.s, hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (NS S)");
+    q.mapB[0] = q.mapA[0];
+    q.n_kb = static_cast<int32_t>(hp / BK);
+    q.mat = i;
+    q.ld_aux = q.ld_out = hp;
+    q.aux0 = mi.s;
+    q.out0 = mi.b;
+  }
+  std::vector<WorkItem> sy, ap;
+  sym_items(ly.shp, sy);
+  app_items(ly.shp, ap);
+  memcpy(meta + ly.off_items_sym, sy.data(), sy.size() * sizeof(WorkItem));
+  memcpy(meta + ly.off_items_app, ap.data(), ap.size() * sizeof(WorkItem));
+  return IFNSO_OK;
+}
+
+// Set the A operand of every NS apply problem to B (quintic) or S (cubic).
+ifnso_status ns_set_apply_source(const Layout& ly, uint8_t* meta, int use_b) {
+  const int n = ly.count;
+  MatInfo* mats = reinterpret_cast<MatInfo*>(meta + ly.off_mats);
+  if (ly.f32) {
+    SgProblem* pr = reinterpret_cast<SgProblem*>(meta + ly.off_probs);
+    for (int st = 0; st < ly.steps; ++st)
+      for (int i = 0; i < n; ++i)
+        pr[ly.pi_ns_apply + st * n + i].A = static_cast<const float*>(use_b ? mats[i].b : mats[i].s);
+    return IFNSO_OK;
+  }
+  TcProblem* pr = reinterpret_cast<TcProblem*>(meta + ly.off_probs);
+  for (int i = 0; i < n; ++i) {
+    const int64_t hp = ly.shp[i].hpad;
+    CUtensorMap m;
+    if (!map_k(&m, bf16_t(), use_b ? mats[i].b : mats[i].s, hp, hp, hp))
+      return fail(IFNSO_ERR_CUDA, "tensor map (NS apply operand)");
+    for (int st = 0; st < ly.steps; ++st) pr[ly.pi_ns_apply + st * n + i].mapA[0] = m;
+  }
+  return IFNSO_OK;
+}
+
+ifnso_status init_plan_device(ifnso_plan* p) {
+  if (p->num_sms > 0) return IFNSO_OK;
+  int dev = 0;
+  IFNSO_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  cudaDeviceProp prop;
+  IFNSO_CUDA(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  if (p->dtype == IFNSO_BF16 && prop.major * 10 + prop.minor < 100)
+    return fail(IFNSO_ERR_UNSUPPORTED, "BF16 plans need a tcgen05 GPU (sm_100 family), found sm_%d%d", prop.major, prop.minor);
+  p->num_sms = prop.multiProcessorCount;
+  return IFNSO_OK;
+}
+
+template <class Params>
+Params base_params(uint8_t* ws, const Layout& ly, const ifnso_coeffs* cf) {
+  Params p{};
+  p.scal = reinterpret_cast<MatScalars*>(ws + ly.off_scal);
+  p.coef.K = cf ? cf->K : 0;
+  if (cf && cf->device) {
+    p.coef.f32 = cf->device;
+    p.coef.stride = cf->K;
+  } else {
+    p.coef.d64 = reinterpret_cast<const double*>(ws + ly.off_coef);
+  }
+  return p;
+}
+
+}  // namespace
+
+void ifnso::count_launch(int n) { g_launches += static_cast<uint64_t>(n); }
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* ifnso_last_error(void) { return g_err.c_str(); }
+
+uint64_t ifnso_launch_count(void) { return g_launches.load(); }
+
+ifnso_status ifnso_plan_create(ifnso_plan** plan, int64_t h, int64_t w, ifnso_dtype dtype,
+                               const int32_t* exponents, int32_t K) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  *plan = nullptr;
+  if (h <= 0 || w <= 0 || h > w)
+    return fail(IFNSO_ERR_INVALID_ARG, "plan shape %lldx%lld must satisfy 0 < h <= w", (long long)h, (long long)w);
+  if (dtype != IFNSO_F32 && dtype != IFNSO_BF16) return fail(IFNSO_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+  if (K < 2 || K > 31 || !exponents) return fail(IFNSO_ERR_INVALID_ARG, "K = %d must be in [2, 31]", K);
+  if (exponents[0] != 0) return fail(IFNSO_ERR_INVALID_ARG, "exponents[0] must be 0");
+  for (int k = 1; k < K; ++k)
+    if (exponents[k] != (1 << (k - 1)))
+      return fail(IFNSO_ERR_INVALID_ARG,
+                  "exponents[%d] = %d: repeated squaring produces only 0, 1, 2, 4, ... (exponents[k] = 2^(k-1))", k,
+                  exponents[k]);
+  ifnso_plan* p = new (std::nothrow) ifnso_plan();
+  if (!p) return fail(IFNSO_ERR_OOM, "out of host memory");
+  p->h = h;
+  p->w = w;
+  p->dtype = dtype;
+  p->L = K - 1;
+  *plan = p;
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  switch (option) {
+    case IFNSO_OPT_PRECISION:
+      if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "precision %lld", (long long)value);
+      plan->precision = static_cast<int>(value);
+      break;
+    case IFNSO_OPT_SCALE:
+      if (value < 0 || value > 1) return fail(IFNSO_ERR_INVALID_ARG, "scale %lld", (long long)value);
+      plan->scale = static_cast<int>(value);
+      break;
+    case IFNSO_OPT_MAX_CTAS:
+      if (value < 0) return fail(IFNSO_ERR_INVALID_ARG, "max ctas %lld", (long long)value);
+      plan->max_ctas = static_cast<int>(value);
+      break;
+    case IFNSO_OPT_STOP_AFTER:
+      plan->stop_after = static_cast<int>(value);
+      break;
+    default:
+      return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
+  }
+  plan->sig_valid = false;
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t* value) {
+  if (!plan || !value) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
+  switch (option) {
+    case IFNSO_OPT_PRECISION:
+      *value = plan->dtype == IFNSO_BF16 ? (resolved_split(plan) ? IFNSO_PREC_SPLIT : IFNSO_PREC_PLAIN) : IFNSO_PREC_PLAIN;
+      return IFNSO_OK;
+    case IFNSO_OPT_SCALE: *value = plan->scale; return IFNSO_OK;
+    case IFNSO_OPT_MAX_CTAS: *value = plan->max_ctas; return IFNSO_OK;
+    case IFNSO_OPT_STOP_AFTER: *value = plan->stop_after; return IFNSO_OK;
+    default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
+  }
+}
+
+ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
+  if (!plan) return IFNSO_OK;
+  if (plan->meta_host) {
+    cudaDeviceSynchronize();
+    cudaFreeHost(plan->meta_host);
+  }
+  delete plan;
+  return IFNSO_OK;
+}
+
+size_t ifnso_workspace_bytes(const ifnso_plan* plan, const ifnso_batch_desc* batch) {
+  if (!plan) {
+    fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+    return 0;
+  }
+  std::vector<Shape> shp;
+  if (read_batch(plan, batch, shp) != IFNSO_OK) return 0;
+  return make_layout(plan, shp, 0, 0, plan->L + 1).total;
+}
+
+size_t ns_workspace_bytes(const ifnso_plan* plan, const ifnso_batch_desc* batch) {
+  if (!plan) {
+    fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+    return 0;
+  }
+  std::vector<Shape> shp;
+  if (read_batch(plan, batch, shp) != IFNSO_OK) return 0;
+  // the step count only changes the metadata; size for up to 16 steps
+  return make_layout(plan, shp, 1, 16, 1).total;
+}
+
+ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch, const ifnso_coeffs* coeffs,
+                                 void* const* out, void* workspace, size_t workspace_bytes,
+                                 ifnso_stream_t stream_) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(plan->mu);
+  std::vector<Shape> shp;
+  ifnso_status st = read_batch(plan, batch, shp);
+  if (st != IFNSO_OK) return st;
+  if (!coeffs || coeffs->K != plan->L + 1 || (!coeffs->host == !coeffs->device))
+    return fail(IFNSO_ERR_INVALID_ARG, "coefficients: need K = %d and exactly one of host/device", plan->L + 1);
+  if (!out) return fail(IFNSO_ERR_INVALID_ARG, "out is NULL");
+  for (int i = 0; i < batch->count; ++i) {
+    if (!out[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is NULL", i);
+    if (out[i] == batch->in[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] aliases the input", i);
+    if (reinterpret_cast<uintptr_t>(out[i]) % 16 != 0)
+      return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is not 16-byte aligned", i);
+  }
+  if (batch->count == 0) return IFNSO_OK;
+  if ((st = init_plan_device(plan)) != IFNSO_OK) return st;
+  Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
+  if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const uint64_t sig = batch_sig(plan, batch, out, workspace, coeffs, nullptr, 0, 0, 1);
+  if (!plan->sig_valid || plan->sig != sig) {
+    if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
+    uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
+    if ((st = build_ifnso_meta(ly, batch, out, ws, coeffs->host, coeffs->K, meta)) != IFNSO_OK) return st;
+    IFNSO_CUDA(cudaMemcpyAsync(ws, meta, ly.meta_bytes, cudaMemcpyHostToDevice, stream), "metadata upload");
+    plan->sig = sig;
+    plan->sig_valid = true;
+  }
+  const int n = ly.count;
+  const int L = ly.L;
+  const int frob = plan->scale == IFNSO_SCALE_FROB;
+  MatInfo* d_mats = reinterpret_cast<MatInfo*>(ws + ly.off_mats);
+  int hpad_max = 0;
+  for (auto& s : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(s.hpad));
+  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
+  count_launch();
+  if (ly.f32) {
+    SgParams p = base_params<SgParams>(ws, ly, coeffs);
+    const SgProblem* probs = reinterpret_cast<const SgProblem*>(ws + ly.off_probs);
+    int max_h = 0, max_w = 0;
+    for (auto& s : shp) {
+      max_h = std::max<int>(max_h, static_cast<int>(s.h));
+      max_w = std::max<int>(max_w, static_cast<int>(s.w));
+    }
+    // the Gram is computed over the whole padded h_pad x h_pad block (zeros beyond h)
+    p.probs = probs + ly.pi_gram;
+    IFNSO_CUDA(sg_launch(EPI_GRAM, p, n, hpad_max, hpad_max, stream), "FP32 Gram");
+    IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+    if (plan->stop_after == 0) return IFNSO_OK;
+    IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, 0, 1, stream), "prep");
+    if (plan->stop_after == 1) return IFNSO_OK;
+    for (int j = 1; j <= L - 1; ++j) {
+      const int par = (j - 1) % 2;
+      p.probs = probs + ly.pi_sqr + par * n;
+      p.coef_l = j + 1;
+      p.final_pass = (j == L - 1);
+      IFNSO_CUDA(sg_launch(EPI_SQR, p, n, hpad_max, hpad_max, stream), "FP32 squaring");
+      if (plan->stop_after == 1 + j) return IFNSO_OK;
+    }
+    p.probs = probs + ly.pi_apply;
+    p.coef_l = 0;
+    p.final_pass = 0;
+    IFNSO_CUDA(sg_launch(EPI_APPLY, p, n, max_h, max_w, stream), "FP32 apply");
+    return IFNSO_OK;
+  }
+  TcParams p = base_params<TcParams>(ws, ly, coeffs);
+  const TcProblem* probs = reinterpret_cast<const TcProblem*>(ws + ly.off_probs);
+  const WorkItem* sym = reinterpret_cast<const WorkItem*>(ws + ly.off_items_sym);
+  const WorkItem* app = reinterpret_cast<const WorkItem*>(ws + ly.off_items_app);
+  const int nab = ly.split ? 2 : 1;
+  p.probs = probs + ly.pi_gram;
+  p.items = sym;
+  p.n_items = static_cast<int32_t>(ly.n_sym);
+  IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "Gram pass");
+  IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+  if (plan->stop_after == 0) return IFNSO_OK;
+  IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, ly.split, 0, stream), "prep");
+  if (plan->stop_after == 1) return IFNSO_OK;
+  for (int j = 1; j <= L - 1; ++j) {
+    const int par = (j - 1) % 2;
+    p.probs = probs + ly.pi_sqr + par * n;
+    p.items = sym;
+    p.n_items = static_cast<int32_t>(ly.n_sym);
+    p.coef_l = j + 1;
+    p.final_pass = (j == L - 1);
+    IFNSO_CUDA(tc_launch(EPI_SQR, nab, nab, p, grid_for(plan, ly.n_sym), stream), "squaring pass");
+    if (plan->stop_after == 1 + j) return IFNSO_OK;
+  }
+  p.probs = probs + ly.pi_apply;
+  p.items = app;
+  p.n_items = static_cast<int32_t>(ly.n_app);
+  p.coef_l = 0;
+  p.final_pass = 0;
+  IFNSO_CUDA(tc_launch(EPI_APPLY, nab, 1, p, grid_for(plan, ly.n_app), stream), "apply pass");
+  return IFNSO_OK;
+}
+
+ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const double* poly, int32_t degree,
+                        int32_t steps, void* const* out, void* workspace, size_t workspace_bytes,
+                        ifnso_stream_t stream_) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (!poly || (degree != 3 && degree != 5)) return fail(IFNSO_ERR_INVALID_ARG, "degree must be 3 or 5 with poly given");
+  if (steps < 1 || steps > 16) return fail(IFNSO_ERR_INVALID_ARG, "steps = %d must be in [1, 16]", steps);
+  std::vector<Shape> shp;
+  ifnso_status st = read_batch(plan, batch, shp);
+  if (st != IFNSO_OK) return st;
+  if (!out) return fail(IFNSO_ERR_INVALID_ARG, "out is NULL");
+  for (int i = 0; i < batch->count; ++i) {
+    if (!out[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is NULL", i);
+    if (out[i] == batch->in[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] aliases the input", i);
+    if (reinterpret_cast<uintptr_t>(out[i]) % 16 != 0)
+      return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is not 16-byte aligned", i);
+  }
+  if (batch->count == 0) return IFNSO_OK;
+  if ((st = init_plan_device(plan)) != IFNSO_OK) return st;
+  Layout ly = make_layout(plan, shp, 1, steps, 1);
+  Layout ly16 = make_layout(plan, shp, 1, 16, 1);
+  // buffers are placed for 16 steps so that the size does not depend on `steps`
+  ly.off_scal = ly16.off_scal;
+  ly.off_buf = ly16.off_buf;
+  ly.total = ly16.total;
+  if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const uint64_t sig = batch_sig(plan, batch, out, workspace, nullptr, poly, degree, steps, 2);
+  if (!plan->sig_valid || plan->sig != sig) {
+    if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
+    uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
+    if ((st = build_ns_meta(ly, batch, out, ws, meta)) != IFNSO_OK) return st;
+    if ((st = ns_set_apply_source(ly, meta, degree == 5)) != IFNSO_OK) return st;
+    IFNSO_CUDA(cudaMemcpyAsync(ws, meta, ly.meta_bytes, cudaMemcpyHostToDevice, stream), "metadata upload");
+    plan->sig = sig;
+    plan->sig_valid = true;
+  }
+  const int n = ly.count;
+  MatInfo* d_mats = reinterpret_cast<MatInfo*>(ws + ly.off_mats);
+  MatScalars* scal = reinterpret_cast<MatScalars*>(ws + ly.off_scal);
+  int hpad_max = 0, max_h = 0, max_w = 0;
+  for (auto& s : shp) {
+    hpad_max = std::max<int>(hpad_max, static_cast<int>(s.hpad));
+    max_h = std::max<int>(max_h, static_cast<int>(s.h));
+    max_w = std::max<int>(max_w, static_cast<int>(s.w));
+  }
+  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
+  count_launch();
+  // ||A||_F^2 into the trace slot, then the scalars with the Frobenius scale
+  int gx = std::max(1, std::min(1024, 4 * plan->num_sms / std::max(1, n)));
+  IFNSO_CUDA(launch_norm2(d_mats, n, plan->dtype == IFNSO_BF16, &scal[0].trace,
+                          sizeof(MatScalars) / sizeof(double), gx, stream),
+             "norm");
+  CoefTable none{};
+  IFNSO_CUDA(launch_scalars(d_mats, n, scal, none, 0, 1, 1, stream), "scalars");
+  const float a = static_cast<float>(poly[0]);
+  const float b = static_cast<float>(poly[1]);
+  const float c = degree == 5 ? static_cast<float>(poly[2]) : 0.f;
+  if (ly.f32) {
+    SgParams p{};
+    p.scal = scal;
+    p.ns_a = a;
+    p.ns_b = b;
+    p.ns_c = c;
+    p.ns_bcoef = degree == 5 ? 1.f : b;
+    const SgProblem* probs = reinterpret_cast<const SgProblem*>(ws + ly.off_probs);
+    for (int s = 0; s < steps; ++s) {
+      p.ns_step = s;
+      p.probs = probs + ly.pi_ns_gram + s * n;
+      IFNSO_CUDA(sg_launch(EPI_NS_GRAM, p, n, hpad_max, hpad_max, stream), "NS Gram");
+      if (degree == 5) {
+        p.probs = probs + ly.pi_ns_sqr;
+        IFNSO_CUDA(sg_launch(EPI_NS_SQR, p, n, hpad_max, hpad_max, stream), "NS square");
+      }
+      p.probs = probs + ly.pi_ns_apply + s * n;
+      IFNSO_CUDA(sg_launch(EPI_NS_APPLY, p, n, max_h, max_w, stream), "NS apply");
+    }
+    return IFNSO_OK;
+  }
+  TcParams p{};
+  p.scal = scal;
+  p.ns_a = a;
+  p.ns_b = b;
+  p.ns_c = c;
+  p.ns_bcoef = degree == 5 ? 1.f : b;
+  const TcProblem* probs = reinterpret_cast<const TcProblem*>(ws + ly.off_probs);
+  const WorkItem* sym = reinterpret_cast<const WorkItem*>(ws + ly.off_items_sym);
+  const WorkItem* app = reinterpret_cast<const WorkItem*>(ws + ly.off_items_app);
+  for (int s = 0; s < steps; ++s) {
+    p.ns_step = s;
+    p.probs = probs + ly.pi_ns_gram + s * n;
+    p.items = sym;
+    p.n_items = static_cast<int32_t>(ly.n_sym);
+    IFNSO_CUDA(tc_launch(EPI_NS_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "NS Gram");
+    if (degree == 5) {
+      p.probs = probs + ly.pi_ns_sqr;
+      IFNSO_CUDA(tc_launch(EPI_NS_SQR, 1, 1, p, grid_for(plan, ly.n_sym), stream), "NS square");
+    }
+    p.probs = probs + ly.pi_ns_apply + s * n;
+    p.items = app;
+    p.n_items = static_cast<int32_t>(ly.n_app);
+    IFNSO_CUDA(tc_launch(EPI_NS_APPLY, 1, 1, p, grid_for(plan, ly.n_app), stream), "NS apply");
+  }
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_device_status(const ifnso_plan* plan, const void* workspace, int32_t count, int32_t* per_matrix,
+                                 double* o_out, double* trace_out, ifnso_stream_t stream_) {
+  if (!plan || !workspace || count < 0) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  if (count == 0) return IFNSO_OK;
+  // the scalars sit right after the metadata, whose size depends on the batch:
+  // find them through the MatInfo of matrix 0 (the offset of its buffers)
+  std::vector<MatInfo> mats(count);
+  IFNSO_CUDA(cudaMemcpy(mats.data(), workspace, count * sizeof(MatInfo), cudaMemcpyDeviceToHost), "status read");
+  const uint8_t* buf0 = static_cast<const uint8_t*>(mats[0].gp ? static_cast<const void*>(mats[0].gp) : mats[0].s);
+  const size_t scal_bytes = a1k(count * sizeof(MatScalars));
+  const uint8_t* scal_ptr = buf0 - scal_bytes;
+  std::vector<MatScalars> sc(count);
+  IFNSO_CUDA(cudaMemcpy(sc.data(), scal_ptr, count * sizeof(MatScalars), cudaMemcpyDeviceToHost), "status read");
+  bool timeout = false;
+  for (int i = 0; i < count; ++i) {
+    if (per_matrix) per_matrix[i] = sc[i].status;
+    if (o_out) o_out[i] = sc[i].s2;
+    if (trace_out) trace_out[i] = sc[i].trace;
+    if (sc[i].status & IFNSO_DEV_TIMEOUT) timeout = true;
+  }
+  if (timeout) return fail(IFNSO_ERR_DEVICE_TIMEOUT, "a device wait timed out");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch, void* workspace,
+                                  int32_t index, int32_t which, void** ptr, int64_t* ld) {
+  if (!plan || !ptr || !ld || !workspace) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
+  std::vector<Shape> shp;
+  ifnso_status st = read_batch(plan, batch, shp);
+  if (st != IFNSO_OK) return st;
+  if (index < 0 || index >= batch->count) return fail(IFNSO_ERR_INVALID_ARG, "index %d", index);
+  Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
+  MatInfo mi = mat_info(ly, batch, nullptr, static_cast<uint8_t*>(workspace), index);
+  *ld = shp[index].hpad;
+  if (which == 0) *ptr = mi.gp;
+  else if (which >= 1 && which <= 4) *ptr = mi.d[which - 1];
+  else return fail(IFNSO_ERR_INVALID_ARG, "which = %d", which);
+  if (!*ptr) return fail(IFNSO_ERR_INVALID_ARG, "buffer %d is not used by this plan", which);
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dtype, double* norm2_out,
+                                   ifnso_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!batch || !norm2_out) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
+  if (dtype != IFNSO_BF16 && dtype != IFNSO_F32) return fail(IFNSO_ERR_INVALID_ARG, "dtype");
+  ifnso_plan tmp;
+  tmp.h = tmp.w = INT64_MAX / 4;
+  tmp.dtype = dtype;
+  std::vector<Shape> shp;
+  ifnso_status st = read_batch(&tmp, batch, shp);
+  if (st != IFNSO_OK) return st;
+  if (batch->count == 0) return IFNSO_OK;
+  int dev = 0, sms = 0;
+  IFNSO_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  IFNSO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  IFNSO_CUDA(cudaMemsetAsync(norm2_out, 0, batch->count * sizeof(double), stream), "reset");
+  count_launch();
+  // one launch per matrix with its description passed through a small device copy
+  // kept in static storage of this entry point (grown on demand)
+  static MatInfo* d_mi = nullptr;
+  static int d_cap = 0;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (d_cap < batch->count) {
+    if (d_mi) {
+      cudaStreamSynchronize(stream);
+      cudaFree(d_mi);
+    }
+    IFNSO_CUDA(cudaMalloc(&d_mi, batch->count * sizeof(MatInfo)), "cudaMalloc");
+    d_cap = batch->count;
+  }
+  std::vector<MatInfo> h(batch->count);
+  for (int i = 0; i < batch->count; ++i) {
+    memset(&h[i], 0, sizeof(MatInfo));
+    h[i].in = batch->in[i];
+    h[i].rows = shp[i].rows;
+    h[i].cols = shp[i].cols;
+    h[i].ld = shp[i].ld;
+  }
+  IFNSO_CUDA(cudaMemcpyAsync(d_mi, h.data(), h.size() * sizeof(MatInfo), cudaMemcpyHostToDevice, stream), "upload");
+  IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  int gx = std::max(1, std::min(1024, 4 * sms / std::max(1, batch->count)));
+  IFNSO_CUDA(launch_norm2(d_mi, batch->count, dtype == IFNSO_BF16, norm2_out, 1, gx, stream), "norm");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_learn_coefficients(int32_t L, int32_t iters, int32_t samples, double lr, int32_t step_size,
+                                      double gamma, uint32_t seed, double* w_out) {
+  if (L < 1 || L > 30 || iters < 0 || samples < 1 || samples > 4096 || !w_out)
+    return fail(IFNSO_ERR_INVALID_ARG, "learn: L in [1,30], samples in [1,4096], iters >= 0");
+  double* d_w = nullptr;
+  IFNSO_CUDA(cudaMalloc(&d_w, sizeof(double) * L), "cudaMalloc");
+  const double cL = std::exp(0.5) * (std::pow(2.0, L / 2.0) - 1.0);
+  cudaError_t e = launch_learn(L, iters, samples, lr, step_size, gamma, seed, cL, d_w, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(w_out, d_w, sizeof(double) * L, cudaMemcpyDeviceToHost);
+  cudaFree(d_w);
+  if (e != cudaSuccess) return cuda_fail(e, "coefficient learning");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_synth_lowrank_bf16(void* out, int64_t rows, int64_t cols, int64_t ld, uint32_t seed, float alpha,
+                                      float beta, ifnso_stream_t stream_) {
+  if (!out || rows <= 0 || cols <= 0 || ld < cols || rows > 0xFFFFFFFFll || cols > 0xFFFFFFFFll)
+    return fail(IFNSO_ERR_INVALID_ARG, "synth: bad shape or pointer");
+  if ((rows + 31) / 32 > 65535) return fail(IFNSO_ERR_INVALID_ARG, "synth: too many rows");
+  IFNSO_CUDA(launch_synth_lowrank(out, rows, cols, ld, seed, alpha, beta, reinterpret_cast<cudaStream_t>(stream_)),
+             "synth");
+  return IFNSO_OK;
+}
+
+}  // extern "C"

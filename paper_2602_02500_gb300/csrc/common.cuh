@@ -1,0 +1,164 @@
+// Types shared by the host orchestration and the kernels of the IFNSO library.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ifnso {
+
+// Tensor-core tiles: 128 x 256 outputs per tile (one tcgen05 MMA of M = 128,
+// N = 256 per 16-wide K step), K blocks of 64 elements (one 128-byte
+// swizzled row per operand row).  Square h x h workspace buffers are padded
+// to multiples of 256 so that a symmetric 256 x 256 block grid covers them.
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;
+constexpr int HPAD = 256;
+
+enum EpiKind : int {
+  EPI_GRAM = 0,      // T_0 tile -> FP32 buffer (direct + mirrored), sum T_0^2 and tr T_0
+  EPI_SQR = 1,       // D_{l+1} = 2 D_l - D_l^2, P -= w_{l+1} D_{l+1}
+  EPI_APPLY = 2,     // Y = P A / sqrt(o)
+  EPI_NS_GRAM = 3,   // S = X X^T (BF16, direct + mirrored)
+  EPI_NS_SQR = 4,    // B = b S + c S^2 (BF16, direct + mirrored)
+  EPI_NS_APPLY = 5,  // X <- a X + (B X  or  b S X)
+};
+
+// Per-matrix scalars kept in the workspace (64 bytes).
+struct MatScalars {
+  double o2;       // sum of squares of T_0 (FP32 partials, FP64 accumulation)
+  double trace;    // tr(T_0) = ||A||_F^2
+  double s2;       // squared input scale: o = ||T_0||_F (Gram scaling) or ||A||_F^2
+  double c0;       // identity weight of the D basis, 1 + sum_l w_l (FP64)
+  float inv_s2;    // 1 / s2, rounded once to FP32
+  float inv_s;     // 1 / sqrt(s2), rounded once to FP32
+  int32_t status;  // IFNSO_DEV_* bits
+  int32_t pad0;
+  double spare[2];
+};
+static_assert(sizeof(MatScalars) == 64, "MatScalars layout");
+
+// Coefficients w_1..w_L: either one FP64 vector shared by all matrices or an
+// FP32 row per matrix (slot 0 of each row is the identity weight, ignored).
+struct CoefTable {
+  const double* d64;
+  const float* f32;
+  int32_t K;
+  int32_t stride;
+};
+
+__device__ __forceinline__ double coef_at(const CoefTable& t, int m, int l) {
+  return t.f32 ? static_cast<double>(t.f32[static_cast<int64_t>(m) * t.stride + l]) : t.d64[l];
+}
+
+// One matrix product of a tensor-core pass.  The tensor maps live in global
+// memory (64-byte aligned) and are read by TMA directly.
+struct TcProblem {
+  CUtensorMap mapA[2];  // A-operand sources (rows of the output tile)
+  CUtensorMap mapB[2];  // B-operand sources (columns of the output tile)
+  int32_t n_kb;         // number of 64-wide K blocks
+  int32_t mat;          // matrix index (scalars, coefficients, status)
+  int32_t a_mn;         // 1: A operand is MN-major in memory (TMA boxes 64 x 64)
+  int32_t b_mn;         // 1: B operand is MN-major in memory
+  int32_t out_trans;    // apply: tile element (r, c) is written to out[c][r]
+  int32_t rows_out;     // valid extent of out0 in its own layout
+  int32_t cols_out;
+  int32_t pad0;
+  int64_t ld_out;       // leading dimension of out0/out1 (elements)
+  int64_t ld_aux;       // leading dimension of aux0/aux1 and pacc (elements)
+  void* out0;
+  void* out1;
+  const void* aux0;
+  const void* aux1;
+  float* pacc;
+};
+
+static_assert(alignof(TcProblem) % 64 == 0 && sizeof(TcProblem) % alignof(TcProblem) == 0,
+              "TcProblem arrays must keep every tensor map 64-byte aligned");
+
+// A 128 x 256 output tile of one problem.  flags bit 0: the tile lies in a
+// diagonal 256 x 256 block (computed in full, no mirrored store).
+struct WorkItem {
+  uint16_t prob;
+  uint16_t tm;
+  uint16_t tn;
+  uint16_t flags;
+};
+
+struct TcParams {
+  const TcProblem* probs;
+  const WorkItem* items;
+  int32_t n_items;
+  int32_t coef_l;      // EPI_SQR: index l + 1 of the coefficient this pass adds
+  int32_t final_pass;  // EPI_SQR: write P (BF16 hi/lo) instead of D_{l+1}
+  int32_t ns_step;     // NS epilogues: step index (step 0 applies the input scale)
+  MatScalars* scal;
+  CoefTable coef;
+  float ns_a, ns_b, ns_c, ns_bcoef;
+};
+
+// Per-matrix description used by the SIMT kernels (norms, scalars, prep,
+// FP32 products).
+struct MatInfo {
+  const void* in;
+  void* out;
+  int64_t rows, cols, ld;  // M's own shape
+  int32_t h, w, hpad, trans;
+  float* gp;               // h_pad x h_pad FP32: T_0, then P
+  void* d[4];              // D buffer 0 hi, lo; D buffer 1 hi, lo
+  void* x[2];              // NS: X ping-pong (M's layout, leading dimension xld)
+  void* s;                 // NS: S = X X^T
+  void* b;                 // NS: B = b S + c S^2
+  int64_t xld;
+};
+
+// ------------------------------------------------------------ launchers
+// (defined in tc_gemm.cu / simt.cu / learn.cu; called by api.cu)
+cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int grid, cudaStream_t s);
+int tc_smem_bytes(int na, int nb);
+
+cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,
+                         int64_t out_stride, int grid_x, cudaStream_t s);
+cudaError_t launch_scalars(const MatInfo* d_mats, int count, MatScalars* scal, CoefTable coef,
+                           int L, int scale_frob, int from_norm2, cudaStream_t s);
+cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
+                        CoefTable coef, int L, int split, int f32, cudaStream_t s);
+
+struct SgProblem {
+  const float* A;  // A operand element (i, k) at A[i * sa0 + k * sa1], zero for i >= a_rows
+  const float* B;  // B operand element (j, k) at B[j * sb0 + k * sb1], zero for j >= b_rows
+  int64_t sa0, sa1, sb0, sb1;
+  int32_t a_rows, b_rows;
+  int32_t M, N, K;  // computed output extent M x N, contraction length K
+  int32_t mat;
+  int32_t out_trans;
+  int32_t rows_out, cols_out;
+  int64_t ld_out;
+  int64_t ld_aux;
+  float* out0;
+  const float* aux0;
+  float* pacc;
+};
+
+struct SgParams {
+  const SgProblem* probs;
+  int32_t coef_l;
+  int32_t final_pass;
+  int32_t ns_step;
+  int32_t pad0;
+  MatScalars* scal;
+  CoefTable coef;
+  float ns_a, ns_b, ns_c, ns_bcoef;
+};
+
+cudaError_t sg_launch(int epi, const SgParams& p, int count, int max_m, int max_n, cudaStream_t s);
+
+cudaError_t launch_learn(int L, int iters, int samples, double lr, int step_size, double gamma,
+                         uint32_t seed, double cL, double* d_w, cudaStream_t s);
+cudaError_t launch_synth_lowrank(void* out, int64_t rows, int64_t cols, int64_t ld, uint32_t seed,
+                                 float alpha, float beta, cudaStream_t s);
+
+void count_launch(int n = 1);
+
+}  // namespace ifnso

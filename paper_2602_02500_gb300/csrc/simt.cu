@@ -1,0 +1,288 @@
+// SIMT kernels of the IFNSO library: the split-K Frobenius norm, the
+// per-matrix scalars (o, 1/sqrt(o), the D-basis identity weight in FP64),
+// the elementwise initialisation D_1 = T_0/o, P = (1 + sum w) I - w_1 D_1,
+// and the FP32 GEMM that carries every product of FP32 plans.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace ifnso {
+
+namespace {
+
+constexpr int kDevZero = 1;       // IFNSO_DEV_ZERO_INPUT
+constexpr int kDevNonFinite = 2;  // IFNSO_DEV_NONFINITE
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (warp == 0) {
+    s = lane < static_cast<int>(blockDim.x >> 5) ? red[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------- norm
+// ||M||_F^2 of every matrix: block (x, m) sums the squares of rows
+// [x * chunk, (x + 1) * chunk) of matrix m in FP32 and adds its partial to
+// out[m * out_stride] in FP64.  Rows whose start is 16-byte aligned are read
+// as 16-byte vectors.
+__global__ void __launch_bounds__(256) k_norm2(const MatInfo* mats, int bf16, double* out,
+                                               int64_t out_stride) {
+  __shared__ float red[32];
+  const MatInfo& mi = mats[blockIdx.y];
+  const int64_t rows = mi.rows, cols = mi.cols, ld = mi.ld;
+  const int64_t chunk = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * chunk;
+  const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
+  float acc = 0.f;
+  if (bf16) {
+    const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(mi.in);
+    const bool vec = (ld % 8 == 0) && (cols % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    if (vec) {
+      const int64_t c8 = cols / 8;
+      const int64_t n = (r1 - r0) * c8;
+      for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const int64_t r = r0 + e / c8, c = (e % c8) * 8;
+        const uint4 u = *reinterpret_cast<const uint4*>(A + r * ld + c);
+        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float2 f = __bfloat1622float2(h2[t]);
+          acc = fmaf(f.x, f.x, acc);
+          acc = fmaf(f.y, f.y, acc);
+        }
+      }
+    } else {
+      const int64_t n = (r1 - r0) * cols;
+      for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const float f = __bfloat162float(A[(r0 + e / cols) * ld + e % cols]);
+        acc = fmaf(f, f, acc);
+      }
+    }
+  } else {
+    const float* A = static_cast<const float*>(mi.in);
+    const int64_t n = (r1 - r0) * cols;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const float f = A[(r0 + e / cols) * ld + e % cols];
+      acc = fmaf(f, f, acc);
+    }
+  }
+  const float s = block_sum(acc, red);
+  if (threadIdx.x == 0 && r0 < rows) atomicAdd(out + blockIdx.y * out_stride, static_cast<double>(s));
+}
+
+// ---------------------------------------------------------------- scalars
+// One thread per matrix: the squared scale s2 (o = sqrt(sum T_0^2) for the
+// Gram scaling of Sec. 2, ||A||_F^2 = tr T_0 for the Frobenius scaling), its
+// FP32 reciprocals, the D-basis identity weight c0 = 1 + sum_{l=1}^L w_l in
+// FP64, and the zero / non-finite status bits.
+__global__ void k_scalars(int count, MatScalars* scal, CoefTable coef, int L, int frob) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  MatScalars& s = scal[m];
+  const double s2 = frob ? s.trace : sqrt(s.o2);
+  int st = s.status;
+  double c0 = 1.0;
+  for (int l = 1; l <= L; ++l) c0 += coef_at(coef, m, l);
+  const bool fin = isfinite(s2) && isfinite(c0);
+  if (!fin) st |= kDevNonFinite;
+  if (fin && s2 == 0.0) st |= kDevZero;
+  const bool pos = fin && s2 > 0.0;
+  s.s2 = s2;
+  s.c0 = c0;
+  s.inv_s2 = pos ? static_cast<float>(1.0 / s2) : 0.f;
+  s.inv_s = pos ? static_cast<float>(1.0 / sqrt(s2)) : 0.f;
+  s.status = st;
+}
+
+// ---------------------------------------------------------------- prep
+// Elementwise over the h_pad x h_pad buffers of every matrix:
+//   d = T_0 * (1/s2)                       (D_1 = T_0 / o, the scaled Gram)
+//   P = c0 [i == j] - w_1 d                (Y' accumulated in the D basis)
+// BF16 plans store D_1 as FP16 (hi, and lo = d - hi when split) in D buffer
+// 0 and keep P in FP32 in place of T_0.  For L = 1 there is no squaring:
+// P itself is written as BF16 (hi, lo) into D buffer 0.  FP32 plans store
+// D_1 in FP32 in D buffer 0 and P in place of T_0.
+__global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* scal, CoefTable coef,
+                                              int L, int split, int f32) {
+  const int m = blockIdx.y;
+  const MatInfo& mi = mats[m];
+  const int64_t hp = mi.hpad;
+  const int64_t n = hp * hp;
+  const float inv = scal[m].inv_s2;
+  const float c0 = static_cast<float>(scal[m].c0);
+  const float w1 = static_cast<float>(coef_at(coef, m, 1));
+  float* gp = mi.gp;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / hp, j = e % hp;
+    const float d = gp[e] * inv;
+    const float p = fmaf(-w1, d, i == j ? c0 : 0.f);
+    if (f32) {
+      static_cast<float*>(mi.d[0])[e] = d;
+      gp[e] = p;
+    } else if (L == 1) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(p);
+      static_cast<__nv_bfloat16*>(mi.d[0])[e] = hi;
+      if (split) static_cast<__nv_bfloat16*>(mi.d[1])[e] = __float2bfloat16_rn(p - __bfloat162float(hi));
+    } else {
+      const __half hi = __float2half_rn(d);
+      static_cast<__half*>(mi.d[0])[e] = hi;
+      if (split) static_cast<__half*>(mi.d[1])[e] = __float2half_rn(d - __half2float(hi));
+      gp[e] = p;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- FP32 GEMM
+// C(i, j) = sum_k A(i, k) B(j, k) over 64 x 64 tiles, 16-wide K slices,
+// 256 threads with 4 x 4 outputs each, followed by the epilogue of the pass.
+template <int EPI>
+__global__ void __launch_bounds__(256) k_sgemm(const SgParams p) {
+  const SgProblem& pr = p.probs[blockIdx.z];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  if (m0 >= pr.M || n0 >= pr.N) return;
+  __shared__ float As[16][68];
+  __shared__ float Bs[16][68];
+  __shared__ float red[32];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  const bool a_kc = pr.sa1 == 1;  // A contiguous along k
+  const bool b_kc = pr.sb1 == 1;
+  for (int k0 = 0; k0 < pr.K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int i, k;
+      if (a_kc) { i = e >> 4; k = e & 15; } else { i = e & 63; k = e >> 6; }
+      const int gi = m0 + i, gk = k0 + k;
+      As[k][i] = (gi < pr.a_rows && gk < pr.K) ? pr.A[gi * pr.sa0 + gk * pr.sa1] : 0.f;
+      int j, kk;
+      if (b_kc) { j = e >> 4; kk = e & 15; } else { j = e & 63; kk = e >> 6; }
+      const int gj = n0 + j, gkk = k0 + kk;
+      Bs[kk][j] = (gj < pr.b_rows && gkk < pr.K) ? pr.B[gj * pr.sb0 + gkk * pr.sb1] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[k][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[k][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  float ss = 0.f, tr = 0.f;
+  const int m = pr.mat;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = m0 + ty * 4 + a, j = n0 + tx * 4 + b;
+      if (i >= pr.M || j >= pr.N) continue;
+      float v = acc[a][b];
+      if constexpr (EPI == EPI_GRAM) {
+        pr.pacc[i * pr.ld_aux + j] = v;
+        ss = fmaf(v, v, ss);
+        if (i == j) tr += v;
+      } else if constexpr (EPI == EPI_SQR) {
+        const int64_t o = i * pr.ld_aux + j;
+        const float dn = 2.0f * pr.aux0[o] - v;
+        const float w = static_cast<float>(coef_at(p.coef, m, p.coef_l));
+        pr.pacc[o] = fmaf(-w, dn, pr.pacc[o]);
+        if (!p.final_pass) pr.out0[i * pr.ld_out + j] = dn;
+      } else if constexpr (EPI == EPI_APPLY || EPI == EPI_NS_APPLY) {
+        const int oi = pr.out_trans ? j : i, oj = pr.out_trans ? i : j;
+        if (oi >= pr.rows_out || oj >= pr.cols_out) continue;
+        float r;
+        if constexpr (EPI == EPI_APPLY) {
+          r = v * p.scal[m].inv_s;
+        } else {
+          const float sc = p.ns_step == 0 ? p.scal[m].inv_s : 1.0f;
+          const float x = pr.aux0[oi * pr.ld_aux + oj];
+          r = fmaf(p.ns_a * sc, x, p.ns_bcoef * sc * v);
+        }
+        pr.out0[oi * pr.ld_out + oj] = r;
+      } else if constexpr (EPI == EPI_NS_GRAM) {
+        const float s2 = p.ns_step == 0 ? p.scal[m].inv_s2 : 1.0f;
+        pr.out0[i * pr.ld_out + j] = v * s2;
+      } else if constexpr (EPI == EPI_NS_SQR) {
+        const float sv = pr.aux0[i * pr.ld_aux + j];
+        pr.out0[i * pr.ld_out + j] = fmaf(p.ns_c, v, p.ns_b * sv);
+      }
+    }
+  }
+  if constexpr (EPI == EPI_GRAM) {
+    const float s = block_sum(ss, red);
+    const float t = block_sum(tr, red);
+    if (threadIdx.x == 0) {
+      atomicAdd(&p.scal[m].o2, static_cast<double>(s));
+      if (t != 0.f) atomicAdd(&p.scal[m].trace, static_cast<double>(t));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,
+                         int64_t out_stride, int grid_x, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  dim3 grid(grid_x, count);
+  k_norm2<<<grid, 256, 0, s>>>(d_mats, bf16, out, out_stride);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalars(const MatInfo*, int count, MatScalars* scal, CoefTable coef, int L,
+                           int scale_frob, int, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_scalars<<<(count + 127) / 128, 128, 0, s>>>(count, scal, coef, L, scale_frob);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
+                        CoefTable coef, int L, int split, int f32, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const int64_t n = static_cast<int64_t>(hpad_max) * hpad_max;
+  int gx = static_cast<int>((n + 256 * 8 - 1) / (256 * 8));
+  if (gx > 4096) gx = 4096;
+  dim3 grid(gx, count);
+  k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t sg_launch(int epi, const SgParams& p, int count, int max_m, int max_n, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  dim3 grid((max_n + 63) / 64, (max_m + 63) / 64, count);
+  switch (epi) {
+    case EPI_GRAM: k_sgemm<EPI_GRAM><<<grid, 256, 0, s>>>(p); break;
+    case EPI_SQR: k_sgemm<EPI_SQR><<<grid, 256, 0, s>>>(p); break;
+    case EPI_APPLY: k_sgemm<EPI_APPLY><<<grid, 256, 0, s>>>(p); break;
+    case EPI_NS_GRAM: k_sgemm<EPI_NS_GRAM><<<grid, 256, 0, s>>>(p); break;
+    case EPI_NS_SQR: k_sgemm<EPI_NS_SQR><<<grid, 256, 0, s>>>(p); break;
+    case EPI_NS_APPLY: k_sgemm<EPI_NS_APPLY><<<grid, 256, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ifnso

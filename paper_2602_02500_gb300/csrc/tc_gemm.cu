@@ -1,0 +1,577 @@
+// Persistent, grouped tcgen05 GEMM for the IFNSO passes and the Newton-Schulz
+// baseline (sm_103a).
+//
+// One launch runs one pass of Algorithm 1 (Sec. 2.4) for every matrix of a
+// batch: the Gram product T_0 = A A^T, one squaring T_{l+1} = T_l^2 (in the
+// D basis, D_{l+1} = 2 D_l - D_l^2), or the final product Y = Y' A / sqrt(o).
+// Each CTA (one per SM) walks a static list of 128 x 256 output tiles.
+//
+// Warp roles (192 threads):
+//   warp 0      TMA producer: K blocks of 64 of every operand source into a
+//               ring of shared-memory stages (128-byte swizzle).
+//   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
+//               and MMA issuer: tcgen05.mma M=128, N=256, K=16, kind::f16.
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, fused elementwise
+//               math of the pass, stores to global memory.
+// The two accumulators let the epilogue of tile t overlap the main loop of
+// tile t + 1.  Symmetric outputs (T_0, D_l, P) are computed on the upper
+// 256 x 256 blocks only and stored twice (direct and mirrored).
+//
+// Every wait is bounded (ptx.cuh): on a timeout the CTA raises a shared
+// abort flag, records IFNSO_DEV_TIMEOUT in the matrix status word, lets its
+// outstanding TMA copies and MMAs land, frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace ifnso {
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr uint32_t kTileA = BM * BK * 2;  // 16 KB: 128 rows x 64 K of 16-bit values
+constexpr uint32_t kTileB = BN * BK * 2;  // 32 KB: 256 rows x 64 K
+constexpr uint32_t kTmemCols = 512;
+constexpr int kDevTimeout = 4;  // IFNSO_DEV_TIMEOUT
+
+template <int NA, int NB>
+struct Cfg {
+  static constexpr uint32_t stage_bytes = NA * kTileA + NB * kTileB;
+  static constexpr int stages_fit = static_cast<int>((200u * 1024u) / stage_bytes);
+  static constexpr int stages = stages_fit > 6 ? 6 : stages_fit;
+  // tiles + 1 KB alignment slack + barriers / flags
+  static constexpr uint32_t smem = stages * stage_bytes + 1024 + 256;
+};
+
+// Number of products per K step: every (A source, B source) pair except
+// (lo, lo): hi*hi + hi*lo + lo*hi for split operands.
+template <int NA, int NB>
+struct Products {
+  static constexpr int n = NA * NB - ((NA == 2 && NB == 2) ? 1 : 0);
+  __device__ static constexpr int a(int i) { return (NA == 2 && NB == 2) ? (i == 2 ? 1 : 0) : (NA == 2 ? i : 0); }
+  __device__ static constexpr int b(int i) { return (NA == 2 && NB == 2) ? (i == 1 ? 1 : 0) : (NB == 2 ? i : 0); }
+};
+
+__device__ __forceinline__ float u2f(uint32_t u) { return __uint_as_float(u); }
+
+__device__ __forceinline__ void set_timeout(MatScalars* scal, int mat) {
+  atomicOr(&scal[mat].status, kDevTimeout);
+}
+
+// ---------------------------------------------------------------- epilogues
+
+__device__ __forceinline__ void load_h32(const __half* src, float* d) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint4 u = s4[j];
+    const __half2* h2 = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float2 f = __half22float2(h2[t]);
+      d[8 * j + 2 * t] = f.x;
+      d[8 * j + 2 * t + 1] = f.y;
+    }
+  }
+}
+
+__device__ __forceinline__ void load_b32(const __nv_bfloat16* src, float* d) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint4 u = s4[j];
+    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float2 f = __bfloat1622float2(h2[t]);
+      d[8 * j + 2 * t] = f.x;
+      d[8 * j + 2 * t + 1] = f.y;
+    }
+  }
+}
+
+__device__ __forceinline__ void store_h32(__half* dst, const float* v) {
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint4 u;
+    __half2* h2 = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) h2[t] = __floats2half2_rn(v[8 * j + 2 * t], v[8 * j + 2 * t + 1]);
+    d4[j] = u;
+  }
+}
+
+__device__ __forceinline__ void store_b32(__nv_bfloat16* dst, const float* v) {
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    uint4 u;
+    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      h2[t] = __floats2bfloat162_rn(v[8 * j + 2 * t], v[8 * j + 2 * t + 1]);
+    d4[j] = u;
+  }
+}
+
+// Store a 32-wide row chunk of a symmetric result at (r, c0..c0+31) and,
+// for tiles off the diagonal blocks, at (c0..c0+31, r).
+template <typename T>
+__device__ __forceinline__ void store_sym(T* buf, int64_t ld, int r, int c0, const float* v,
+                                          bool mirror);
+
+template <>
+__device__ __forceinline__ void store_sym<float>(float* buf, int64_t ld, int r, int c0,
+                                                 const float* v, bool mirror) {
+  float4* d4 = reinterpret_cast<float4*>(buf + static_cast<int64_t>(r) * ld + c0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  if (mirror) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) buf[static_cast<int64_t>(c0 + j) * ld + r] = v[j];
+  }
+}
+
+template <>
+__device__ __forceinline__ void store_sym<__half>(__half* buf, int64_t ld, int r, int c0,
+                                                  const float* v, bool mirror) {
+  store_h32(buf + static_cast<int64_t>(r) * ld + c0, v);
+  if (mirror) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) buf[static_cast<int64_t>(c0 + j) * ld + r] = __float2half_rn(v[j]);
+  }
+}
+
+template <>
+__device__ __forceinline__ void store_sym<__nv_bfloat16>(__nv_bfloat16* buf, int64_t ld, int r,
+                                                         int c0, const float* v, bool mirror) {
+  store_b32(buf + static_cast<int64_t>(r) * ld + c0, v);
+  if (mirror) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      buf[static_cast<int64_t>(c0 + j) * ld + r] = __float2bfloat16_rn(v[j]);
+  }
+}
+
+// Bounds-checked BF16 store of a 32-wide chunk of an output tile.
+__device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r, int c0, const float* v) {
+  __nv_bfloat16* out = static_cast<__nv_bfloat16*>(pr.out0);
+  if (!pr.out_trans) {
+    if (r >= pr.rows_out) return;
+    __nv_bfloat16* o = out + static_cast<int64_t>(r) * pr.ld_out + c0;
+    if (c0 + 32 <= pr.cols_out && (pr.ld_out & 7) == 0) {
+      store_b32(o, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < pr.cols_out) o[j] = __float2bfloat16_rn(v[j]);
+    }
+  } else {
+    if (r >= pr.cols_out) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (c0 + j < pr.rows_out)
+        out[static_cast<int64_t>(c0 + j) * pr.ld_out + r] = __float2bfloat16_rn(v[j]);
+  }
+}
+
+// Load the 32 values of the NS iterate X at the positions a chunk of the
+// output tile is written to (same layout rules as store_out_bf16).
+__device__ __forceinline__ void load_x_bf16(const TcProblem& pr, int r, int c0, float* x) {
+  const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(pr.aux0);
+  if (!pr.out_trans) {
+    if (r >= pr.rows_out) return;
+    const __nv_bfloat16* s = X + static_cast<int64_t>(r) * pr.ld_aux + c0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = (c0 + j < pr.cols_out) ? __bfloat162float(s[j]) : 0.f;
+  } else {
+    if (r >= pr.cols_out) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      x[j] = (c0 + j < pr.rows_out)
+                 ? __bfloat162float(X[static_cast<int64_t>(c0 + j) * pr.ld_aux + r])
+                 : 0.f;
+  }
+}
+
+struct EpiAcc {
+  float ss;  // sum of squares (EPI_GRAM)
+  float tr;  // trace contribution (EPI_GRAM)
+};
+
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProblem& pr,
+                                               const WorkItem& wi, int r, int c0, float* v,
+                                               EpiAcc& ea) {
+  const bool mirror = (wi.flags & 1) == 0;
+  if constexpr (EPI == EPI_GRAM) {
+    store_sym<float>(pr.pacc, pr.ld_aux, r, c0, v, mirror);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      ea.ss = fmaf(v[j], v[j], ea.ss);
+      if (c0 + j == r) ea.tr += v[j];
+    }
+  } else if constexpr (EPI == EPI_SQR) {
+    float d[32], lo[32];
+    const int64_t off = static_cast<int64_t>(r) * pr.ld_aux + c0;
+    load_h32(static_cast<const __half*>(pr.aux0) + off, d);
+    if (pr.aux1) {
+      load_h32(static_cast<const __half*>(pr.aux1) + off, lo);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) d[j] += lo[j];
+    }
+    const float w = static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l));
+    float* P = pr.pacc + off;
+    float pv[32];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float4 t = reinterpret_cast<const float4*>(P)[j];
+      pv[4 * j] = t.x;
+      pv[4 * j + 1] = t.y;
+      pv[4 * j + 2] = t.z;
+      pv[4 * j + 3] = t.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float dn = 2.0f * d[j] - v[j];  // D_{l+1} = 2 D_l - D_l^2
+      v[j] = dn;
+      pv[j] = fmaf(-w, dn, pv[j]);          // P -= w_{l+1} D_{l+1}
+    }
+    if (!p.final_pass) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        reinterpret_cast<float4*>(P)[j] =
+            make_float4(pv[4 * j], pv[4 * j + 1], pv[4 * j + 2], pv[4 * j + 3]);
+      if (pr.out1) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float hi = __half2float(__float2half_rn(v[j]));
+          lo[j] = v[j] - hi;
+          v[j] = hi;
+        }
+        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+        store_sym<__half>(static_cast<__half*>(pr.out1), pr.ld_out, r, c0, lo, mirror);
+      } else {
+        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+      }
+    } else {
+      if (pr.out1) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float hi = __bfloat162float(__float2bfloat16_rn(pv[j]));
+          lo[j] = pv[j] - hi;
+          pv[j] = hi;
+        }
+        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror);
+        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out1), pr.ld_out, r, c0, lo, mirror);
+      } else {
+        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror);
+      }
+    }
+  } else if constexpr (EPI == EPI_APPLY) {
+    const float s = p.scal[pr.mat].inv_s;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] *= s;
+    store_out_bf16(pr, r, c0, v);
+  } else if constexpr (EPI == EPI_NS_GRAM) {
+    const float s2 = p.ns_step == 0 ? p.scal[pr.mat].inv_s2 : 1.0f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] *= s2;
+    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+  } else if constexpr (EPI == EPI_NS_SQR) {
+    float s[32];
+    load_b32(static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r) * pr.ld_aux + c0, s);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = fmaf(p.ns_c, v[j], p.ns_b * s[j]);
+    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+  } else if constexpr (EPI == EPI_NS_APPLY) {
+    const float sc = p.ns_step == 0 ? p.scal[pr.mat].inv_s : 1.0f;
+    float x[32];
+    load_x_bf16(pr, r, c0, x);
+    const float ka = p.ns_a * sc, kb = p.ns_bcoef * sc;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = fmaf(ka, x[j], kb * v[j]);
+    store_out_bf16(pr, r, c0, v);
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int NA, int NB, int EPI>
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+  using C = Cfg<NA, NB>;
+  using PR = Products<NA, NB>;
+  constexpr int S = C::stages;
+  constexpr uint32_t kIsBf16 = (EPI == EPI_SQR) ? 0u : 1u;  // D_l are FP16, all else BF16
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base_ptr + S * C::stage_bytes);
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * S + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 128);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t filled[6] = {0, 0, 0, 0, 0, 0};
+      int cur_mat = 0;
+      int last_prob = -1;
+      bool ok = true;
+      for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+        const WorkItem wi = p.items[it];
+        const TcProblem& pr = p.probs[wi.prob];
+        cur_mat = pr.mat;
+        if (wi.prob != last_prob) {
+          last_prob = wi.prob;
+#pragma unroll
+          for (int a = 0; a < NA; ++a) tmap_acquire(&pr.mapA[a]);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) tmap_acquire(&pr.mapB[b]);
+        }
+        const int a_mn = pr.a_mn, b_mn = pr.b_mn;
+        const int n_kb = pr.n_kb;
+        for (int kb = 0; kb < n_kb; ++kb) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full_bar(stage);
+          mbar_arrive_expect_tx(fb, C::stage_bytes);
+          const uint32_t st = base + stage * C::stage_bytes;
+          const int k0 = kb * BK;
+#pragma unroll
+          for (int a = 0; a < NA; ++a) {
+            const uint32_t dst = st + a * kTileA;
+            const void* m = &pr.mapA[a];
+            if (!a_mn) {
+              tma_load_2d(dst, m, fb, k0, wi.tm * BM);
+            } else {
+              tma_load_2d(dst, m, fb, wi.tm * BM, k0);
+              tma_load_2d(dst + 8192, m, fb, wi.tm * BM + 64, k0);
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const uint32_t dst = st + NA * kTileA + b * kTileB;
+            const void* m = &pr.mapB[b];
+            if (!b_mn) {
+              tma_load_2d(dst, m, fb, k0, wi.tn * BN);
+              tma_load_2d(dst + 16384, m, fb, k0, wi.tn * BN + 128);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) tma_load_2d(dst + 8192 * j, m, fb, wi.tn * BN + 64 * j, k0);
+            }
+          }
+          ++filled[stage];
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        set_timeout(p.scal, cur_mat);
+        // let the copies already issued land before the CTA exits
+        for (int s = 0; s < S; ++s)
+          if (filled[s]) mbar_wait_bounded(full_bar(s), (filled[s] - 1u) & 1u);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int local = 0;
+      int cur_mat = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x, ++local) {
+        const WorkItem wi = p.items[it];
+        const TcProblem& pr = p.probs[wi.prob];
+        cur_mat = pr.mat;
+        const int acc = local & 1;
+        const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
+        if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+        const uint32_t a_mn = static_cast<uint32_t>(pr.a_mn), b_mn = static_cast<uint32_t>(pr.b_mn);
+        const uint32_t idesc = idesc_f16(kIsBf16, BM, BN, a_mn, b_mn);
+        const int n_kb = pr.n_kb;
+        for (int kb = 0; kb < n_kb; ++kb) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + stage * C::stage_bytes;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+#pragma unroll
+            for (int q = 0; q < PR::n; ++q) {
+              const uint32_t sa = st + PR::a(q) * kTileA;
+              const uint32_t sb = st + NA * kTileA + PR::b(q) * kTileB;
+              const uint64_t ad = a_mn ? sdesc_sw128(sa + k * 2048, 8192, 1024)
+                                       : sdesc_sw128(sa + k * 32, 16, 1024);
+              const uint64_t bd = b_mn ? sdesc_sw128(sb + k * 2048, 8192, 1024)
+                                       : sdesc_sw128(sb + k * 32, 16, 1024);
+              umma_f16(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
+            }
+          }
+          umma_commit(empty_bar(stage));  // frees the stage once these MMAs have read it
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(tfull_bar(acc));  // accumulator ready for the epilogue
+      }
+      if (!ok) set_timeout(p.scal, cur_mat);
+      // make sure no MMA is still writing TMEM or reading shared memory
+      umma_commit(drain_bar);
+      mbar_wait_bounded(drain_bar, 0);
+    }
+  } else {
+    // -------------------------------------------------- epilogue (warps 2..5)
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row_in_tile = q * 32 + lane;
+    int local = 0;
+    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x, ++local) {
+      const WorkItem wi = p.items[it];
+      const TcProblem& pr = p.probs[wi.prob];
+      const int acc = local & 1;
+      const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
+      // one lane waits, the warp follows its verdict (tcgen05.ld needs a converged warp)
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait(tfull_bar(acc), acc_phase, abort_flag) ? 1 : 0;
+      ready = __shfl_sync(0xffffffffu, ready, 0);
+      if (!ready) {
+        if (lane == 0) set_timeout(p.scal, pr.mat);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN);
+      const int r = wi.tm * BM + row_in_tile;
+      EpiAcc ea{0.f, 0.f};
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t u[32];
+        IFNSO_TMEM_LD32(tbase + static_cast<uint32_t>(ch * 32), u);
+        IFNSO_TMEM_WAIT_LD(u);
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = u2f(u[j]);
+        epilogue_chunk<EPI>(p, pr, wi, r, wi.tn * BN + ch * 32, v, ea);
+      }
+      tc_fence_before();
+      mbar_arrive(tempty_bar(acc));
+      if constexpr (EPI == EPI_GRAM) {
+        float ss = ea.ss, tr = ea.tr;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        }
+        if (lane == 0) {
+          const double wgt = (wi.flags & 1) ? 1.0 : 2.0;  // off-diagonal blocks stand for two
+          atomicAdd(&p.scal[pr.mat].o2, wgt * static_cast<double>(ss));
+          if (tr != 0.f) atomicAdd(&p.scal[pr.mat].trace, static_cast<double>(tr));
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, kTmemCols);
+  }
+}
+
+template <int NA, int NB, int EPI>
+cudaError_t launch_one(const TcParams& p, int grid, cudaStream_t s) {
+  using C = Cfg<NA, NB>;
+  auto kern = tc_gemm_kernel<NA, NB, EPI>;
+  static bool attr_done = false;  // set once per process (per instantiation)
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  kern<<<grid, kThreads, C::smem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_smem_bytes(int na, int nb) {
+  if (na == 1 && nb == 1) return Cfg<1, 1>::smem;
+  if (na == 2 && nb == 2) return Cfg<2, 2>::smem;
+  if (na == 2 && nb == 1) return Cfg<2, 1>::smem;
+  return -1;
+}
+
+cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int grid, cudaStream_t s) {
+  if (p.n_items == 0) return cudaSuccess;
+  switch (epi) {
+    case EPI_GRAM:
+      return launch_one<1, 1, EPI_GRAM>(p, grid, s);
+    case EPI_SQR:
+      if (na == 2) return launch_one<2, 2, EPI_SQR>(p, grid, s);
+      return launch_one<1, 1, EPI_SQR>(p, grid, s);
+    case EPI_APPLY:
+      if (na == 2) return launch_one<2, 1, EPI_APPLY>(p, grid, s);
+      return launch_one<1, 1, EPI_APPLY>(p, grid, s);
+    case EPI_NS_GRAM:
+      return launch_one<1, 1, EPI_NS_GRAM>(p, grid, s);
+    case EPI_NS_SQR:
+      return launch_one<1, 1, EPI_NS_SQR>(p, grid, s);
+    case EPI_NS_APPLY:
+      return launch_one<1, 1, EPI_NS_APPLY>(p, grid, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ifnso

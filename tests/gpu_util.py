@@ -1,0 +1,44 @@
+"""Helpers shared by the GPU parity tests: inputs from synth/, expected values
+from oracle/, the device path through the C ABI binding."""
+import json
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+_COEFFS = None
+
+
+def coeffs(L):
+    """w_1..w_L of the committed oracle-learned artefact."""
+    global _COEFFS
+    if _COEFFS is None:
+        with open(os.path.join(GOLDEN, "ifnso_coeffs.json")) as f:
+            _COEFFS = json.load(f)
+    return np.array(_COEFFS["L"][str(L)]["w"])
+
+
+def lib():
+    from paper_2602_02500_gb300 import _build
+
+    _build.build()
+    from paper_2602_02500_gb300 import ifnso
+
+    return ifnso
+
+
+def to_dev(M, dtype):
+    import torch
+
+    t = torch.tensor(np.asarray(M, dtype=np.float32), device="cuda")
+    return t.to(torch.bfloat16) if dtype == "bf16" else t
+
+
+def to_np(t):
+    return t.float().double().cpu().numpy()
+
+
+def rel(a, b):
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(np.linalg.norm(b), 1e-300))

@@ -1,0 +1,99 @@
+"""The C-ABI library loads and exports every entry point include/ifnso.h
+declares; host-side validation and workspace sizing (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_2602_02500_gb300 import _build
+
+    _build.build()
+    from paper_2602_02500_gb300 import ifnso
+
+    return ifnso
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "ifnso.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(F):
+    names = header_functions()
+    assert "ifnso_orthogonalize" in names and "ns_iterate" in names and "ifnso_plan_create" in names
+    lib = C.CDLL(F._LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(F.EXPORTED)
+
+
+def _plan(F, h, w, L, dtype=1):
+    K = L + 1
+    ex = (C.c_int32 * K)(*([0] + [1 << (l - 1) for l in range(1, K)]))
+    p = C.c_void_p()
+    st = F.ifnso_plan_create(C.byref(p), h, w, dtype, ex, K)
+    return st, p
+
+
+def test_plan_validation(F):
+    st, p = _plan(F, 128, 256, 4)
+    assert st == F.IFNSO_OK
+    F.ifnso_plan_destroy(p)
+    # exponents must be 0, 1, 2, 4, ... (repeated squaring)
+    ex = (C.c_int32 * 4)(0, 1, 3, 4)
+    q = C.c_void_p()
+    assert F.ifnso_plan_create(C.byref(q), 128, 256, 1, ex, 4) == F.IFNSO_ERR_INVALID_ARG
+    assert b"repeated squaring" in F.ifnso_last_error()
+    assert F.ifnso_plan_create(C.byref(q), 300, 256, 1, (C.c_int32 * 2)(0, 1), 2) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_plan_create(C.byref(q), 8, 8, 1, (C.c_int32 * 1)(0), 1) == F.IFNSO_ERR_INVALID_ARG
+
+
+def _fake_batch(F, shapes, ld=None, base=1 << 30):
+    n = len(shapes)
+    ptrs = (C.c_void_p * n)(*[base + (i << 24) for i in range(n)])
+    rows = (C.c_int64 * n)(*[s[0] for s in shapes])
+    cols = (C.c_int64 * n)(*[s[1] for s in shapes])
+    lds = (C.c_int64 * n)(*(ld or [s[1] for s in shapes]))
+    d = F.ifnso_batch_desc(n, ptrs, rows, cols, lds)
+    return d, (ptrs, rows, cols, lds)
+
+
+def test_workspace_sizes(F):
+    st, p = _plan(F, 2048, 5632, 14)
+    d, keep = _fake_batch(F, [(2048, 2048), (2048, 5632), (5632, 2048)])
+    split = F.ifnso_workspace_bytes(p, C.byref(d))
+    F.ifnso_plan_set(p, F.IFNSO_OPT_PRECISION, F.IFNSO_PREC_PLAIN)
+    plain = F.ifnso_workspace_bytes(p, C.byref(d))
+    hp2 = 2048 * 2048
+    assert 3 * 12 * hp2 <= split < 3 * 12 * hp2 + (4 << 20)
+    assert 3 * 8 * hp2 <= plain < 3 * 8 * hp2 + (4 << 20)
+    v = C.c_int64()
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_PRECISION, C.byref(v)) == 0 and v.value == F.IFNSO_PREC_PLAIN
+    F.ifnso_plan_destroy(p)
+
+
+def test_batch_validation(F):
+    st, p = _plan(F, 256, 512, 4)
+    d, keep = _fake_batch(F, [(256, 500)], ld=[500])   # BF16 ld must be a multiple of 8
+    assert F.ifnso_workspace_bytes(p, C.byref(d)) == 0
+    assert b"multiple of 8" in F.ifnso_last_error()
+    d, keep = _fake_batch(F, [(300, 512)])               # oriented 300 x 512 exceeds 256 x 512
+    assert F.ifnso_workspace_bytes(p, C.byref(d)) == 0
+    d, keep = _fake_batch(F, [(512, 200)])               # tall: oriented 200 x 512 fits
+    assert F.ifnso_workspace_bytes(p, C.byref(d)) > 0
+    d, keep = _fake_batch(F, [(0, 5)])
+    assert F.ifnso_workspace_bytes(p, C.byref(d)) == 0
+    F.ifnso_plan_destroy(p)
+
+
+def test_learn_argument_checks(F):
+    w = (C.c_double * 4)()
+    assert F.ifnso_learn_coefficients(0, 10, 100, 0.1, 10, 0.5, 0, w) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_learn_coefficients(4, 10, 5000, 0.1, 10, 0.5, 0, w) == F.IFNSO_ERR_INVALID_ARG

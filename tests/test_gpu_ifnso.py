@@ -1,0 +1,157 @@
+"""GPU parity of the hot path through the C ABI against the FP64 oracle.
+
+Tolerances (relative Frobenius error against Algorithm 1 evaluated in FP64 on
+the same, already rounded input): 1e-5 for FP32 plans, 2e-2 for BF16 plans.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ifnso as O
+from oracle import ns as ONS
+from tests.gpu_util import coeffs, lib, rel, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "bf16": 2e-2}
+
+
+def run_ifnso(mats, L, dtype, precision=None, scale=None, stop_after=None, plan_shape=None):
+    import torch
+
+    F = lib()
+    xs = [to_dev(m, dtype) for m in mats]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    hmax = max(min(x.shape) for x in xs)
+    wmax = max(max(x.shape) for x in xs)
+    plan = F.Plan(*(plan_shape or (hmax, wmax)), dtype, L=L, precision=precision, scale=scale)
+    if stop_after is not None:
+        plan.set(F.IFNSO_OPT_STOP_AFTER, stop_after)
+    b = F.Batch(xs)
+    w = coeffs(L)
+    plan.orthogonalize(b, np.r_[1.0, w], ys)
+    torch.cuda.synchronize()
+    return F, plan, b, xs, ys, w
+
+
+# --------------------------------------------------------------- FP32 path
+@pytest.mark.parametrize("shape", [(256, 512), (512, 256), (100, 300), (64, 64), (1, 40)])
+def test_f32_ifnso(shape):
+    M = synth.gaussian(0, *shape)
+    F, plan, b, xs, ys, w = run_ifnso([M], 4, "f32")
+    ref = O.ifnso_alg1(to_np(xs[0]), w)
+    assert rel(to_np(ys[0]), ref) < TOL["f32"]
+    st, s2, tr = plan.device_status(1)
+    assert st[0] == 0
+    A = to_np(xs[0])
+    assert abs(tr[0] - np.sum(A * A)) / np.sum(A * A) < 1e-6
+
+
+@pytest.mark.parametrize("scale", ["gram", "frob"])
+def test_f32_scale_modes(scale):
+    M = synth.gaussian(5, 96, 200)
+    F, plan, b, xs, ys, w = run_ifnso([M], 6, "f32", scale=scale)
+    assert rel(to_np(ys[0]), O.ifnso_alg1(to_np(xs[0]), w, scale)) < TOL["f32"]
+
+
+@pytest.mark.parametrize("shape", [(256, 512), (300, 180)])
+def test_f32_ns(shape):
+    import torch
+
+    F = lib()
+    M = synth.gaussian(1, *shape)
+    x = to_dev(M, "f32")
+    for poly, steps in [(ONS.MUON_ABC, 5), (ONS.CUBIC, 8)]:
+        y = torch.empty_like(x)
+        plan = F.Plan(min(shape), max(shape), "f32", L=1)
+        plan.ns_iterate(F.Batch([x]), poly, steps, [y])
+        torch.cuda.synchronize()
+        ref = ONS.ns_generic(to_np(x), poly, steps)
+        assert rel(to_np(y), ref) < TOL["f32"]
+
+
+# --------------------------------------------------------------- BF16 tcgen05 path
+@pytest.mark.parametrize("shape", [(256, 512), (200, 328), (392, 136), (512, 512), (640, 1000)])
+def test_bf16_gram(shape):
+    """The symmetric tcgen05 Gram: T_0 = A A^T in FP32, sum T_0^2 and tr T_0."""
+    import torch
+
+    M = synth.gaussian(2, *shape)
+    F, plan, b, xs, ys, w = run_ifnso([M], 4, "bf16", stop_after=0)
+    ptr, ld = plan.workspace_view(b, 0, 0)
+    G = F.tensor_at(ptr, (ld, ld), torch.float32, plan._last_ws.buf).double().cpu().numpy()
+    A = O.orient(to_np(xs[0]))[0]
+    h = A.shape[0]
+    ref = A @ A.T
+    assert rel(G[:h, :h], ref) < 1e-5
+    assert np.all(G[h:, :] == 0) and np.all(G[:, h:] == 0)
+    st, s2, tr = plan.device_status(1)
+    assert abs(s2[0] - np.linalg.norm(ref)) / np.linalg.norm(ref) < 1e-5
+    assert abs(tr[0] - np.trace(ref)) / np.trace(ref) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["plain", "split"])
+def test_bf16_prep(precision):
+    import torch
+
+    M = synth.gaussian(3, 300, 700)
+    F, plan, b, xs, ys, w = run_ifnso([M], 4, "bf16", precision=precision, stop_after=1)
+    ptr, ld = plan.workspace_view(b, 0, 1)
+    D = F.tensor_at(ptr, (ld, ld), torch.float16, plan._last_ws.buf).double().cpu().numpy()
+    if precision == "split":
+        ptr2, _ = plan.workspace_view(b, 0, 2)
+        D = D + F.tensor_at(ptr2, (ld, ld), torch.float16, plan._last_ws.buf).double().cpu().numpy()
+    A = to_np(xs[0])
+    G = A @ A.T
+    ref = G / np.linalg.norm(G)
+    tol = 2e-6 if precision == "split" else 1e-3
+    assert rel(D[:300, :300], ref) < tol
+
+
+@pytest.mark.parametrize("L,precision", [(4, "plain"), (4, "split"), (14, "split"), (9, "plain")])
+@pytest.mark.parametrize("shape", [(256, 512), (200, 328), (392, 136), (512, 512), (640, 1000)])
+def test_bf16_ifnso(shape, L, precision):
+    M = synth.gaussian(4, *shape)
+    F, plan, b, xs, ys, w = run_ifnso([M], L, "bf16", precision=precision)
+    A = to_np(xs[0])
+    ref = O.ifnso_alg1(A, w)
+    err = rel(to_np(ys[0]), ref)
+    assert err < TOL["bf16"], err
+
+
+def test_bf16_batch_heterogeneous():
+    shapes = [(256, 512), (392, 136), (200, 328), (512, 512), (130, 260), (1, 64)]
+    mats = [synth.gaussian(10 + i, *s) for i, s in enumerate(shapes)]
+    F, plan, b, xs, ys, w = run_ifnso(mats, 6, "bf16")
+    for x, y in zip(xs, ys):
+        assert rel(to_np(y), O.ifnso_alg1(to_np(x), w)) < TOL["bf16"]
+
+
+def test_bf16_zero_and_scale_invariance():
+    import torch
+
+    Z = np.zeros((128, 256))
+    M = synth.gaussian(6, 128, 256)
+    F, plan, b, xs, ys, w = run_ifnso([Z, M, 1000.0 * M], 4, "bf16")
+    assert torch.all(ys[0] == 0)
+    st, s2, tr = plan.device_status(3)
+    assert st[0] & F.IFNSO_DEV_ZERO_INPUT and st[1] == 0 and st[2] == 0
+    # the output does not depend on the scale of the input (up to BF16 rounding of 1000 M)
+    assert rel(to_np(ys[2]), O.ifnso_alg1(to_np(xs[2]), w)) < TOL["bf16"]
+
+
+@pytest.mark.parametrize("shape", [(256, 512), (392, 136)])
+def test_bf16_ns(shape):
+    import torch
+
+    F = lib()
+    M = synth.gaussian(7, *shape)
+    x = to_dev(M, "bf16")
+    for poly, steps in [(ONS.MUON_ABC, 5), (ONS.CUBIC, 8)]:
+        y = torch.empty_like(x)
+        plan = F.Plan(min(shape), max(shape), "bf16", L=1)
+        plan.ns_iterate(F.Batch([x]), poly, steps, [y])
+        torch.cuda.synchronize()
+        ref = ONS.ns_generic(to_np(x), poly, steps)
+        # BF16 storage of X, X X^T and B every step: 5e-2 relative
+        assert rel(to_np(y), ref) < 5e-2
