@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Throughput of IFNSO on GB300: orthogonalized matrices/s (and TFLOP/s) of one
+batched Muon step, next to a 5-step quintic Newton-Schulz on the same GPU.
+
+Default workload (one step = one pass of the whole hot path over the list):
+the weight-gradient list of a synthetic 1B-parameter transformer,
+24 layers x {Q, K, V, O 2048x2048; gate, up 2048x5632; down 5632x2048},
+168 BF16 matrices of rank-32 signal plus noise (10:1), seeds 0..167, at
+L = 14 (the depth whose distance to U V^T matches the 5-step quintic NS on
+these matrices).  Inputs (2.47 GB) are larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded
+sample of the same workload per step).  Under torchrun every rank runs its
+own copy of the list (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orthogonalized matrices/s & TFLOP/s vs 5-step NS at equal polar error, 1 GB300"
+MUON_ABC = (3.4445, -4.7750, 2.0315)
+
+WORKLOADS = {
+    "muon_1b": {
+        "desc": "synthetic 1B transformer weight-gradient list: 24 layers x {Q,K,V,O 2048x2048; gate, up "
+                "2048x5632; down 5632x2048}, 168 BF16 rank-32 + noise (10:1) matrices, seeds 0..167",
+        "list": "list_1b", "L": 14,
+    },
+    "muon_1b_4l": {
+        "desc": "first 4 layers of the synthetic 1B list (28 BF16 matrices, 412 MB of input > L2): the "
+                "small case used for ncu captures",
+        "list": "list_1b_4l", "L": 14,
+    },
+    "muon_7b": {
+        "desc": "synthetic 7B transformer weight-gradient list: 32 layers x {4 x 4096x4096; gate, up "
+                "4096x14336; down 14336x4096}, 224 BF16 rank-32 + noise (10:1) matrices, seeds 0..223",
+        "list": "list_7b", "L": 14,
+    },
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="muon_1b", choices=sorted(WORKLOADS))
+    ap.add_argument("--L", type=int, default=None)
+    ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def flops_ifnso(h, w, L):
+    """Matrix-product FLOPs of Algorithm 1: Gram 2h^2 w, (L - 1) squarings 2h^3, apply 2h^2 w."""
+    return 4 * h * h * w + 2 * (L - 1) * h ** 3
+
+
+def flops_ns5(h, w, steps=5):
+    return steps * (4 * h * h * w + 2 * h ** 3)
+
+
+def workload_list(wl):
+    import synth
+
+    if wl["list"] == "list_1b_4l":
+        return synth.transformer_list(4, 2048, 5632)
+    return getattr(synth, wl["list"])()
+
+
+def oriented(r, c):
+    return (min(r, c), max(r, c))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def load_traffic():
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(F, torch, shapes, seed0, device):
+    import synth
+
+    alpha, beta = synth.lowrank_constants()
+    xs = []
+    for i, (_, r, c) in enumerate(shapes):
+        x = torch.empty((r, c), dtype=torch.bfloat16, device=device)
+        F.synth_lowrank_bf16(x, seed0 + i, float(alpha), float(beta))
+        xs.append(x)
+    return xs
+
+
+def cpu_oracle_sample(shapes, L, budget_s=20.0):
+    """Time the FP64 oracle (Algorithm 1) on one matrix of each distinct shape;
+    project the time of the whole list.  Returns (matrices/s, sample text, cores)."""
+    import numpy as np
+
+    import synth
+    from oracle import coeffs as OC
+    from oracle import ifnso as O
+
+    w = OC.complete(np.zeros(L - 1), L)  # timing does not depend on the coefficient values
+    distinct = {}
+    for i, (nm, r, c) in enumerate(shapes):
+        distinct.setdefault((r, c), []).append(i)
+    per_shape = {}
+    t_used = 0.0
+    for (r, c), idx in distinct.items():
+        M = synth.bf16_bits_to_f64(synth.lowrank_noise_bf16(idx[0], r, c))
+        t0 = time.perf_counter()
+        O.ifnso_alg1(M, w)
+        dt = time.perf_counter() - t0
+        per_shape[(r, c)] = dt
+        t_used += dt
+        if t_used > budget_s:
+            break
+    total = 0.0
+    for (r, c), idx in distinct.items():
+        if (r, c) not in per_shape:
+            return None, "sample incomplete", os.cpu_count()
+        total += per_shape[(r, c)] * len(idx)
+    sample = ("FP64 oracle (Algorithm 1, numpy) on one matrix of each distinct shape "
+              + ", ".join(f"{r}x{c}: {t:.2f}s" for (r, c), t in per_shape.items())
+              + f"; list time projected over {len(shapes)} matrices")
+    return len(shapes) / total, sample, os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    from oracle import coeffs as OC
+    from oracle import ifnso as O
+    import numpy as np
+
+    wl = WORKLOADS[args.workload]
+    shapes = workload_list(wl)
+    L = args.L or wl["L"]
+    w = OC.complete(np.zeros(L - 1), L)
+    distinct = {}
+    for i, (nm, r, c) in enumerate(shapes):
+        distinct.setdefault((r, c), []).append(i)
+    keys = list(distinct)
+    mats = {k: synth.bf16_bits_to_f64(synth.lowrank_noise_bf16(distinct[k][0], *k)) for k in keys}
+    times = {k: [] for k in keys}
+    for s in range(args.warmup + args.steps):
+        k = keys[s % len(keys)]
+        t0 = time.perf_counter()
+        O.ifnso_alg1(mats[k], w)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times[k].append(dt)
+    for k in keys:
+        if not times[k]:
+            times[k] = [float("nan")]
+    list_time = sum(np.mean(times[k]) * len(distinct[k]) for k in keys)
+    value = len(shapes) / list_time
+    step_ms = 1000.0 * sum(sum(v) for v in times.values()) / max(1, args.steps)
+    sample = (f"each step: FP64 oracle (Algorithm 1, numpy) on one matrix, cycling through the distinct shapes "
+              + ", ".join(f"{r}x{c}" for r, c in keys) + f"; matrices/s projected to the {len(shapes)}-matrix list")
+    line = {
+        "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "L": L, "parallelism": "host cores"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2602_02500_gb300 import ifnso as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    wl = WORKLOADS[args.workload]
+    shapes = workload_list(wl)
+    L = args.L or wl["L"]
+    n = len(shapes)
+    hw = [oriented(r, c) for _, r, c in shapes]
+    hmax = max(h for h, _ in hw)
+    wmax = max(w for _, w in hw)
+    seed0 = rank * 100000
+    xs = make_inputs(F, torch, shapes, seed0, device)
+    ys = [torch.empty_like(x) for x in xs]
+    batch = F.Batch(xs)
+
+    # fixed coefficients from the library's own GPU learner (Sec. 2.3 / 3.1.1)
+    w_full = F.learn_coefficients(L)
+    coef = np.r_[1.0, w_full]
+
+    plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision)
+    plan.set(F.IFNSO_OPT_TIMING, 1)
+    ws = F.Workspace(plan.workspace_bytes(batch), device=device)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        plan.orthogonalize(batch, coef, ys, ws=ws)
+    torch.cuda.synchronize()
+    plan.pass_times()  # discard warm-up events
+    st, _, _ = plan.device_status(n, ws=ws)
+    if np.any(st & F.IFNSO_DEV_TIMEOUT):
+        raise RuntimeError("device wait timed out during warm-up")
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = F.launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.orthogonalize(batch, coef, ys, ws=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = F.launch_count() - n0
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    pass_ms, calls = plan.pass_times()
+    ms_step = ms_total / args.steps
+    value = world * n * args.steps / (ms_total / 1000.0)
+    fl = sum(flops_ifnso(h, w, L) for h, w in hw)
+    tflops = world * fl * args.steps / (ms_total / 1000.0) / 1e12
+
+    # the dominant kernel: the squaring pass (L - 1 launches per step)
+    peaks, peak_src = load_peaks()
+    sq = pass_ms[2:2 + (L - 1)] if L > 1 else np.array([])
+    sq_launch_ms = float(np.sum(sq)) / max(1, calls * (L - 1)) if L > 1 else None
+    sq_alg = sum(2 * h ** 3 for h, _ in hw)  # algorithmic FLOPs per squaring launch
+    split = plan.get(F.IFNSO_OPT_PRECISION) == F.IFNSO_PREC_SPLIT
+    hp = [((h + 255) // 256) * 256 for h, _ in hw]
+    sq_exec = sum(((p // 256) * (p // 256 + 1) // 2) * 2 * (2 * 128 * 256 * p) * (3 if split else 1) for p in hp)
+    traffic = load_traffic().get(f"{args.workload}:squaring")
+    roof = None
+    if sq_launch_ms:
+        ach = sq_alg / (sq_launch_ms / 1000.0) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic,
+                "kernel": "tc_gemm_kernel squaring pass (D_{l+1} = 2 D_l - D_l^2, P -= w D_{l+1})",
+                "launch_ms": sq_launch_ms, "algorithmic_flop_per_launch": sq_alg,
+                "executed_flop_per_launch": sq_exec,
+                "executed_tflops": sq_exec / (sq_launch_ms / 1000.0) / 1e12,
+                "peak_source": f"bf16_tflops_sustained ({peak_src})",
+                "pass_ms_per_step": [float(x) / max(1, calls) for x in pass_ms]}
+
+    # 5-step quintic Newton-Schulz on the same list
+    nsplan = F.Plan(hmax, wmax, "bf16", L=1)
+    nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
+    zs = [torch.empty_like(x) for x in xs]
+    for _ in range(max(args.warmup, 3)):
+        nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ns_ms = max_over_ranks(e0.elapsed_time(e1))
+    ns_value = world * n * args.steps / (ns_ms / 1000.0)
+    ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
+    del nsws, zs
+
+    # end to end through the C ABI with host buffers: H2D inputs, the call, D2H outputs
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+        hout = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+        for h_, x in zip(hin, xs):
+            h_.copy_(x)
+        bi = sum(x.numel() * x.element_size() for x in xs)
+
+        def e2e_step():
+            for h_, x in zip(hin, xs):
+                x.copy_(h_, non_blocking=True)
+            plan.orthogonalize(batch, coef, ys, ws=ws)
+            for h_, y in zip(hout, ys):
+                h_.copy_(y, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": world * n * args.steps / (e2e_ms / 1000.0), "unit": "matrices/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "ms_per_step": e2e_ms / args.steps}
+        plan.pass_times()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sample, cores = cpu_oracle_sample(shapes, L)
+        cpu = {"value": v, "unit": "matrices/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + wl["desc"], "L": L,
+                       "precision": "split fp16/bf16 hi+lo operands" if split else "plain",
+                       "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "coefficients": "learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 schedule)"},
+            "tflops": tflops,
+            "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
+                    "ifnso_over_ns5": value / ns_value},
+            "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -60,7 +60,11 @@ typedef enum {
   /* Testing aid: stop after this stage (0 = Gram only, 1 = Gram and the
    * D_1 / P initialisation, 2 + j = after squaring pass j+1).  -1 (default)
    * runs everything.  Intermediate buffers are read with ifnso_workspace_view(). */
-  IFNSO_OPT_STOP_AFTER = 4
+  IFNSO_OPT_STOP_AFTER = 4,
+  /* Measurement aid: when non-zero, every ifnso_orthogonalize / ns_iterate
+   * call records a CUDA event on its stream before its first launch and after
+   * each pass; ifnso_pass_times() returns the per-pass durations. */
+  IFNSO_OPT_TIMING = 5
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2 };
@@ -175,6 +179,17 @@ size_t ns_workspace_bytes(const ifnso_plan* plan, const ifnso_batch_desc* batch)
 ifnso_status ifnso_device_status(const ifnso_plan* plan, const void* workspace, int32_t count,
                                  int32_t* per_matrix, double* o_out, double* trace_out,
                                  ifnso_stream_t stream);
+
+/* Per-pass durations (milliseconds, summed over every call made since the
+ * last query with IFNSO_OPT_TIMING on) into ms_out[0..max_passes) (host);
+ * *n_passes (host) receives the number of passes of the last call and
+ * *n_calls (host, may be NULL) the number of calls summed.  Waits for the
+ * recorded events.  Pass order of ifnso_orthogonalize: 0 Gram (with the
+ * per-matrix scalars), 1 D_1 / P initialisation, 2 .. L squarings l = 1..L-1,
+ * L + 1 the final product.  ns_iterate: 0 norm and scalars, then per step
+ * Gram, squaring (degree 5 only), product. */
+ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_passes,
+                              int32_t* n_passes, int32_t* n_calls);
 
 /* Testing aid: device pointer and leading dimension (elements) of an h_pad x
  * h_pad intermediate of matrix `index` in a workspace used by

@@ -34,6 +34,10 @@ struct ifnso_plan {
   bool sig_valid = false;
   void* meta_host = nullptr;
   size_t meta_cap = 0;
+  // per-pass timing (IFNSO_OPT_TIMING): events of every call since the last query
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::vector<cudaEvent_t>> ev_calls;
   std::mutex mu;
 };
 
@@ -77,6 +81,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Record a timing event on `stream` if the plan times its passes.
+cudaError_t mark(ifnso_plan* plan, cudaStream_t stream, bool first) {
+  if (!plan->timing) return cudaSuccess;
+  if (first) plan->ev_calls.emplace_back();
+  cudaEvent_t e;
+  if (!plan->ev_pool.empty()) {
+    e = plan->ev_pool.back();
+    plan->ev_pool.pop_back();
+  } else {
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+  }
+  plan->ev_calls.back().push_back(e);
+  return cudaEventRecord(e, stream);
+}
 
 // 2D tiled tensor map, 128-byte swizzle, zero fill outside the tensor.
 // inner/outer: extents in elements, ld: row pitch in elements.
@@ -767,6 +787,9 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
     case IFNSO_OPT_STOP_AFTER:
       plan->stop_after = static_cast<int>(value);
       break;
+    case IFNSO_OPT_TIMING:
+      plan->timing = value != 0;
+      break;
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -783,12 +806,16 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_SCALE: *value = plan->scale; return IFNSO_OK;
     case IFNSO_OPT_MAX_CTAS: *value = plan->max_ctas; return IFNSO_OK;
     case IFNSO_OPT_STOP_AFTER: *value = plan->stop_after; return IFNSO_OK;
+    case IFNSO_OPT_TIMING: *value = plan->timing ? 1 : 0; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }
 
 ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
   if (!plan) return IFNSO_OK;
+  for (auto& c : plan->ev_calls)
+    for (cudaEvent_t e : c) cudaEventDestroy(e);
+  for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
   if (plan->meta_host) {
     cudaDeviceSynchronize();
     cudaFreeHost(plan->meta_host);
@@ -857,7 +884,7 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   int hpad_max = 0;
   for (auto& s : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(s.hpad));
   IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
-  count_launch();
+  IFNSO_CUDA(mark(plan, stream, true), "timing event");
   if (ly.f32) {
     SgParams p = base_params<SgParams>(ws, ly, coeffs);
     const SgProblem* probs = reinterpret_cast<const SgProblem*>(ws + ly.off_probs);
@@ -870,8 +897,10 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
     p.probs = probs + ly.pi_gram;
     IFNSO_CUDA(sg_launch(EPI_GRAM, p, n, hpad_max, hpad_max, stream), "FP32 Gram");
     IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (plan->stop_after == 0) return IFNSO_OK;
     IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, 0, 1, stream), "prep");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (plan->stop_after == 1) return IFNSO_OK;
     for (int j = 1; j <= L - 1; ++j) {
       const int par = (j - 1) % 2;
@@ -879,12 +908,14 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
       p.coef_l = j + 1;
       p.final_pass = (j == L - 1);
       IFNSO_CUDA(sg_launch(EPI_SQR, p, n, hpad_max, hpad_max, stream), "FP32 squaring");
+      IFNSO_CUDA(mark(plan, stream, false), "timing event");
       if (plan->stop_after == 1 + j) return IFNSO_OK;
     }
     p.probs = probs + ly.pi_apply;
     p.coef_l = 0;
     p.final_pass = 0;
     IFNSO_CUDA(sg_launch(EPI_APPLY, p, n, max_h, max_w, stream), "FP32 apply");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
     return IFNSO_OK;
   }
   TcParams p = base_params<TcParams>(ws, ly, coeffs);
@@ -897,8 +928,10 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   p.n_items = static_cast<int32_t>(ly.n_sym);
   IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "Gram pass");
   IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 0) return IFNSO_OK;
   IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, ly.split, 0, stream), "prep");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 1) return IFNSO_OK;
   for (int j = 1; j <= L - 1; ++j) {
     const int par = (j - 1) % 2;
@@ -908,6 +941,7 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
     p.coef_l = j + 1;
     p.final_pass = (j == L - 1);
     IFNSO_CUDA(tc_launch(EPI_SQR, nab, nab, p, grid_for(plan, ly.n_sym), stream), "squaring pass");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (plan->stop_after == 1 + j) return IFNSO_OK;
   }
   p.probs = probs + ly.pi_apply;
@@ -916,6 +950,7 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   p.coef_l = 0;
   p.final_pass = 0;
   IFNSO_CUDA(tc_launch(EPI_APPLY, nab, 1, p, grid_for(plan, ly.n_app), stream), "apply pass");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
   return IFNSO_OK;
 }
 
@@ -967,7 +1002,7 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
     max_w = std::max<int>(max_w, static_cast<int>(s.w));
   }
   IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
-  count_launch();
+  IFNSO_CUDA(mark(plan, stream, true), "timing event");
   // ||A||_F^2 into the trace slot, then the scalars with the Frobenius scale
   int gx = std::max(1, std::min(1024, 4 * plan->num_sms / std::max(1, n)));
   IFNSO_CUDA(launch_norm2(d_mats, n, plan->dtype == IFNSO_BF16, &scal[0].trace,
@@ -975,6 +1010,7 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
              "norm");
   CoefTable none{};
   IFNSO_CUDA(launch_scalars(d_mats, n, scal, none, 0, 1, 1, stream), "scalars");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
   const float a = static_cast<float>(poly[0]);
   const float b = static_cast<float>(poly[1]);
   const float c = degree == 5 ? static_cast<float>(poly[2]) : 0.f;
@@ -990,12 +1026,15 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
       p.ns_step = s;
       p.probs = probs + ly.pi_ns_gram + s * n;
       IFNSO_CUDA(sg_launch(EPI_NS_GRAM, p, n, hpad_max, hpad_max, stream), "NS Gram");
+      IFNSO_CUDA(mark(plan, stream, false), "timing event");
       if (degree == 5) {
         p.probs = probs + ly.pi_ns_sqr;
         IFNSO_CUDA(sg_launch(EPI_NS_SQR, p, n, hpad_max, hpad_max, stream), "NS square");
+        IFNSO_CUDA(mark(plan, stream, false), "timing event");
       }
       p.probs = probs + ly.pi_ns_apply + s * n;
       IFNSO_CUDA(sg_launch(EPI_NS_APPLY, p, n, max_h, max_w, stream), "NS apply");
+      IFNSO_CUDA(mark(plan, stream, false), "timing event");
     }
     return IFNSO_OK;
   }
@@ -1014,14 +1053,17 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
     p.items = sym;
     p.n_items = static_cast<int32_t>(ly.n_sym);
     IFNSO_CUDA(tc_launch(EPI_NS_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "NS Gram");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (degree == 5) {
       p.probs = probs + ly.pi_ns_sqr;
       IFNSO_CUDA(tc_launch(EPI_NS_SQR, 1, 1, p, grid_for(plan, ly.n_sym), stream), "NS square");
+      IFNSO_CUDA(mark(plan, stream, false), "timing event");
     }
     p.probs = probs + ly.pi_ns_apply + s * n;
     p.items = app;
     p.n_items = static_cast<int32_t>(ly.n_app);
     IFNSO_CUDA(tc_launch(EPI_NS_APPLY, 1, 1, p, grid_for(plan, ly.n_app), stream), "NS apply");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
   }
   return IFNSO_OK;
 }
@@ -1049,6 +1091,30 @@ ifnso_status ifnso_device_status(const ifnso_plan* plan, const void* workspace, 
     if (sc[i].status & IFNSO_DEV_TIMEOUT) timeout = true;
   }
   if (timeout) return fail(IFNSO_ERR_DEVICE_TIMEOUT, "a device wait timed out");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_passes, int32_t* n_passes,
+                              int32_t* n_calls) {
+  if (!plan || !ms_out || !n_passes || max_passes < 0) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  for (int k = 0; k < max_passes; ++k) ms_out[k] = 0.0;
+  *n_passes = 0;
+  if (n_calls) *n_calls = static_cast<int32_t>(plan->ev_calls.size());
+  for (auto& c : plan->ev_calls) {
+    if (c.size() < 2) continue;
+    IFNSO_CUDA(cudaEventSynchronize(c.back()), "cudaEventSynchronize");
+    const int np = static_cast<int>(c.size()) - 1;
+    *n_passes = np;
+    for (int k = 0; k < np && k < max_passes; ++k) {
+      float ms = 0.f;
+      IFNSO_CUDA(cudaEventElapsedTime(&ms, c[k], c[k + 1]), "cudaEventElapsedTime");
+      ms_out[k] += ms;
+    }
+  }
+  for (auto& c : plan->ev_calls)
+    for (cudaEvent_t e : c) plan->ev_pool.push_back(e);
+  plan->ev_calls.clear();
   return IFNSO_OK;
 }
 
@@ -1085,7 +1151,6 @@ ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dt
   IFNSO_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   IFNSO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
   IFNSO_CUDA(cudaMemsetAsync(norm2_out, 0, batch->count * sizeof(double), stream), "reset");
-  count_launch();
   // one launch per matrix with its description passed through a small device copy
   // kept in static storage of this entry point (grown on demand)
   static MatInfo* d_mi = nullptr;

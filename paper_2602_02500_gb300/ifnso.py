@@ -34,6 +34,7 @@ IFNSO_OPT_PRECISION = 1
 IFNSO_OPT_SCALE = 2
 IFNSO_OPT_MAX_CTAS = 3
 IFNSO_OPT_STOP_AFTER = 4
+IFNSO_OPT_TIMING = 5
 IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT = 0, 1, 2
 IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB = 0, 1
 IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4
@@ -41,7 +42,7 @@ IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4
 EXPORTED = [
     "ifnso_plan_create", "ifnso_plan_set", "ifnso_plan_get", "ifnso_plan_destroy",
     "ifnso_workspace_bytes", "ifnso_orthogonalize", "ns_iterate", "ns_workspace_bytes",
-    "ifnso_device_status", "ifnso_workspace_view", "ifnso_frobenius_norm2",
+    "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
     "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
     "ifnso_launch_count",
 ]
@@ -70,6 +71,8 @@ _sig = {
                              C.POINTER(_P), _P, C.c_size_t, _P]),
     "ifnso_device_status": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), _P]),
+    "ifnso_pass_times": (C.c_int, [_P, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32)]),
     "ifnso_workspace_view": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), _P, C.c_int32, C.c_int32,
                                        C.POINTER(_P), C.POINTER(C.c_int64)]),
     "ifnso_frobenius_norm2": (C.c_int, [C.POINTER(ifnso_batch_desc), C.c_int, _P, _P]),
@@ -262,6 +265,14 @@ class Plan:
         if rc not in (IFNSO_OK, IFNSO_ERR_DEVICE_TIMEOUT):
             check(rc, "ifnso_device_status")
         return np.array(st[:count]), np.array(o[:count]), np.array(tr[:count])
+
+    def pass_times(self, max_passes=64):
+        """(per-pass milliseconds summed over the calls since the last query, number of calls)."""
+        ms = (C.c_double * max_passes)()
+        n = C.c_int32()
+        calls = C.c_int32()
+        check(ifnso_pass_times(self.handle, ms, max_passes, C.byref(n), C.byref(calls)), "ifnso_pass_times")
+        return np.array(ms[:n.value]), calls.value
 
     def workspace_view(self, batch, index, which, ws=None):
         """(device pointer, ld) of an intermediate h_pad x h_pad buffer."""

@@ -29,10 +29,19 @@ def lib():
 
 
 def to_dev(M, dtype):
+    """Device copy of M; BF16 rows are padded to a multiple of 8 elements (the
+    16-byte row pitch TMA needs) and the view of the first cols columns returned."""
     import torch
 
-    t = torch.tensor(np.asarray(M, dtype=np.float32), device="cuda")
-    return t.to(torch.bfloat16) if dtype == "bf16" else t
+    M = np.asarray(M, dtype=np.float32)
+    t = torch.tensor(M, device="cuda")
+    if dtype != "bf16":
+        return t
+    r, c = M.shape
+    ld = (c + 7) // 8 * 8
+    buf = torch.zeros((r, ld), dtype=torch.bfloat16, device="cuda")
+    buf[:, :c] = t.to(torch.bfloat16)
+    return buf[:, :c]
 
 
 def to_np(t):

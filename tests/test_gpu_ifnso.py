@@ -21,7 +21,7 @@ def run_ifnso(mats, L, dtype, precision=None, scale=None, stop_after=None, plan_
 
     F = lib()
     xs = [to_dev(m, dtype) for m in mats]
-    ys = [torch.full_like(x, float("nan")) for x in xs]
+    ys = [torch.full(x.shape, float("nan"), dtype=x.dtype, device=x.device) for x in xs]
     hmax = max(min(x.shape) for x in xs)
     wmax = max(max(x.shape) for x in xs)
     plan = F.Plan(*(plan_shape or (hmax, wmax)), dtype, L=L, precision=precision, scale=scale)
@@ -148,7 +148,7 @@ def test_bf16_ns(shape):
     M = synth.gaussian(7, *shape)
     x = to_dev(M, "bf16")
     for poly, steps in [(ONS.MUON_ABC, 5), (ONS.CUBIC, 8)]:
-        y = torch.empty_like(x)
+        y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
         plan = F.Plan(min(shape), max(shape), "bf16", L=1)
         plan.ns_iterate(F.Batch([x]), poly, steps, [y])
         torch.cuda.synchronize()
