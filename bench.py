@@ -93,9 +93,18 @@ def load_peaks():
 
 
 def load_traffic():
+    """Per-launch DRAM traffic from the committed ncu summary, or {} when the
+    kernel source changed since the capture (the counters no longer apply)."""
+    import hashlib
+
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            return json.load(f)
+            t = json.load(f)
+        src = os.path.join(ROOT, "paper_2602_02500_gb300", "csrc", "tc_gemm.cu")
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != t.get("tc_gemm_sha256_16"):
+                return {}
+        return t
     except Exception:
         return {}
 

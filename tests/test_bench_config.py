@@ -1,0 +1,29 @@
+"""The benchmark's depth is the equal-polar-error depth recorded by the oracle analysis."""
+import importlib.util
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_bench_depth_matches_equal_polar_analysis():
+    with open(os.path.join(ROOT, "tests", "golden", "equal_polar.json")) as f:
+        eq = json.load(f)
+    chosen = set()
+    for shape, v in eq.items():
+        chosen.add(min(L for L in range(4, 21) if v[f"ifnso_L{L}"] <= v["ns5"]))
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert chosen == {bench.WORKLOADS["muon_1b"]["L"]}
+
+
+def test_flop_counts_match_oracle():
+    from oracle import flops
+
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for h, w in [(2048, 2048), (2048, 5632), (128, 1024)]:
+        assert bench.flops_ifnso(h, w, 14) == flops.ifnso_nominal(h, w, 14)
+        assert bench.flops_ns5(h, w) == flops.ns5_nominal(h, w)

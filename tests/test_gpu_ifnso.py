@@ -104,7 +104,8 @@ def test_bf16_prep(precision):
     A = to_np(xs[0])
     G = A @ A.T
     ref = G / np.linalg.norm(G)
-    tol = 2e-6 if precision == "split" else 1e-3
+    # split: limited by the FP32 accumulation of T_0 (as in test_bf16_gram); plain: FP16 rounding
+    tol = 1e-5 if precision == "split" else 1e-3
     assert rel(D[:300, :300], ref) < tol
 
 
