@@ -209,6 +209,29 @@ ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc
 ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dtype,
                                    double* norm2_out, ifnso_stream_t stream);
 
+/* Same result as ifnso_frobenius_norm2, without allocating device memory.
+ * The paper has no counterpart: this exists for callers that cannot let a
+ * library call cudaMalloc -- hosts that own all device memory through their
+ * own pool (a framework's caching allocator, a serving process's arena) and
+ * must not have memory taken or an out-of-memory raised behind their back,
+ * and latency-critical callers that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  (ifnso_frobenius_norm2 allocates
+ * its descriptor buffer on first use and grows it.)  The per-matrix
+ * descriptors go to a fixed array compiled into the library (about 120 KB,
+ * held on every GPU that loads the library until the process exits), so at
+ * most IFNSO_STATIC_NORM_MAX_MATRICES matrices per call; a larger batch is
+ * rejected with IFNSO_ERR_INVALID_ARG before anything is enqueued.  The
+ * caller passes the inputs and norm2_out (device, FP64, count entries), which
+ * the call zeroes before accumulating.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the array and it keeps the last call's descriptors: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Asynchronous on `stream`. */
+#define IFNSO_STATIC_NORM_MAX_MATRICES 1024
+ifnso_status ifnso_frobenius_norm2_static(const ifnso_batch_desc* batch, ifnso_dtype dtype,
+                                          double* norm2_out, ifnso_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Coefficient learning (Algorithm 1, "Coefficient learning"; Sec. 2.3, 3.1.1)
  * ------------------------------------------------------------------------- */

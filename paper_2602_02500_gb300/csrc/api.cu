@@ -737,6 +737,8 @@ Params base_params(uint8_t* ws, const Layout& ly, const ifnso_coeffs* cf) {
 
 void ifnso::count_launch(int n) { g_launches += static_cast<uint64_t>(n); }
 
+void ifnso::set_last_error(const char* msg) { g_err = msg; }
+
 // ====================================================================== C ABI
 extern "C" {
 

@@ -161,4 +161,7 @@ cudaError_t launch_synth_lowrank(void* out, int64_t rows, int64_t cols, int64_t 
 
 void count_launch(int n = 1);
 
+// Set the thread's message returned by ifnso_last_error() (defined in api.cu).
+void set_last_error(const char* msg);
+
 }  // namespace ifnso

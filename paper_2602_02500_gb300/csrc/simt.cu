@@ -286,3 +286,113 @@ cudaError_t sg_launch(int epi, const SgParams& p, int count, int max_m, int max_
 }
 
 }  // namespace ifnso
+
+// ====================================================================
+// Frobenius norm without any device allocation.
+//
+// ifnso_frobenius_norm2 keeps its per-matrix descriptors in device memory it
+// allocates with cudaMalloc on first use.  Some callers cannot allow that:
+// hosts that own all device memory through their own pool (a framework's
+// caching allocator, an inference server's arena) and do not want a library
+// to take memory behind their back or fail with out-of-memory mid-step, and
+// latency-critical code for which the device-wide synchronisation of
+// cudaMalloc / cudaFree is not acceptable.  This variant runs the same
+// k_norm2 kernel with its descriptors in a fixed array that lives in the
+// library image itself.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ifnso.h"
+
+namespace ifnso {
+namespace {
+
+constexpr int kStaticNormMaxMatrices = 1024;  // IFNSO_STATIC_NORM_MAX_MATRICES
+
+// Descriptor scratch of ifnso_frobenius_norm2_static: about 120 KB, held by
+// every GPU that loads the library until the process exits.
+static __device__ __align__(256) MatInfo g_norm_scratch[kStaticNormMaxMatrices];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_norm_scratch on the current device, looked up once per
+// device.  In host code the array's name is only a host-side stand-in, so
+// the kernel must be given this address instead.
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_norm_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace ifnso
+
+extern "C" ifnso_status ifnso_frobenius_norm2_static(const ifnso_batch_desc* batch, ifnso_dtype dtype,
+                                                     double* norm2_out, ifnso_stream_t stream_) {
+  using namespace ifnso;
+  char msg[160];
+  if (!batch || !norm2_out || batch->count < 0 || (batch->count > 0 && (!batch->in || !batch->rows || !batch->cols))) {
+    set_last_error("ifnso_frobenius_norm2_static: NULL or incomplete argument");
+    return IFNSO_ERR_INVALID_ARG;
+  }
+  if (dtype != IFNSO_BF16 && dtype != IFNSO_F32) {
+    set_last_error("ifnso_frobenius_norm2_static: dtype must be IFNSO_BF16 or IFNSO_F32");
+    return IFNSO_ERR_INVALID_ARG;
+  }
+  if (batch->count > kStaticNormMaxMatrices) {
+    snprintf(msg, sizeof(msg), "ifnso_frobenius_norm2_static: %d matrices exceed the static maximum of %d per call",
+             batch->count, kStaticNormMaxMatrices);
+    set_last_error(msg);
+    return IFNSO_ERR_INVALID_ARG;
+  }
+  const int n = batch->count;
+  if (n == 0) return IFNSO_OK;
+  std::vector<MatInfo> mi(n);
+  for (int i = 0; i < n; ++i) {
+    const int64_t r = batch->rows[i], c = batch->cols[i], ld = batch->ld ? batch->ld[i] : c;
+    if (r <= 0 || c <= 0 || ld < c || !batch->in[i]) {
+      snprintf(msg, sizeof(msg), "ifnso_frobenius_norm2_static: matrix %d has a bad shape or pointer", i);
+      set_last_error(msg);
+      return IFNSO_ERR_INVALID_ARG;
+    }
+    memset(&mi[i], 0, sizeof(MatInfo));
+    mi[i].in = batch->in[i];
+    mi[i].rows = r;
+    mi[i].cols = c;
+    mi[i].ld = ld;
+  }
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  void* scratch = nullptr;
+  cudaError_t e = scratch_address(&scratch);
+  // the descriptors overwrite the previous call's; the sums start at zero
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch, mi.data(), n * sizeof(MatInfo), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(norm2_out, 0, n * sizeof(double), stream);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    int gx = 4 * sms / n;
+    gx = gx < 1 ? 1 : (gx > 1024 ? 1024 : gx);
+    e = launch_norm2(static_cast<const MatInfo*>(scratch), n, dtype == IFNSO_BF16, norm2_out, 1, gx, stream);
+  }
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof(msg), "ifnso_frobenius_norm2_static: %s", cudaGetErrorString(e));
+    set_last_error(msg);
+    return IFNSO_ERR_CUDA;
+  }
+  return IFNSO_OK;
+}

@@ -38,12 +38,13 @@ IFNSO_OPT_TIMING = 5
 IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT = 0, 1, 2
 IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB = 0, 1
 IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4
+IFNSO_STATIC_NORM_MAX_MATRICES = 1024
 
 EXPORTED = [
     "ifnso_plan_create", "ifnso_plan_set", "ifnso_plan_get", "ifnso_plan_destroy",
     "ifnso_workspace_bytes", "ifnso_orthogonalize", "ns_iterate", "ns_workspace_bytes",
     "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
-    "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
+    "ifnso_frobenius_norm2_static", "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
     "ifnso_launch_count",
 ]
 
@@ -76,6 +77,7 @@ _sig = {
     "ifnso_workspace_view": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), _P, C.c_int32, C.c_int32,
                                        C.POINTER(_P), C.POINTER(C.c_int64)]),
     "ifnso_frobenius_norm2": (C.c_int, [C.POINTER(ifnso_batch_desc), C.c_int, _P, _P]),
+    "ifnso_frobenius_norm2_static": (C.c_int, [C.POINTER(ifnso_batch_desc), C.c_int, _P, _P]),
     "ifnso_learn_coefficients": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_double,
                                            C.c_uint32, C.POINTER(C.c_double)]),
     "ifnso_synth_lowrank_bf16": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, C.c_uint32, C.c_float, C.c_float, _P]),
