@@ -49,7 +49,11 @@ typedef enum {
    *   IFNSO_PREC_PLAIN: one FP16 operand per D_l, one BF16 operand for P.
    *   IFNSO_PREC_SPLIT: D_l = hi + lo (two FP16 parts, three products per
    *                     squaring), P = hi + lo (two BF16 parts, two products).
-   *   IFNSO_PREC_AUTO (default): SPLIT when L > 6, PLAIN otherwise. */
+   *   IFNSO_PREC_MIXED: the first max(0, L - 8) squarings split, the last
+   *                     ones plain (a rounding error of squaring l grows by up
+   *                     to 2^(L - l) in the later squarings), P split.
+   *   IFNSO_PREC_AUTO (default): PLAIN for L <= 4, MIXED for 5 <= L <= 14,
+   *                     SPLIT for L >= 15. */
   IFNSO_OPT_PRECISION = 1,
   /* Input scaling.  IFNSO_SCALE_GRAM (default): X = A / ||A A^T||_F^(1/2)
    * (Eq. new_scale_formula, Sec. 2; o = ||T_0||_F in Algorithm 1).
@@ -67,7 +71,7 @@ typedef enum {
   IFNSO_OPT_TIMING = 5
 } ifnso_option;
 
-enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2 };
+enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };
 enum { IFNSO_SCALE_GRAM = 0, IFNSO_SCALE_FROB = 1 };
 
 /* Per-matrix device status bits (ifnso_device_status). */

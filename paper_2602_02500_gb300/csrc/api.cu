@@ -131,10 +131,18 @@ struct Shape {
 
 // ------------------------------------------------------------------ layout
 // Workspace = [metadata | scalars | per-matrix buffers].  Offsets in bytes.
+struct Prec {
+  int ws_lo;    // the workspace keeps lo buffers
+  int k_split;  // squarings 1..k_split use split operands
+  int p_split;  // P = hi + lo for the final product
+  int mode;     // resolved IFNSO_PREC_*
+};
+
 struct Layout {
   int count = 0;
   int L = 0;
-  int split = 0;
+  int split = 0;     // the workspace keeps lo buffers (BF16 plans)
+  Prec prec{};
   int f32 = 0;
   int ns = 0;        // Newton-Schulz layout
   int steps = 0;
@@ -187,11 +195,27 @@ ifnso_status read_batch(const ifnso_plan* plan, const ifnso_batch_desc* b, std::
   return IFNSO_OK;
 }
 
-int resolved_split(const ifnso_plan* p) {
-  if (p->dtype != IFNSO_BF16) return 0;
-  if (p->precision == IFNSO_PREC_SPLIT) return 1;
-  if (p->precision == IFNSO_PREC_PLAIN) return 0;
-  return p->L > 6 ? 1 : 0;
+// Operand precision of a BF16 plan: how many of the L - 1 squarings multiply
+// split (hi + lo) operands -- always the first ones: a rounding error made in
+// squaring l is amplified by up to 2^(L - l) in the later ones, so the last
+// seven squarings tolerate plain FP16 operands -- and whether P is split for
+// the final product.
+Prec resolve_prec(const ifnso_plan* p) {
+  Prec r{0, 0, 0, IFNSO_PREC_PLAIN};
+  if (p->dtype != IFNSO_BF16) return r;
+  int mode = p->precision;
+  const int L = p->L;
+  if (mode == IFNSO_PREC_AUTO) mode = L <= 4 ? IFNSO_PREC_PLAIN : (L >= 15 ? IFNSO_PREC_SPLIT : IFNSO_PREC_MIXED);
+  r.mode = mode;
+  if (mode == IFNSO_PREC_SPLIT) {
+    r.k_split = L - 1;
+    r.p_split = 1;
+  } else if (mode == IFNSO_PREC_MIXED) {
+    r.k_split = std::max(0, L - 8);
+    r.p_split = 1;
+  }
+  r.ws_lo = r.p_split || r.k_split > 0;
+  return r;
 }
 
 void sym_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
@@ -231,7 +255,8 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   Layout ly;
   ly.count = static_cast<int>(shp.size());
   ly.L = plan->L;
-  ly.split = ns ? 0 : resolved_split(plan);
+  ly.prec = ns ? Prec{0, 0, 0, IFNSO_PREC_PLAIN} : resolve_prec(plan);
+  ly.split = ly.prec.ws_lo;
   ly.f32 = plan->dtype == IFNSO_F32;
   ly.ns = ns;
   ly.steps = steps;
@@ -355,7 +380,8 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
 uint64_t batch_sig(const ifnso_plan* plan, const ifnso_batch_desc* b, void* const* out, const void* ws,
                    const ifnso_coeffs* cf, const double* poly, int degree, int steps, int kind) {
   uint64_t h = 1469598103934665603ull;
-  int opts[6] = {plan->L, resolved_split(plan), plan->scale, plan->dtype, kind, steps};
+  const Prec pr = resolve_prec(plan);
+  int opts[8] = {plan->L, pr.mode, pr.k_split, pr.p_split, plan->scale, plan->dtype, kind, steps};
   h = fnv(h, opts, sizeof(opts));
   h = fnv(h, &ws, sizeof(ws));
   h = fnv(h, &b->count, sizeof(b->count));
@@ -775,7 +801,7 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
   std::lock_guard<std::mutex> lk(plan->mu);
   switch (option) {
     case IFNSO_OPT_PRECISION:
-      if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "precision %lld", (long long)value);
+      if (value < 0 || value > 3) return fail(IFNSO_ERR_INVALID_ARG, "precision %lld", (long long)value);
       plan->precision = static_cast<int>(value);
       break;
     case IFNSO_OPT_SCALE:
@@ -803,7 +829,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
   if (!plan || !value) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
   switch (option) {
     case IFNSO_OPT_PRECISION:
-      *value = plan->dtype == IFNSO_BF16 ? (resolved_split(plan) ? IFNSO_PREC_SPLIT : IFNSO_PREC_PLAIN) : IFNSO_PREC_PLAIN;
+      *value = resolve_prec(plan).mode;
       return IFNSO_OK;
     case IFNSO_OPT_SCALE: *value = plan->scale; return IFNSO_OK;
     case IFNSO_OPT_MAX_CTAS: *value = plan->max_ctas; return IFNSO_OK;
@@ -924,7 +950,8 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   const TcProblem* probs = reinterpret_cast<const TcProblem*>(ws + ly.off_probs);
   const WorkItem* sym = reinterpret_cast<const WorkItem*>(ws + ly.off_items_sym);
   const WorkItem* app = reinterpret_cast<const WorkItem*>(ws + ly.off_items_app);
-  const int nab = ly.split ? 2 : 1;
+  const Prec& pc = ly.prec;
+  p.p_split = pc.p_split;
   p.probs = probs + ly.pi_gram;
   p.items = sym;
   p.n_items = static_cast<int32_t>(ly.n_sym);
@@ -932,17 +959,23 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
   IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 0) return IFNSO_OK;
-  IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, ly.split, 0, stream), "prep");
+  // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo)
+  const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
+  IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, prep_lo, 0, stream), "prep");
   IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 1) return IFNSO_OK;
   for (int j = 1; j <= L - 1; ++j) {
     const int par = (j - 1) % 2;
+    const int split = j <= pc.k_split ? 1 : 0;
     p.probs = probs + ly.pi_sqr + par * n;
     p.items = sym;
     p.n_items = static_cast<int32_t>(ly.n_sym);
     p.coef_l = j + 1;
     p.final_pass = (j == L - 1);
-    IFNSO_CUDA(tc_launch(EPI_SQR, nab, nab, p, grid_for(plan, ly.n_sym), stream), "squaring pass");
+    p.read_lo = split;
+    p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
+    IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, ly.n_sym), stream),
+               "squaring pass");
     IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (plan->stop_after == 1 + j) return IFNSO_OK;
   }
@@ -951,7 +984,8 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   p.n_items = static_cast<int32_t>(ly.n_app);
   p.coef_l = 0;
   p.final_pass = 0;
-  IFNSO_CUDA(tc_launch(EPI_APPLY, nab, 1, p, grid_for(plan, ly.n_app), stream), "apply pass");
+  p.read_lo = p.write_lo = 0;
+  IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, ly.n_app), stream), "apply pass");
   IFNSO_CUDA(mark(plan, stream, false), "timing event");
   return IFNSO_OK;
 }
@@ -1006,7 +1040,7 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
   IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
   IFNSO_CUDA(mark(plan, stream, true), "timing event");
   // ||A||_F^2 into the trace slot, then the scalars with the Frobenius scale
-  int gx = std::max(1, std::min(1024, 4 * plan->num_sms / std::max(1, n)));
+  int gx = std::max(1, std::min(1024, 16 * plan->num_sms / std::max(1, n)));
   IFNSO_CUDA(launch_norm2(d_mats, n, plan->dtype == IFNSO_BF16, &scal[0].trace,
                           sizeof(MatScalars) / sizeof(double), gx, stream),
              "norm");
@@ -1177,7 +1211,7 @@ ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dt
   }
   IFNSO_CUDA(cudaMemcpyAsync(d_mi, h.data(), h.size() * sizeof(MatInfo), cudaMemcpyHostToDevice, stream), "upload");
   IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
-  int gx = std::max(1, std::min(1024, 4 * sms / std::max(1, batch->count)));
+  int gx = std::max(1, std::min(1024, 16 * sms / std::max(1, batch->count)));
   IFNSO_CUDA(launch_norm2(d_mi, batch->count, dtype == IFNSO_BF16, norm2_out, 1, gx, stream), "norm");
   return IFNSO_OK;
 }

@@ -93,6 +93,10 @@ struct TcParams {
   int32_t coef_l;      // EPI_SQR: index l + 1 of the coefficient this pass adds
   int32_t final_pass;  // EPI_SQR: write P (BF16 hi/lo) instead of D_{l+1}
   int32_t ns_step;     // NS epilogues: step index (step 0 applies the input scale)
+  int32_t read_lo;     // EPI_SQR: this pass multiplies D_l = hi + lo (split operands)
+  int32_t write_lo;    // EPI_SQR: store D_{l+1} as hi + lo (the next pass is split)
+  int32_t p_split;     // EPI_SQR final pass / prep: store P as BF16 hi + lo
+  int32_t pad1;
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;

@@ -122,23 +122,54 @@ __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* s
   const float c0 = static_cast<float>(scal[m].c0);
   const float w1 = static_cast<float>(coef_at(coef, m, 1));
   float* gp = mi.gp;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = e / hp, j = e % hp;
-    const float d = gp[e] * inv;
-    const float p = fmaf(-w1, d, i == j ? c0 : 0.f);
+  // 8 consecutive elements of one row per step (h_pad is a multiple of 256):
+  // two 16-byte loads of T_0, 16-byte stores of every output
+  const int64_t row8 = hp / 8;
+  for (int64_t e8 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e8 < n / 8;
+       e8 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e8 / row8, j0 = (e8 - i * row8) * 8;
+    const int64_t e = i * hp + j0;
+    const float4 g0 = reinterpret_cast<const float4*>(gp + e)[0];
+    const float4 g1 = reinterpret_cast<const float4*>(gp + e)[1];
+    const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+    float d[8], p[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      d[t] = g[t] * inv;
+      p[t] = fmaf(-w1, d[t], (j0 + t == i) ? c0 : 0.f);
+    }
     if (f32) {
-      static_cast<float*>(mi.d[0])[e] = d;
-      gp[e] = p;
+      float4* dd = reinterpret_cast<float4*>(static_cast<float*>(mi.d[0]) + e);
+      dd[0] = make_float4(d[0], d[1], d[2], d[3]);
+      dd[1] = make_float4(d[4], d[5], d[6], d[7]);
+      reinterpret_cast<float4*>(gp + e)[0] = make_float4(p[0], p[1], p[2], p[3]);
+      reinterpret_cast<float4*>(gp + e)[1] = make_float4(p[4], p[5], p[6], p[7]);
     } else if (L == 1) {
-      const __nv_bfloat16 hi = __float2bfloat16_rn(p);
-      static_cast<__nv_bfloat16*>(mi.d[0])[e] = hi;
-      if (split) static_cast<__nv_bfloat16*>(mi.d[1])[e] = __float2bfloat16_rn(p - __bfloat162float(hi));
+      uint4 uh, ul;
+      __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&uh);
+      __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(&ul);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        h2[t] = __floats2bfloat162_rn(p[2 * t], p[2 * t + 1]);
+        const float2 hf = __bfloat1622float2(h2[t]);
+        l2[t] = __floats2bfloat162_rn(p[2 * t] - hf.x, p[2 * t + 1] - hf.y);
+      }
+      *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(mi.d[0]) + e) = uh;
+      if (split) *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(mi.d[1]) + e) = ul;
     } else {
-      const __half hi = __float2half_rn(d);
-      static_cast<__half*>(mi.d[0])[e] = hi;
-      if (split) static_cast<__half*>(mi.d[1])[e] = __float2half_rn(d - __half2float(hi));
-      gp[e] = p;
+      uint4 uh, ul;
+      __half2* h2 = reinterpret_cast<__half2*>(&uh);
+      __half2* l2 = reinterpret_cast<__half2*>(&ul);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        h2[t] = __floats2half2_rn(d[2 * t], d[2 * t + 1]);
+        const float2 hf = __half22float2(h2[t]);
+        l2[t] = __floats2half2_rn(d[2 * t] - hf.x, d[2 * t + 1] - hf.y);
+      }
+      *reinterpret_cast<uint4*>(static_cast<__half*>(mi.d[0]) + e) = uh;
+      if (split) *reinterpret_cast<uint4*>(static_cast<__half*>(mi.d[1]) + e) = ul;
+      reinterpret_cast<float4*>(gp + e)[0] = make_float4(p[0], p[1], p[2], p[3]);
+      reinterpret_cast<float4*>(gp + e)[1] = make_float4(p[4], p[5], p[6], p[7]);
     }
   }
 }
@@ -385,7 +416,7 @@ extern "C" ifnso_status ifnso_frobenius_norm2_static(const ifnso_batch_desc* bat
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    int gx = 4 * sms / n;
+    int gx = 16 * sms / n;
     gx = gx < 1 ? 1 : (gx > 1024 ? 1024 : gx);
     e = launch_norm2(static_cast<const MatInfo*>(scratch), n, dtype == IFNSO_BF16, norm2_out, 1, gx, stream);
   }

@@ -34,6 +34,8 @@ constexpr int kThreads = 192;
 constexpr uint32_t kTileA = BM * BK * 2;  // 16 KB: 128 rows x 64 K of 16-bit values
 constexpr uint32_t kTileB = BN * BK * 2;  // 32 KB: 256 rows x 64 K
 constexpr uint32_t kTmemCols = 512;
+constexpr int kStageLd = 33;                               // padded row of a transpose buffer
+constexpr uint32_t kStageBytes = 4 * 32 * kStageLd * 4;   // one 32 x 33 float buffer per epilogue warp
 constexpr int kDevTimeout = 4;  // IFNSO_DEV_TIMEOUT
 
 template <int NA, int NB>
@@ -41,8 +43,8 @@ struct Cfg {
   static constexpr uint32_t stage_bytes = NA * kTileA + NB * kTileB;
   static constexpr int stages_fit = static_cast<int>((200u * 1024u) / stage_bytes);
   static constexpr int stages = stages_fit > 6 ? 6 : stages_fit;
-  // tiles + 1 KB alignment slack + barriers / flags
-  static constexpr uint32_t smem = stages * stage_bytes + 1024 + 256;
+  // tiles + 1 KB alignment slack + barriers / flags + epilogue transpose buffers
+  static constexpr uint32_t smem = stages * stage_bytes + 1024 + 256 + kStageBytes;
 };
 
 // Number of products per K step: every (A source, B source) pair except
@@ -117,52 +119,66 @@ __device__ __forceinline__ void store_b32(__nv_bfloat16* dst, const float* v) {
   }
 }
 
-// Store a 32-wide row chunk of a symmetric result at (r, c0..c0+31) and,
-// for tiles off the diagonal blocks, at (c0..c0+31, r).
-template <typename T>
-__device__ __forceinline__ void store_sym(T* buf, int64_t ld, int r, int c0, const float* v,
-                                          bool mirror);
+// Per-warp 32 x 32 transpose through shared memory (rows padded to 33
+// floats: conflict-free in both directions).  Lane t holds v[0..31] = row
+// t of a 32 x 32 block; afterwards it holds w[0..31] = column t.  Every lane
+// of the warp must call it.
 
+__device__ __forceinline__ void warp_transpose(float* st, const float* v, float* w) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) st[lane * kStageLd + j] = v[j];
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < 32; ++i) w[i] = st[i * kStageLd + lane];
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row32(T* dst, const float* v);
 template <>
-__device__ __forceinline__ void store_sym<float>(float* buf, int64_t ld, int r, int c0,
-                                                 const float* v, bool mirror) {
-  float4* d4 = reinterpret_cast<float4*>(buf + static_cast<int64_t>(r) * ld + c0);
+__device__ __forceinline__ void store_row32<float>(float* dst, const float* v) {
+  float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
   for (int j = 0; j < 8; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-  if (mirror) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) buf[static_cast<int64_t>(c0 + j) * ld + r] = v[j];
-  }
 }
-
 template <>
-__device__ __forceinline__ void store_sym<__half>(__half* buf, int64_t ld, int r, int c0,
-                                                  const float* v, bool mirror) {
-  store_h32(buf + static_cast<int64_t>(r) * ld + c0, v);
-  if (mirror) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) buf[static_cast<int64_t>(c0 + j) * ld + r] = __float2half_rn(v[j]);
-  }
+__device__ __forceinline__ void store_row32<__half>(__half* dst, const float* v) {
+  store_h32(dst, v);
 }
-
 template <>
-__device__ __forceinline__ void store_sym<__nv_bfloat16>(__nv_bfloat16* buf, int64_t ld, int r,
-                                                         int c0, const float* v, bool mirror) {
-  store_b32(buf + static_cast<int64_t>(r) * ld + c0, v);
+__device__ __forceinline__ void store_row32<__nv_bfloat16>(__nv_bfloat16* dst, const float* v) {
+  store_b32(dst, v);
+}
+
+// Store a 32-wide row chunk of a symmetric h_pad x h_pad result at
+// (r, c0..c0+31) and, for tiles off the diagonal blocks, at (c0..c0+31, r):
+// the mirrored chunk is transposed through shared memory so that every lane
+// writes one contiguous 32-element row segment.  `mirror` is warp-uniform.
+template <typename T>
+__device__ __forceinline__ void store_sym(T* buf, int64_t ld, int r, int c0, const float* v,
+                                          bool mirror, float* st) {
+  store_row32<T>(buf + static_cast<int64_t>(r) * ld + c0, v);
   if (mirror) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      buf[static_cast<int64_t>(c0 + j) * ld + r] = __float2bfloat16_rn(v[j]);
+    float w[32];
+    warp_transpose(st, v, w);
+    const int lane = threadIdx.x & 31;
+    store_row32<T>(buf + static_cast<int64_t>(c0 + lane) * ld + (r - lane), w);
   }
 }
 
-// Bounds-checked BF16 store of a 32-wide chunk of an output tile.
-__device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r, int c0, const float* v) {
+// Bounds-checked BF16 store of a 32-wide chunk of an output tile (row r,
+// columns c0..c0+31).  With out_trans the tile is the transpose of the
+// output: the chunk is transposed through shared memory and lane t writes
+// output row c0 + t, columns (r - lane)..(r - lane + 31).  Warp-uniform call.
+__device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r, int c0, const float* v,
+                                               float* st) {
   __nv_bfloat16* out = static_cast<__nv_bfloat16*>(pr.out0);
+  const bool vec_ld = (pr.ld_out & 7) == 0;
   if (!pr.out_trans) {
     if (r >= pr.rows_out) return;
     __nv_bfloat16* o = out + static_cast<int64_t>(r) * pr.ld_out + c0;
-    if (c0 + 32 <= pr.cols_out && (pr.ld_out & 7) == 0) {
+    if (c0 + 32 <= pr.cols_out && vec_ld) {
       store_b32(o, v);
     } else {
 #pragma unroll
@@ -170,30 +186,58 @@ __device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r, int c
         if (c0 + j < pr.cols_out) o[j] = __float2bfloat16_rn(v[j]);
     }
   } else {
-    if (r >= pr.cols_out) return;
+    float w[32];
+    warp_transpose(st, v, w);
+    const int lane = threadIdx.x & 31;
+    const int orow = c0 + lane, ocol = r - lane;
+    if (orow >= pr.rows_out) return;
+    __nv_bfloat16* o = out + static_cast<int64_t>(orow) * pr.ld_out + ocol;
+    if (ocol + 32 <= pr.cols_out && vec_ld) {
+      store_b32(o, w);
+    } else {
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (c0 + j < pr.rows_out)
-        out[static_cast<int64_t>(c0 + j) * pr.ld_out + r] = __float2bfloat16_rn(v[j]);
+      for (int i = 0; i < 32; ++i)
+        if (ocol + i < pr.cols_out) o[i] = __float2bfloat16_rn(w[i]);
+    }
   }
 }
 
 // Load the 32 values of the NS iterate X at the positions a chunk of the
-// output tile is written to (same layout rules as store_out_bf16).
-__device__ __forceinline__ void load_x_bf16(const TcProblem& pr, int r, int c0, float* x) {
+// output tile is written to (same layout rules as store_out_bf16; zero
+// outside the matrix).  Warp-uniform call.
+__device__ __forceinline__ void load_x_bf16(const TcProblem& pr, int r, int c0, float* x, float* st) {
   const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(pr.aux0);
+  const bool vec_ld = (pr.ld_aux & 7) == 0;
   if (!pr.out_trans) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = 0.f;
     if (r >= pr.rows_out) return;
     const __nv_bfloat16* s = X + static_cast<int64_t>(r) * pr.ld_aux + c0;
+    if (c0 + 32 <= pr.cols_out && vec_ld) {
+      load_b32(s, x);
+    } else {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = (c0 + j < pr.cols_out) ? __bfloat162float(s[j]) : 0.f;
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < pr.cols_out) x[j] = __bfloat162float(s[j]);
+    }
   } else {
-    if (r >= pr.cols_out) return;
+    // lane t reads row c0 + t of X, columns (r - lane)..+31, then the block is transposed
+    const int lane = threadIdx.x & 31;
+    const int xrow = c0 + lane, xcol = r - lane;
+    float u[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-      x[j] = (c0 + j < pr.rows_out)
-                 ? __bfloat162float(X[static_cast<int64_t>(c0 + j) * pr.ld_aux + r])
-                 : 0.f;
+    for (int i = 0; i < 32; ++i) u[i] = 0.f;
+    if (xrow < pr.rows_out) {
+      const __nv_bfloat16* s = X + static_cast<int64_t>(xrow) * pr.ld_aux + xcol;
+      if (xcol + 32 <= pr.cols_out && vec_ld) {
+        load_b32(s, u);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (xcol + i < pr.cols_out) u[i] = __bfloat162float(s[i]);
+      }
+    }
+    warp_transpose(st, u, x);
   }
 }
 
@@ -205,10 +249,10 @@ struct EpiAcc {
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProblem& pr,
                                                const WorkItem& wi, int r, int c0, float* v,
-                                               EpiAcc& ea) {
+                                               EpiAcc& ea, float* st) {
   const bool mirror = (wi.flags & 1) == 0;
   if constexpr (EPI == EPI_GRAM) {
-    store_sym<float>(pr.pacc, pr.ld_aux, r, c0, v, mirror);
+    store_sym<float>(pr.pacc, pr.ld_aux, r, c0, v, mirror, st);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       ea.ss = fmaf(v[j], v[j], ea.ss);
@@ -218,7 +262,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     float d[32], lo[32];
     const int64_t off = static_cast<int64_t>(r) * pr.ld_aux + c0;
     load_h32(static_cast<const __half*>(pr.aux0) + off, d);
-    if (pr.aux1) {
+    if (p.read_lo) {
       load_h32(static_cast<const __half*>(pr.aux1) + off, lo);
 #pragma unroll
       for (int j = 0; j < 32; ++j) d[j] += lo[j];
@@ -245,56 +289,56 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       for (int j = 0; j < 8; ++j)
         reinterpret_cast<float4*>(P)[j] =
             make_float4(pv[4 * j], pv[4 * j + 1], pv[4 * j + 2], pv[4 * j + 3]);
-      if (pr.out1) {
+      if (p.write_lo) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float hi = __half2float(__float2half_rn(v[j]));
           lo[j] = v[j] - hi;
           v[j] = hi;
         }
-        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror);
-        store_sym<__half>(static_cast<__half*>(pr.out1), pr.ld_out, r, c0, lo, mirror);
+        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
+        store_sym<__half>(static_cast<__half*>(pr.out1), pr.ld_out, r, c0, lo, mirror, st);
       } else {
-        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
       }
     } else {
-      if (pr.out1) {
+      if (p.p_split) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float hi = __bfloat162float(__float2bfloat16_rn(pv[j]));
           lo[j] = pv[j] - hi;
           pv[j] = hi;
         }
-        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror);
-        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out1), pr.ld_out, r, c0, lo, mirror);
+        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror, st);
+        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out1), pr.ld_out, r, c0, lo, mirror, st);
       } else {
-        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror);
+        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror, st);
       }
     }
   } else if constexpr (EPI == EPI_APPLY) {
     const float s = p.scal[pr.mat].inv_s;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] *= s;
-    store_out_bf16(pr, r, c0, v);
+    store_out_bf16(pr, r, c0, v, st);
   } else if constexpr (EPI == EPI_NS_GRAM) {
     const float s2 = p.ns_step == 0 ? p.scal[pr.mat].inv_s2 : 1.0f;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] *= s2;
-    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
   } else if constexpr (EPI == EPI_NS_SQR) {
     float s[32];
     load_b32(static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r) * pr.ld_aux + c0, s);
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(p.ns_c, v[j], p.ns_b * s[j]);
-    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror);
+    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
   } else if constexpr (EPI == EPI_NS_APPLY) {
     const float sc = p.ns_step == 0 ? p.scal[pr.mat].inv_s : 1.0f;
     float x[32];
-    load_x_bf16(pr, r, c0, x);
+    load_x_bf16(pr, r, c0, x, st);
     const float ka = p.ns_a * sc, kb = p.ns_bcoef * sc;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(ka, x[j], kb * v[j]);
-    store_out_bf16(pr, r, c0, v);
+    store_out_bf16(pr, r, c0, v, st);
   }
 }
 
@@ -473,6 +517,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..5)
+    float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256) + (warp - 2) * 32 * kStageLd;
     const int q = warp & 3;  // TMEM lane quadrant this warp may access
     const int row_in_tile = q * 32 + lane;
     int local = 0;
@@ -501,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = u2f(u[j]);
-        epilogue_chunk<EPI>(p, pr, wi, r, wi.tn * BN + ch * 32, v, ea);
+        epilogue_chunk<EPI>(p, pr, wi, r, wi.tn * BN + ch * 32, v, ea, stage);
       }
       tc_fence_before();
       mbar_arrive(tempty_bar(acc));

@@ -35,7 +35,7 @@ IFNSO_OPT_SCALE = 2
 IFNSO_OPT_MAX_CTAS = 3
 IFNSO_OPT_STOP_AFTER = 4
 IFNSO_OPT_TIMING = 5
-IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT = 0, 1, 2
+IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT, IFNSO_PREC_MIXED = 0, 1, 2, 3
 IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB = 0, 1
 IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4
 IFNSO_STATIC_NORM_MAX_MATRICES = 1024
@@ -174,7 +174,7 @@ class Plan:
         check(ifnso_plan_create(C.byref(h_), int(h), int(w), self.dtype, ex, K), "ifnso_plan_create")
         self.handle = h_
         if precision is not None:
-            self.set(IFNSO_OPT_PRECISION, {"auto": 0, "plain": 1, "split": 2}.get(precision, precision))
+            self.set(IFNSO_OPT_PRECISION, {"auto": 0, "plain": 1, "split": 2, "mixed": 3}.get(precision, precision))
         if scale is not None:
             self.set(IFNSO_OPT_SCALE, {"gram": 0, "frob": 1}.get(scale, scale))
         if max_ctas is not None:

@@ -97,3 +97,14 @@ def test_learn_argument_checks(F):
     w = (C.c_double * 4)()
     assert F.ifnso_learn_coefficients(0, 10, 100, 0.1, 10, 0.5, 0, w) == F.IFNSO_ERR_INVALID_ARG
     assert F.ifnso_learn_coefficients(4, 10, 5000, 0.1, 10, 0.5, 0, w) == F.IFNSO_ERR_INVALID_ARG
+
+
+def test_precision_resolution(F):
+    # AUTO: plain for L <= 4, mixed (first L - 8 squarings split, P split) for 5..14, split above
+    for L, mode in [(4, F.IFNSO_PREC_PLAIN), (5, F.IFNSO_PREC_MIXED), (14, F.IFNSO_PREC_MIXED),
+                    (15, F.IFNSO_PREC_SPLIT)]:
+        st, p = _plan(F, 256, 512, L)
+        v = C.c_int64()
+        assert F.ifnso_plan_get(p, F.IFNSO_OPT_PRECISION, C.byref(v)) == 0
+        assert v.value == mode, (L, v.value)
+        F.ifnso_plan_destroy(p)
