@@ -974,6 +974,9 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
     p.final_pass = (j == L - 1);
     p.read_lo = split;
     p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
+    // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
+    // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
+    p.p_mode = j == 1 ? 1 : ((j & 1) ? 2 : (j == L - 1 ? 3 : 0));
     IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, ly.n_sym), stream),
                "squaring pass");
     IFNSO_CUDA(mark(plan, stream, false), "timing event");

@@ -96,7 +96,8 @@ struct TcParams {
   int32_t read_lo;     // EPI_SQR: this pass multiplies D_l = hi + lo (split operands)
   int32_t write_lo;    // EPI_SQR: store D_{l+1} as hi + lo (the next pass is split)
   int32_t p_split;     // EPI_SQR final pass / prep: store P as BF16 hi + lo
-  int32_t pad1;
+  int32_t p_mode;      // EPI_SQR: 0 P untouched, 1 P written from c0 I and two terms,
+                       // 2 P read and two terms subtracted, 3 P read and one term subtracted
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;

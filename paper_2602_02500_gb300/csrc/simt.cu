@@ -109,9 +109,9 @@ __global__ void k_scalars(int count, MatScalars* scal, CoefTable coef, int L, in
 //   d = T_0 * (1/s2)                       (D_1 = T_0 / o, the scaled Gram)
 //   P = c0 [i == j] - w_1 d                (Y' accumulated in the D basis)
 // BF16 plans store D_1 as FP16 (hi, and lo = d - hi when split) in D buffer
-// 0 and keep P in FP32 in place of T_0.  For L = 1 there is no squaring:
-// P itself is written as BF16 (hi, lo) into D buffer 0.  FP32 plans store
-// D_1 in FP32 in D buffer 0 and P in place of T_0.
+// 0; their first squaring writes P (FP32, in place of T_0).  For L = 1 there
+// is no squaring: P itself is written as BF16 (hi, lo) into D buffer 0.
+// FP32 plans store D_1 in FP32 in D buffer 0 and P in place of T_0.
 __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* scal, CoefTable coef,
                                               int L, int split, int f32) {
   const int m = blockIdx.y;
@@ -168,8 +168,7 @@ __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* s
       }
       *reinterpret_cast<uint4*>(static_cast<__half*>(mi.d[0]) + e) = uh;
       if (split) *reinterpret_cast<uint4*>(static_cast<__half*>(mi.d[1]) + e) = ul;
-      reinterpret_cast<float4*>(gp + e)[0] = make_float4(p[0], p[1], p[2], p[3]);
-      reinterpret_cast<float4*>(gp + e)[1] = make_float4(p[4], p[5], p[6], p[7]);
+      // P itself is first written by the first squaring (with its first two terms)
     }
   }
 }

@@ -6,13 +6,14 @@
 // D basis, D_{l+1} = 2 D_l - D_l^2), or the final product Y = Y' A / sqrt(o).
 // Each CTA (one per SM) walks a static list of 128 x 256 output tiles.
 //
-// Warp roles (192 threads):
+// Warp roles (320 threads):
 //   warp 0      TMA producer: K blocks of 64 of every operand source into a
 //               ring of shared-memory stages (128-byte swizzle).
 //   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
 //               and MMA issuer: tcgen05.mma M=128, N=256, K=16, kind::f16.
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, fused elementwise
-//               math of the pass, stores to global memory.
+//   warps 2..9  epilogue (two warps per TMEM lane quadrant, 128 columns each):
+//               tcgen05.ld of the accumulator, fused elementwise math of the
+//               pass, stores to global memory.
 // The two accumulators let the epilogue of tile t overlap the main loop of
 // tile t + 1.  Symmetric outputs (T_0, D_l, P) are computed on the upper
 // 256 x 256 blocks only and stored twice (direct and mirrored).
@@ -30,12 +31,13 @@ namespace ifnso {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                  // two per TMEM lane quadrant, 128 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr uint32_t kTileA = BM * BK * 2;  // 16 KB: 128 rows x 64 K of 16-bit values
 constexpr uint32_t kTileB = BN * BK * 2;  // 32 KB: 256 rows x 64 K
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStageLd = 33;                               // padded row of a transpose buffer
-constexpr uint32_t kStageBytes = 4 * 32 * kStageLd * 4;   // one 32 x 33 float buffer per epilogue warp
+constexpr uint32_t kStageBytes = kEpiWarps * 32 * kStageLd * 4;  // one 32 x 33 float buffer per epilogue warp
 constexpr int kDevTimeout = 4;  // IFNSO_DEV_TIMEOUT
 
 template <int NA, int NB>
@@ -267,28 +269,42 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
 #pragma unroll
       for (int j = 0; j < 32; ++j) d[j] += lo[j];
     }
+    // P = (1 + sum w) I - sum_l w_l D_l is accumulated two terms at a time:
+    // p_mode 1 (first squaring) writes P = c0 I - w_l D_l - w_{l+1} D_{l+1},
+    // p_mode 2 subtracts w_l D_l + w_{l+1} D_{l+1}, p_mode 3 only
+    // w_{l+1} D_{l+1} (last squaring after an even count), p_mode 0 leaves P.
     const float w = static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l));
+    const float wp = (p.p_mode == 1 || p.p_mode == 2)
+                         ? static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l - 1)) : 0.f;
     float* P = pr.pacc + off;
     float pv[32];
+    if (p.p_mode >= 2) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      float4 t = reinterpret_cast<const float4*>(P)[j];
-      pv[4 * j] = t.x;
-      pv[4 * j + 1] = t.y;
-      pv[4 * j + 2] = t.z;
-      pv[4 * j + 3] = t.w;
+      for (int j = 0; j < 8; ++j) {
+        float4 t = reinterpret_cast<const float4*>(P)[j];
+        pv[4 * j] = t.x;
+        pv[4 * j + 1] = t.y;
+        pv[4 * j + 2] = t.z;
+        pv[4 * j + 3] = t.w;
+      }
+    } else {
+      const float c0f = p.p_mode == 1 ? static_cast<float>(p.scal[pr.mat].c0) : 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) pv[j] = (c0 + j == r) ? c0f : 0.f;
     }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const float dn = 2.0f * d[j] - v[j];  // D_{l+1} = 2 D_l - D_l^2
       v[j] = dn;
-      pv[j] = fmaf(-w, dn, pv[j]);          // P -= w_{l+1} D_{l+1}
+      pv[j] = fmaf(-w, dn, fmaf(-wp, d[j], pv[j]));
     }
     if (!p.final_pass) {
+      if (p.p_mode != 0) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        reinterpret_cast<float4*>(P)[j] =
-            make_float4(pv[4 * j], pv[4 * j + 1], pv[4 * j + 2], pv[4 * j + 3]);
+        for (int j = 0; j < 8; ++j)
+          reinterpret_cast<float4*>(P)[j] =
+              make_float4(pv[4 * j], pv[4 * j + 1], pv[4 * j + 2], pv[4 * j + 3]);
+      }
       if (p.write_lo) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -375,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 128);
+      mbar_init(tempty_bar(a), 32 * kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -516,9 +532,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       mbar_wait_bounded(drain_bar, 0);
     }
   } else {
-    // -------------------------------------------------- epilogue (warps 2..5)
+    // -------------------------------------------------- epilogue (warps 2..9)
     float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256) + (warp - 2) * 32 * kStageLd;
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int q = warp & 3;            // TMEM lane quadrant this warp may access
+    const int half = (warp - 2) >> 2;  // which 128 of the tile's 256 columns
     const int row_in_tile = q * 32 + lane;
     int local = 0;
     for (int it = blockIdx.x; it < p.n_items; it += gridDim.x, ++local) {
@@ -539,7 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const int r = wi.tm * BM + row_in_tile;
       EpiAcc ea{0.f, 0.f};
 #pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
+      for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
         uint32_t u[32];
         IFNSO_TMEM_LD32(tbase + static_cast<uint32_t>(ch * 32), u);
         IFNSO_TMEM_WAIT_LD(u);

@@ -110,7 +110,8 @@ def test_bf16_prep(precision):
 
 
 @pytest.mark.parametrize("L,precision", [(4, "plain"), (4, "split"), (14, "split"), (9, "plain"),
-                                         (14, "mixed"), (14, "auto"), (10, "mixed")])
+                                         (14, "mixed"), (14, "auto"), (10, "mixed"), (2, "split"),
+                                         (3, "plain"), (1, "split"), (5, "auto")])
 @pytest.mark.parametrize("shape", [(256, 512), (200, 328), (392, 136), (512, 512), (640, 1000)])
 def test_bf16_ifnso(shape, L, precision):
     M = synth.gaussian(4, *shape)
