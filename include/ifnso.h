@@ -103,14 +103,20 @@ typedef struct {
  * exponents n = (0, 1, 2, 4, ..., 2^(L-1)) (Eq. generalized_matrix_formula and
  * the exponential selection of Sec. 2.2).  K = L + 1 slots; slot 0 is the
  * identity weight and is forced to 1 (y -> 1 as x -> 1, Eq. our_scalar_formula).
- * Exactly one of `host` (FP64, K values shared by every matrix) and `device`
- * (FP32, count x K values, one row per matrix) is non-NULL.  The identity
- * weight of the equivalent D-basis form, 1 + sum w_l, is formed in FP64 on the
- * device. */
+ * Exactly one of `host` (FP64, K values shared by every matrix), `device`
+ * (FP32, count x K values, one row per matrix) and `mlp` is non-NULL.  With
+ * `mlp` (a trained coefficient-proposal network with the same K; L >= 3; BF16
+ * plans) the coefficients are proposed per matrix inside ifnso_orthogonalize
+ * from the features the Gram and the first squaring produce, with the
+ * network's fixed coefficients as the fallback.  The identity weight of the
+ * equivalent D-basis form, 1 + sum w_l, is formed in FP64 on the device. */
+typedef struct ifnso_mlp ifnso_mlp;
+
 typedef struct {
   int32_t K;
   const double* host;
   const float* device;
+  const ifnso_mlp* mlp;
 } ifnso_coeffs;
 
 /* ---------------------------------------------------------------------------
@@ -198,7 +204,9 @@ ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_pass
 /* Testing aid: device pointer and leading dimension (elements) of an h_pad x
  * h_pad intermediate of matrix `index` in a workspace used by
  * ifnso_orthogonalize.  which: 0 = T_0 then P (FP32), 1/2 = D buffer 0 hi/lo
- * (FP16, or FP32 for F32 plans), 3/4 = D buffer 1 hi/lo. */
+ * (FP16, or FP32 for F32 plans), 3/4 = D buffer 1 hi/lo, 5 = the FP32
+ * coefficient row (c_0, w_1..w_L) the proposal network chose for the matrix
+ * (ld = 32). */
 ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch,
                                   void* workspace, int32_t index, int32_t which, void** ptr,
                                   int64_t* ld);
@@ -252,6 +260,71 @@ ifnso_status ifnso_frobenius_norm2_static(const ifnso_batch_desc* batch, ifnso_d
 ifnso_status ifnso_learn_coefficients(int32_t L, int32_t iters, int32_t samples, double lr,
                                       int32_t step_size, double gamma, uint32_t seed,
                                       double* w_out);
+
+/* ---------------------------------------------------------------------------
+ * Coefficient proposal: per-matrix coefficients from spectral features (the
+ * paper's future work on dynamic coefficients, Sec. 4).
+ *
+ * Network (FP32): z = standardised [log tr(D)/h, log tr(D^2)/h, log tr(D^4)/h,
+ * log h, log w, log ||A||_F] (D = A A^T / ||A A^T||_F) -> 64 GELU -> 64 GELU
+ * -> K + 1 outputs.  Outputs 1..L: w_l = wfix_l + s_l out_l with
+ * s_l = max(1, |wfix_l|)/10; output 0 (the identity weight) is projected onto
+ * p(1) = 1; output K predicts log E(proposal) - log E(wfix), and the fixed
+ * coefficients wfix are used whenever it is > 0.  E(c) = (1/h) sum_i
+ * (f_c(x_i) - 1)^2 is the squared distance of Algorithm 1's output to the
+ * polar factor U V^T (per h), exact from the singular values x_i of
+ * X = A / ||A A^T||_F^(1/2).  Parameters: flat FP32 array W1 (64 x 6,
+ * row-major) | b1 (64) | W2 (64 x 64) | b2 (64) | W3 ((K+1) x 64) | b3 (K+1).
+ * The object owns its device memory (parameters, Adam moments, data).
+ * ------------------------------------------------------------------------- */
+
+/* Number of FP32 parameters for K = L + 1 coefficient slots. */
+int32_t ifnso_mlp_param_count(int32_t K);
+
+/* Create a network with K slots (3 <= K <= 31) around the fixed coefficients
+ * wfix (host, K - 1 doubles w_1..w_L).  params (host, ifnso_mlp_param_count
+ * floats) or NULL for a Philox-seeded Gaussian initialisation. */
+ifnso_status ifnso_mlp_create(ifnso_mlp** mlp, int32_t K, const double* wfix, const float* params,
+                              uint32_t seed);
+ifnso_status ifnso_mlp_destroy(ifnso_mlp* mlp);
+
+/* Copy parameters (host, param_count floats) and/or the 12 standardisation
+ * constants (host: 6 means then 6 standard deviations) out of / into the
+ * network; either pointer may be NULL.  Synchronous. */
+ifnso_status ifnso_mlp_get_params(const ifnso_mlp* mlp, float* params, float* stats);
+ifnso_status ifnso_mlp_set_params(ifnso_mlp* mlp, const float* params, const float* stats);
+
+/* Attach a data set of n matrices given by their singular values: sigma
+ * (device, FP32, concatenated), offsets (device, n + 1 int64: matrix i owns
+ * sigma[offsets[i] .. offsets[i+1])), h and w (device int32, n each).  The
+ * features are computed on the device; with fit_standardisation the
+ * standardisation constants are refitted on this set.  Replaces the previous
+ * data set.  Asynchronous on `stream`. */
+ifnso_status ifnso_mlp_set_data(ifnso_mlp* mlp, int32_t n, const float* sigma, const int64_t* offsets,
+                                const int32_t* h, const int32_t* w, int32_t fit_standardisation,
+                                ifnso_stream_t stream);
+
+/* Mean loss over the samples idx[0..batch) (device int32) of the data set,
+ * and its gradient (device, param_count floats), by the forward and backward
+ * kernels.  loss (device, 1 float).  Asynchronous. */
+ifnso_status ifnso_mlp_loss_grad(ifnso_mlp* mlp, const int32_t* idx, int32_t batch, float* grad, float* loss,
+                                 ifnso_stream_t stream);
+
+/* `steps` Adam steps (moments from zero at creation, betas 0.9 / 0.999,
+ * eps 1e-8) of learning rate lr on batches of `batch` samples drawn with
+ * replacement (Philox4x32-10 word 0 of counter (j, step), key (seed,
+ * 0x4D4C5042), modulo n).  loss_curve (device, steps floats) or NULL.
+ * Asynchronous. */
+ifnso_status ifnso_mlp_train(ifnso_mlp* mlp, int32_t steps, int32_t batch, float lr, uint32_t seed,
+                             float* loss_curve, ifnso_stream_t stream);
+
+/* For samples idx[0..n) (device; NULL = 0..n-1): E of the coefficients the
+ * network proposes after the fallback rule (e_mlp), E of the fixed
+ * coefficients (e_fix), the coefficient rows (coeffs, n x K, may be NULL)
+ * and the fallback flags (fallback, may be NULL); all device arrays.
+ * Asynchronous. */
+ifnso_status ifnso_mlp_evaluate(const ifnso_mlp* mlp, const int32_t* idx, int32_t n, float* e_mlp,
+                                float* e_fix, float* coeffs, int32_t* fallback, ifnso_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Synthetic inputs (benchmark and test data; not part of the method)

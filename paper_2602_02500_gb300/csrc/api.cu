@@ -148,7 +148,7 @@ struct Layout {
   int steps = 0;
   std::vector<Shape> shp;
   // metadata
-  size_t off_mats = 0, off_probs = 0, off_items_sym = 0, off_items_app = 0, off_coef = 0;
+  size_t off_mats = 0, off_probs = 0, off_items_sym = 0, off_items_app = 0, off_coef = 0, off_rows = 0;
   size_t n_probs = 0, n_sym = 0, n_app = 0;
   size_t prob_bytes = 0;
   size_t meta_bytes = 0;
@@ -161,6 +161,8 @@ struct Layout {
 };
 
 size_t a64(size_t v) { return (v + 127) & ~size_t(127); }  // 128: the alignment of CUtensorMap
+
+constexpr int kRowSlots = 32;  // FP32 coefficient slots per matrix (K <= 31)
 size_t a1k(size_t v) { return (v + 1023) & ~size_t(1023); }
 
 ifnso_status read_batch(const ifnso_plan* plan, const ifnso_batch_desc* b, std::vector<Shape>& shp) {
@@ -292,6 +294,8 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   off = a64(off + ly.n_app * sizeof(WorkItem));
   ly.off_coef = off;
   off = a64(off + sizeof(double) * (K > 0 ? K : 1));
+  ly.off_rows = off;  // per-matrix coefficient rows written by the proposal network
+  off = a64(off + n * kRowSlots * sizeof(float));
   ly.meta_bytes = off;
   off = a1k(off);
   ly.off_scal = off;
@@ -396,6 +400,7 @@ uint64_t batch_sig(const ifnso_plan* plan, const ifnso_batch_desc* b, void* cons
   if (cf) {
     h = fnv(h, &cf->K, sizeof(cf->K));
     h = fnv(h, &cf->device, sizeof(void*));
+    h = fnv(h, &cf->mlp, sizeof(void*));
     if (cf->host) h = fnv(h, cf->host, sizeof(double) * cf->K);
   }
   if (poly) h = fnv(h, poly, sizeof(double) * (degree == 5 ? 3 : 2));
@@ -753,10 +758,91 @@ Params base_params(uint8_t* ws, const Layout& ly, const ifnso_coeffs* cf) {
   if (cf && cf->device) {
     p.coef.f32 = cf->device;
     p.coef.stride = cf->K;
+  } else if (cf && cf->mlp) {
+    p.coef.f32 = reinterpret_cast<const float*>(ws + ly.off_rows);
+    p.coef.stride = kRowSlots;
   } else {
     p.coef.d64 = reinterpret_cast<const double*>(ws + ly.off_coef);
   }
   return p;
+}
+
+// Philox4x32-10 word pair -> two N(0,1) values (Box-Muller), for the
+// network's initial parameters.
+void host_philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c[0];
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c[2];
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c[1] ^ k0;
+    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c[3] ^ k1;
+    c[1] = static_cast<uint32_t>(p1);
+    c[3] = static_cast<uint32_t>(p0);
+    c[0] = n0;
+    c[2] = n2;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+double host_normal(uint32_t seed, uint32_t i) {
+  uint32_t c[4] = {i, 0u, 0u, 0u};
+  host_philox(c, seed, 0x4D4C5049u);
+  const double u1 = (static_cast<double>(c[0] >> 8) + 0.5) / 16777216.0;
+  const double u2 = (static_cast<double>(c[1] >> 8) + 0.5) / 16777216.0;
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+}  // namespace
+
+struct ifnso_mlp {
+  int K = 0, L = 0, P = 0;
+  float* prm = nullptr;     // device parameters
+  float* mom = nullptr;     // Adam first moments
+  float* vel = nullptr;     // Adam second moments
+  float* wfix = nullptr;    // device w_1..w_L (FP32)
+  float* wslots = nullptr;  // device (1, w_1..w_L): the fixed coefficients as a coefficient row
+  float* scale = nullptr;   // device s_l
+  float* stats = nullptr;   // device 6 means, 6 standard deviations
+  int step = 0;
+  int n = 0;
+  float* xs = nullptr;
+  float* raw = nullptr;
+  float* z = nullptr;
+  int64_t* offs = nullptr;
+  int32_t* hs = nullptr;
+  int cap_batch = 0;
+  int32_t* idx = nullptr;
+  float* grad_part = nullptr;
+  float* loss_part = nullptr;
+  float* grad = nullptr;
+  std::mutex mu;
+};
+
+namespace {
+
+void mlp_free_data(ifnso_mlp* m) {
+  cudaFree(m->xs);
+  cudaFree(m->raw);
+  cudaFree(m->z);
+  cudaFree(m->offs);
+  cudaFree(m->hs);
+  m->xs = m->raw = m->z = nullptr;
+  m->offs = nullptr;
+  m->hs = nullptr;
+  m->n = 0;
+}
+
+ifnso_status mlp_ensure_batch(ifnso_mlp* m, int batch) {
+  if (m->cap_batch >= batch) return IFNSO_OK;
+  cudaFree(m->idx);
+  cudaFree(m->grad_part);
+  cudaFree(m->loss_part);
+  const int blocks = (batch + 31) / 32;
+  IFNSO_CUDA(cudaMalloc(&m->idx, sizeof(int32_t) * batch), "cudaMalloc");
+  IFNSO_CUDA(cudaMalloc(&m->grad_part, sizeof(float) * static_cast<size_t>(blocks) * m->P), "cudaMalloc");
+  IFNSO_CUDA(cudaMalloc(&m->loss_part, sizeof(float) * blocks), "cudaMalloc");
+  m->cap_batch = batch;
+  return IFNSO_OK;
 }
 
 }  // namespace
@@ -882,8 +968,14 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   std::vector<Shape> shp;
   ifnso_status st = read_batch(plan, batch, shp);
   if (st != IFNSO_OK) return st;
-  if (!coeffs || coeffs->K != plan->L + 1 || (!coeffs->host == !coeffs->device))
-    return fail(IFNSO_ERR_INVALID_ARG, "coefficients: need K = %d and exactly one of host/device", plan->L + 1);
+  if (!coeffs || coeffs->K != plan->L + 1 ||
+      (coeffs->host ? 1 : 0) + (coeffs->device ? 1 : 0) + (coeffs->mlp ? 1 : 0) != 1)
+    return fail(IFNSO_ERR_INVALID_ARG, "coefficients: need K = %d and exactly one of host/device/mlp", plan->L + 1);
+  if (coeffs->mlp) {
+    if (coeffs->mlp->K != coeffs->K) return fail(IFNSO_ERR_INVALID_ARG, "coefficient network has K = %d", coeffs->mlp->K);
+    if (plan->L < 3) return fail(IFNSO_ERR_INVALID_ARG, "proposed coefficients need L >= 3");
+    if (plan->dtype != IFNSO_BF16) return fail(IFNSO_ERR_UNSUPPORTED, "proposed coefficients need a BF16 plan");
+  }
   if (!out) return fail(IFNSO_ERR_INVALID_ARG, "out is NULL");
   for (int i = 0; i < batch->count; ++i) {
     if (!out[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is NULL", i);
@@ -956,7 +1048,14 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   p.items = sym;
   p.n_items = static_cast<int32_t>(ly.n_sym);
   IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "Gram pass");
-  IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+  const ifnso_mlp* net = coeffs->mlp;
+  if (net) {
+    // until the network has spoken, the scalars see the fixed coefficients
+    CoefTable fixed{nullptr, net->wslots, coeffs->K, 0};
+    IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, fixed, L, frob, 0, stream), "scalars");
+  } else {
+    IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+  }
   IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 0) return IFNSO_OK;
   // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo)
@@ -974,11 +1073,25 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
     p.final_pass = (j == L - 1);
     p.read_lo = split;
     p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
-    // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
-    // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
-    p.p_mode = j == 1 ? 1 : ((j & 1) ? 2 : (j == L - 1 ? 3 : 0));
+    if (!net) {
+      // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
+      // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
+      p.p_mode = j == 1 ? 1 : ((j & 1) ? 2 : (j == L - 1 ? 3 : 0));
+      p.feat = 0;
+    } else {
+      // proposed coefficients: squaring 1 only measures tr(D_1^4); squaring 2
+      // writes P from T_0, D_2 and D_3; even squarings add D_j and D_{j+1};
+      // an odd last squaring adds D_L
+      p.p_mode = j == 1 ? 0 : (j == 2 ? 4 : ((j & 1) == 0 ? 2 : (j == L - 1 ? 3 : 0)));
+      p.feat = j == 1 ? 1 : 0;
+    }
     IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, ly.n_sym), stream),
                "squaring pass");
+    if (net && j == 1) {
+      IFNSO_CUDA(mlp_infer(net->prm, net->K, net->wfix, net->scale, net->stats, d_mats, p.scal, n,
+                           reinterpret_cast<float*>(ws + ly.off_rows), stream),
+                 "coefficient proposal");
+    }
     IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (plan->stop_after == 1 + j) return IFNSO_OK;
   }
@@ -1169,6 +1282,10 @@ ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc
   *ld = shp[index].hpad;
   if (which == 0) *ptr = mi.gp;
   else if (which >= 1 && which <= 4) *ptr = mi.d[which - 1];
+  else if (which == 5) {
+    *ptr = static_cast<uint8_t*>(workspace) + ly.off_rows + static_cast<size_t>(index) * kRowSlots * sizeof(float);
+    *ld = kRowSlots;
+  }
   else return fail(IFNSO_ERR_INVALID_ARG, "which = %d", which);
   if (!*ptr) return fail(IFNSO_ERR_INVALID_ARG, "buffer %d is not used by this plan", which);
   return IFNSO_OK;
@@ -1240,6 +1357,167 @@ ifnso_status ifnso_synth_lowrank_bf16(void* out, int64_t rows, int64_t cols, int
   if ((rows + 31) / 32 > 65535) return fail(IFNSO_ERR_INVALID_ARG, "synth: too many rows");
   IFNSO_CUDA(launch_synth_lowrank(out, rows, cols, ld, seed, alpha, beta, reinterpret_cast<cudaStream_t>(stream_)),
              "synth");
+  return IFNSO_OK;
+}
+
+// ------------------------------------------------------------------ coefficient proposal
+
+int32_t ifnso_mlp_param_count(int32_t K) { return (K >= 2 && K <= 31) ? mlp_param_count(K) : 0; }
+
+ifnso_status ifnso_mlp_create(ifnso_mlp** out, int32_t K, const double* wfix, const float* params, uint32_t seed) {
+  if (!out || !wfix || K < 3 || K > 31) return fail(IFNSO_ERR_INVALID_ARG, "mlp: K must be in [3, 31] and wfix given");
+  *out = nullptr;
+  ifnso_mlp* m = new (std::nothrow) ifnso_mlp();
+  if (!m) return fail(IFNSO_ERR_OOM, "out of host memory");
+  m->K = K;
+  m->L = K - 1;
+  m->P = mlp_param_count(K);
+  const int P = m->P, L = m->L, NO = K + 1;
+  std::vector<float> init(P, 0.f);
+  if (params) {
+    memcpy(init.data(), params, sizeof(float) * P);
+  } else {
+    // W1 ~ N(0, 1/6), W2 ~ N(0, 1/64), W3 ~ 0.01 N(0, 1/64), biases 0
+    const int oW1 = 0, ob1 = 64 * 6, oW2 = ob1 + 64, ob2 = oW2 + 64 * 64, oW3 = ob2 + 64;
+    uint32_t i = 0;
+    for (int k = 0; k < 64 * 6; ++k) init[oW1 + k] = static_cast<float>(host_normal(seed, i++) / std::sqrt(6.0));
+    for (int k = 0; k < 64 * 64; ++k) init[oW2 + k] = static_cast<float>(host_normal(seed, i++) / 8.0);
+    for (int k = 0; k < NO * 64; ++k) init[oW3 + k] = static_cast<float>(0.01 * host_normal(seed, i++) / 8.0);
+  }
+  std::vector<float> wf(L), ws(K), sc(L), st(12);
+  for (int l = 0; l < L; ++l) {
+    wf[l] = static_cast<float>(wfix[l]);
+    ws[1 + l] = wf[l];
+    sc[l] = static_cast<float>(std::max(1.0, std::fabs(wfix[l])) / 10.0);
+  }
+  ws[0] = 1.f;
+  for (int f = 0; f < 6; ++f) {
+    st[f] = 0.f;
+    st[6 + f] = 1.f;
+  }
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](float** p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc(p, n * sizeof(float));
+  };
+  alloc(&m->prm, P);
+  alloc(&m->mom, P);
+  alloc(&m->vel, P);
+  alloc(&m->grad, P);
+  alloc(&m->wfix, L);
+  alloc(&m->wslots, K);
+  alloc(&m->scale, L);
+  alloc(&m->stats, 12);
+  if (e == cudaSuccess) e = cudaMemcpy(m->prm, init.data(), sizeof(float) * P, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->mom, 0, sizeof(float) * P);
+  if (e == cudaSuccess) e = cudaMemset(m->vel, 0, sizeof(float) * P);
+  if (e == cudaSuccess) e = cudaMemcpy(m->wfix, wf.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->wslots, ws.data(), sizeof(float) * K, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->scale, sc.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->stats, st.data(), sizeof(float) * 12, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ifnso_mlp_destroy(m);
+    return cuda_fail(e, "mlp create");
+  }
+  *out = m;
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_destroy(ifnso_mlp* m) {
+  if (!m) return IFNSO_OK;
+  cudaDeviceSynchronize();
+  mlp_free_data(m);
+  for (float* p : {m->prm, m->mom, m->vel, m->grad, m->wfix, m->wslots, m->scale, m->stats, m->grad_part,
+                   m->loss_part})
+    cudaFree(p);
+  cudaFree(m->idx);
+  delete m;
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_get_params(const ifnso_mlp* m, float* params, float* stats) {
+  if (!m) return fail(IFNSO_ERR_INVALID_ARG, "mlp is NULL");
+  IFNSO_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  if (params) IFNSO_CUDA(cudaMemcpy(params, m->prm, sizeof(float) * m->P, cudaMemcpyDeviceToHost), "copy");
+  if (stats) IFNSO_CUDA(cudaMemcpy(stats, m->stats, sizeof(float) * 12, cudaMemcpyDeviceToHost), "copy");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_set_params(ifnso_mlp* m, const float* params, const float* stats) {
+  if (!m) return fail(IFNSO_ERR_INVALID_ARG, "mlp is NULL");
+  IFNSO_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  if (params) IFNSO_CUDA(cudaMemcpy(m->prm, params, sizeof(float) * m->P, cudaMemcpyHostToDevice), "copy");
+  if (stats) IFNSO_CUDA(cudaMemcpy(m->stats, stats, sizeof(float) * 12, cudaMemcpyHostToDevice), "copy");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_set_data(ifnso_mlp* m, int32_t n, const float* sigma, const int64_t* offsets,
+                                const int32_t* h, const int32_t* w, int32_t fit, ifnso_stream_t stream_) {
+  if (!m || n <= 0 || !sigma || !offsets || !h || !w) return fail(IFNSO_ERR_INVALID_ARG, "mlp_set_data: bad argument");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(m->mu);
+  IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  mlp_free_data(m);
+  int64_t total = 0;
+  IFNSO_CUDA(cudaMemcpy(&total, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost), "copy");
+  if (total <= 0) return fail(IFNSO_ERR_INVALID_ARG, "mlp_set_data: empty data set");
+  IFNSO_CUDA(cudaMalloc(&m->xs, sizeof(float) * total), "cudaMalloc");
+  IFNSO_CUDA(cudaMalloc(&m->raw, sizeof(float) * 8 * n), "cudaMalloc");
+  IFNSO_CUDA(cudaMalloc(&m->z, sizeof(float) * 8 * n), "cudaMalloc");
+  IFNSO_CUDA(cudaMalloc(&m->offs, sizeof(int64_t) * (n + 1)), "cudaMalloc");
+  IFNSO_CUDA(cudaMalloc(&m->hs, sizeof(int32_t) * n), "cudaMalloc");
+  IFNSO_CUDA(cudaMemcpyAsync(m->offs, offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, stream), "copy");
+  IFNSO_CUDA(cudaMemcpyAsync(m->hs, h, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, stream), "copy");
+  m->n = n;
+  IFNSO_CUDA(mlp_prepare(n, sigma, m->offs, m->hs, w, m->xs, m->raw, m->stats, fit, m->z, stream), "mlp features");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_loss_grad(ifnso_mlp* m, const int32_t* idx, int32_t batch, float* grad, float* loss,
+                                 ifnso_stream_t stream_) {
+  if (!m || !idx || batch <= 0) return fail(IFNSO_ERR_INVALID_ARG, "mlp_loss_grad: bad argument");
+  if (m->n == 0) return fail(IFNSO_ERR_INVALID_ARG, "mlp_loss_grad: no data set");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(m->mu);
+  ifnso_status st = mlp_ensure_batch(m, batch);
+  if (st != IFNSO_OK) return st;
+  IFNSO_CUDA(mlp_grad(m->prm, m->K, m->wfix, m->scale, m->z, m->xs, m->offs, m->hs, idx, batch, m->grad_part,
+                      m->loss_part, stream),
+             "mlp forward/backward");
+  IFNSO_CUDA(mlp_reduce_adam(m->K, batch, m->grad_part, m->loss_part, grad, loss, m->prm, m->mom, m->vel, 0, 0.f, 0,
+                             stream),
+             "mlp reduce");
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_train(ifnso_mlp* m, int32_t steps, int32_t batch, float lr, uint32_t seed, float* loss_curve,
+                             ifnso_stream_t stream_) {
+  if (!m || steps < 0 || batch <= 0) return fail(IFNSO_ERR_INVALID_ARG, "mlp_train: bad argument");
+  if (m->n == 0) return fail(IFNSO_ERR_INVALID_ARG, "mlp_train: no data set");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(m->mu);
+  ifnso_status st = mlp_ensure_batch(m, batch);
+  if (st != IFNSO_OK) return st;
+  for (int s = 0; s < steps; ++s) {
+    ++m->step;
+    IFNSO_CUDA(mlp_batch_idx(batch, m->step, seed, m->n, m->idx, stream), "mlp batch");
+    IFNSO_CUDA(mlp_grad(m->prm, m->K, m->wfix, m->scale, m->z, m->xs, m->offs, m->hs, m->idx, batch, m->grad_part,
+                        m->loss_part, stream),
+               "mlp forward/backward");
+    IFNSO_CUDA(mlp_reduce_adam(m->K, batch, m->grad_part, m->loss_part, m->grad, loss_curve ? loss_curve + s : nullptr,
+                               m->prm, m->mom, m->vel, m->step, lr, 1, stream),
+               "mlp adam");
+  }
+  return IFNSO_OK;
+}
+
+ifnso_status ifnso_mlp_evaluate(const ifnso_mlp* m, const int32_t* idx, int32_t n, float* e_mlp, float* e_fix,
+                                float* coeffs, int32_t* fallback, ifnso_stream_t stream_) {
+  if (!m || n <= 0 || !e_mlp || !e_fix) return fail(IFNSO_ERR_INVALID_ARG, "mlp_evaluate: bad argument");
+  if (m->n == 0) return fail(IFNSO_ERR_INVALID_ARG, "mlp_evaluate: no data set");
+  if (!idx && n > m->n) return fail(IFNSO_ERR_INVALID_ARG, "mlp_evaluate: n exceeds the data set");
+  IFNSO_CUDA(mlp_eval(m->prm, m->K, m->wfix, m->scale, m->z, m->xs, m->offs, m->hs, idx, n, e_mlp, e_fix, coeffs,
+                      fallback, reinterpret_cast<cudaStream_t>(stream_)),
+             "mlp evaluate");
   return IFNSO_OK;
 }
 

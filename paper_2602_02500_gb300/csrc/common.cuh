@@ -97,7 +97,10 @@ struct TcParams {
   int32_t write_lo;    // EPI_SQR: store D_{l+1} as hi + lo (the next pass is split)
   int32_t p_split;     // EPI_SQR final pass / prep: store P as BF16 hi + lo
   int32_t p_mode;      // EPI_SQR: 0 P untouched, 1 P written from c0 I and two terms,
-                       // 2 P read and two terms subtracted, 3 P read and one term subtracted
+                       // 2 P read and two terms subtracted, 3 P read and one term subtracted,
+                       // 4 P written from c0 I, w_1 T_0 / o (read) and two terms
+  int32_t feat;        // EPI_SQR: accumulate sum (D_l^2)_ij^2 into MatScalars::spare[0]
+  int32_t pad2;
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;
@@ -163,6 +166,23 @@ cudaError_t launch_learn(int L, int iters, int samples, double lr, int step_size
                          uint32_t seed, double cL, double* d_w, cudaStream_t s);
 cudaError_t launch_synth_lowrank(void* out, int64_t rows, int64_t cols, int64_t ld, uint32_t seed,
                                  float alpha, float beta, cudaStream_t s);
+
+// coefficient-proposal MLP (mlp.cu)
+int mlp_param_count(int K);
+cudaError_t mlp_prepare(int n, const float* sigma, const int64_t* offs, const int32_t* hs, const int32_t* ws,
+                        float* xs, float* raw, float* stats, int fit, float* z, cudaStream_t s);
+cudaError_t mlp_grad(const float* prm, int K, const float* wfix, const float* scale, const float* z,
+                     const float* xs, const int64_t* offs, const int32_t* hs, const int32_t* idx, int batch,
+                     float* grad_part, float* loss_part, cudaStream_t s);
+cudaError_t mlp_reduce_adam(int K, int batch, const float* grad_part, const float* loss_part, float* grad_out,
+                            float* loss_out, float* prm, float* m, float* v, int step, float lr, int do_adam,
+                            cudaStream_t s);
+cudaError_t mlp_batch_idx(int batch, int step, uint32_t seed, int n, int32_t* idx, cudaStream_t s);
+cudaError_t mlp_eval(const float* prm, int K, const float* wfix, const float* scale, const float* z, const float* xs,
+                     const int64_t* offs, const int32_t* hs, const int32_t* idx, int n, float* e_mlp, float* e_fix,
+                     float* coef_out, int32_t* fallback, cudaStream_t s);
+cudaError_t mlp_infer(const float* prm, int K, const float* wfix, const float* scale, const float* stats,
+                      const MatInfo* mats, MatScalars* scal, int n, float* coef_rows, cudaStream_t s);
 
 void count_launch(int n = 1);
 

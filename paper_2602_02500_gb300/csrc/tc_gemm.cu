@@ -60,6 +60,12 @@ struct Products {
 
 __device__ __forceinline__ float u2f(uint32_t u) { return __uint_as_float(u); }
 
+__device__ __forceinline__ float warp_reduce_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ void set_timeout(MatScalars* scal, int mat) {
   atomicOr(&scal[mat].status, kDevTimeout);
 }
@@ -273,12 +279,33 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     // p_mode 1 (first squaring) writes P = c0 I - w_l D_l - w_{l+1} D_{l+1},
     // p_mode 2 subtracts w_l D_l + w_{l+1} D_{l+1}, p_mode 3 only
     // w_{l+1} D_{l+1} (last squaring after an even count), p_mode 0 leaves P.
+    if (p.feat) {
+      // sum of (D_1^2)_ij^2 = tr(D_1^4), a feature of the coefficient proposal
+#pragma unroll
+      for (int j = 0; j < 32; ++j) ea.ss = fmaf(v[j], v[j], ea.ss);
+    }
     const float w = static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l));
-    const float wp = (p.p_mode == 1 || p.p_mode == 2)
+    const float wp = (p.p_mode == 1 || p.p_mode == 2 || p.p_mode == 4)
                          ? static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l - 1)) : 0.f;
     float* P = pr.pacc + off;
     float pv[32];
-    if (p.p_mode >= 2) {
+    if (p.p_mode == 4) {
+      // P = c0 I - w_1 D_1 - w_l D_l - w_{l+1} D_{l+1} with D_1 = T_0 / o read
+      // from the T_0 buffer (coefficients known only after the first squaring)
+      const float c0f = static_cast<float>(p.scal[pr.mat].c0);
+      const float w1 = static_cast<float>(coef_at(p.coef, pr.mat, 1));
+      const float inv = p.scal[pr.mat].inv_s2;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float4 t = reinterpret_cast<const float4*>(P)[j];
+        pv[4 * j] = t.x;
+        pv[4 * j + 1] = t.y;
+        pv[4 * j + 2] = t.z;
+        pv[4 * j + 3] = t.w;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) pv[j] = fmaf(-w1, pv[j] * inv, (c0 + j == r) ? c0f : 0.f);
+    } else if (p.p_mode >= 2) {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         float4 t = reinterpret_cast<const float4*>(P)[j];
@@ -578,6 +605,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const double wgt = (wi.flags & 1) ? 1.0 : 2.0;  // off-diagonal blocks stand for two
           atomicAdd(&p.scal[pr.mat].o2, wgt * static_cast<double>(ss));
           if (tr != 0.f) atomicAdd(&p.scal[pr.mat].trace, static_cast<double>(tr));
+        }
+      }
+      if constexpr (EPI == EPI_SQR) {
+        if (p.feat) {
+          const float ss = warp_reduce_sum(ea.ss);
+          if (lane == 0)
+            atomicAdd(&p.scal[pr.mat].spare[0], ((wi.flags & 1) ? 1.0 : 2.0) * static_cast<double>(ss));
         }
       }
     }

@@ -45,7 +45,9 @@ EXPORTED = [
     "ifnso_workspace_bytes", "ifnso_orthogonalize", "ns_iterate", "ns_workspace_bytes",
     "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
     "ifnso_frobenius_norm2_static", "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
-    "ifnso_launch_count",
+    "ifnso_launch_count", "ifnso_mlp_param_count", "ifnso_mlp_create", "ifnso_mlp_destroy",
+    "ifnso_mlp_get_params", "ifnso_mlp_set_params", "ifnso_mlp_set_data", "ifnso_mlp_loss_grad",
+    "ifnso_mlp_train", "ifnso_mlp_evaluate",
 ]
 
 
@@ -55,7 +57,7 @@ class ifnso_batch_desc(C.Structure):
 
 
 class ifnso_coeffs(C.Structure):
-    _fields_ = [("K", C.c_int32), ("host", C.POINTER(C.c_double)), ("device", C.c_void_p)]
+    _fields_ = [("K", C.c_int32), ("host", C.POINTER(C.c_double)), ("device", C.c_void_p), ("mlp", C.c_void_p)]
 
 
 _P = C.c_void_p
@@ -81,6 +83,15 @@ _sig = {
     "ifnso_learn_coefficients": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_double,
                                            C.c_uint32, C.POINTER(C.c_double)]),
     "ifnso_synth_lowrank_bf16": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, C.c_uint32, C.c_float, C.c_float, _P]),
+    "ifnso_mlp_param_count": (C.c_int32, [C.c_int32]),
+    "ifnso_mlp_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.POINTER(C.c_double), _P, C.c_uint32]),
+    "ifnso_mlp_destroy": (C.c_int, [_P]),
+    "ifnso_mlp_get_params": (C.c_int, [_P, _P, _P]),
+    "ifnso_mlp_set_params": (C.c_int, [_P, _P, _P]),
+    "ifnso_mlp_set_data": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_int32, _P]),
+    "ifnso_mlp_loss_grad": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P]),
+    "ifnso_mlp_train": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_float, C.c_uint32, _P, _P]),
+    "ifnso_mlp_evaluate": (C.c_int, [_P, _P, C.c_int32, _P, _P, _P, _P, _P]),
     "ifnso_last_error": (C.c_char_p, []),
     "ifnso_launch_count": (C.c_uint64, []),
 }
@@ -229,13 +240,16 @@ class Plan:
             if coeffs.dtype != torch.float32 or coeffs.shape != (batch.desc.count, K) or not coeffs.is_contiguous():
                 raise ValueError("device coefficients must be contiguous float32 of shape (count, L + 1)")
             self._cf_keep = coeffs
-            cf = ifnso_coeffs(K, None, C.c_void_p(coeffs.data_ptr()))
+            cf = ifnso_coeffs(K, None, C.c_void_p(coeffs.data_ptr()), None)
+        elif isinstance(coeffs, Mlp):
+            self._cf_keep = coeffs
+            cf = ifnso_coeffs(K, None, None, coeffs.handle)
         else:
             arr = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
             if arr.shape != (K,):
                 raise ValueError(f"host coefficients must have K = {K} values")
             self._cf_keep = arr
-            cf = ifnso_coeffs(K, arr.ctypes.data_as(C.POINTER(C.c_double)), None)
+            cf = ifnso_coeffs(K, arr.ctypes.data_as(C.POINTER(C.c_double)), None, None)
         need = self.workspace_bytes(batch)
         if ws is None:
             ws = self.workspace(need)
@@ -284,6 +298,81 @@ class Plan:
         check(ifnso_workspace_view(self.handle, batch.ref(), C.c_void_p(ws.ptr), index, which, C.byref(p),
                                    C.byref(ld)), "ifnso_workspace_view")
         return p.value, ld.value
+
+
+class Mlp:
+    """ifnso_mlp: the coefficient-proposal network (K = L + 1 slots)."""
+
+    def __init__(self, K, wfix, params=None, seed=0):
+        self.K = int(K)
+        self.P = int(ifnso_mlp_param_count(self.K))
+        wf = np.ascontiguousarray(np.asarray(wfix, dtype=np.float64))
+        assert wf.shape == (self.K - 1,)
+        h = C.c_void_p()
+        pp = None
+        if params is not None:
+            self._p0 = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+            pp = C.c_void_p(self._p0.ctypes.data)
+        check(ifnso_mlp_create(C.byref(h), self.K, wf.ctypes.data_as(C.POINTER(C.c_double)), pp, int(seed)),
+              "ifnso_mlp_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ifnso_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        p = np.zeros(self.P, dtype=np.float32)
+        st = np.zeros(12, dtype=np.float32)
+        check(ifnso_mlp_get_params(self.handle, C.c_void_p(p.ctypes.data), C.c_void_p(st.ctypes.data)),
+              "ifnso_mlp_get_params")
+        return p, st
+
+    def set_params(self, params=None, stats=None):
+        pp = None if params is None else np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        ss = None if stats is None else np.ascontiguousarray(np.asarray(stats, dtype=np.float32))
+        check(ifnso_mlp_set_params(self.handle, None if pp is None else C.c_void_p(pp.ctypes.data),
+                                   None if ss is None else C.c_void_p(ss.ctypes.data)), "ifnso_mlp_set_params")
+
+    def set_data(self, sigma, offsets, h, w, fit=True, stream=None):
+        """sigma: CUDA float32 (concatenated), offsets: CUDA int64 (n + 1), h, w: CUDA int32 (n)."""
+        self._data = (sigma, offsets, h, w)
+        check(ifnso_mlp_set_data(self.handle, int(h.numel()), C.c_void_p(sigma.data_ptr()),
+                                 C.c_void_p(offsets.data_ptr()), C.c_void_p(h.data_ptr()), C.c_void_p(w.data_ptr()),
+                                 1 if fit else 0, _stream(stream)), "ifnso_mlp_set_data")
+
+    def loss_grad(self, idx, stream=None):
+        torch = _torch()
+        g = torch.empty(self.P, dtype=torch.float32, device=idx.device)
+        loss = torch.empty(1, dtype=torch.float32, device=idx.device)
+        check(ifnso_mlp_loss_grad(self.handle, C.c_void_p(idx.data_ptr()), int(idx.numel()), C.c_void_p(g.data_ptr()),
+                                  C.c_void_p(loss.data_ptr()), _stream(stream)), "ifnso_mlp_loss_grad")
+        return g, loss
+
+    def train(self, steps, batch=256, lr=1e-3, seed=0, stream=None):
+        torch = _torch()
+        curve = torch.empty(max(int(steps), 1), dtype=torch.float32, device="cuda")
+        check(ifnso_mlp_train(self.handle, int(steps), int(batch), float(lr), int(seed), C.c_void_p(curve.data_ptr()),
+                              _stream(stream)), "ifnso_mlp_train")
+        return curve[:steps]
+
+    def evaluate(self, n, idx=None, stream=None):
+        torch = _torch()
+        e1 = torch.empty(n, dtype=torch.float32, device="cuda")
+        e0 = torch.empty(n, dtype=torch.float32, device="cuda")
+        cf = torch.empty((n, self.K), dtype=torch.float32, device="cuda")
+        fb = torch.empty(n, dtype=torch.int32, device="cuda")
+        check(ifnso_mlp_evaluate(self.handle, None if idx is None else C.c_void_p(idx.data_ptr()), int(n),
+                                 C.c_void_p(e1.data_ptr()), C.c_void_p(e0.data_ptr()), C.c_void_p(cf.data_ptr()),
+                                 C.c_void_p(fb.data_ptr()), _stream(stream)), "ifnso_mlp_evaluate")
+        return e1, e0, cf, fb
 
 
 def tensor_at(ptr, shape, dtype, owner):

@@ -170,7 +170,47 @@ def learner_uniforms(seed: int, iteration: int, count: int) -> np.ndarray:
     return uniform53(w0, w1)
 
 
+# --- spectra of the coefficient-proposal training set -----------------------
+
+MLP_FAMILIES = ("loguniform", "powerlaw", "clustered")
+
+
+def mlp_spectrum(seed: int):
+    """One synthetic matrix of the coefficient-proposal data set, as a spectrum.
+
+    h ~ U{64..1024}; w = round(h r), r ~ U[1, 4]; family chosen uniformly:
+      loguniform  sigma_i = 10^U(-4, 0)
+      powerlaw    sigma_i = i^-alpha, alpha ~ U[0.5, 2]
+      clustered   2..4 centres 10^U(-4, 0), sigma = centre * exp(0.1 N(0, 1))
+    times an overall scale 10^U(-2, 2).  Returns (h, w, sigma sorted
+    descending, family index).
+    """
+    rng = np.random.default_rng(seed)
+    h = int(rng.integers(64, 1025))
+    w = int(round(h * rng.uniform(1.0, 4.0)))
+    fam = int(rng.integers(0, 3))
+    if fam == 0:
+        sig = 10.0 ** rng.uniform(-4.0, 0.0, size=h)
+    elif fam == 1:
+        alpha = rng.uniform(0.5, 2.0)
+        sig = np.arange(1, h + 1, dtype=np.float64) ** (-alpha)
+    else:
+        k = int(rng.integers(2, 5))
+        centres = 10.0 ** rng.uniform(-4.0, 0.0, size=k)
+        which = rng.integers(0, k, size=h)
+        sig = centres[which] * np.exp(0.1 * rng.standard_normal(h))
+    sig = np.sort(sig)[::-1] * 10.0 ** rng.uniform(-2.0, 2.0)
+    return h, w, sig.copy(), fam
+
+
+def mlp_matrix(seed: int):
+    """The matrix U diag(sigma) V^T (h x w) of ``mlp_spectrum(seed)``, FP64."""
+    h, w, sig, fam = mlp_spectrum(seed)
+    return spectral(seed + 17, h, w, sig)
+
+
 __all__ = [
+    "MLP_FAMILIES", "mlp_spectrum", "mlp_matrix",
     "gaussian", "haar_stiefel", "spectral", "loguniform_sigma", "to_bf16_bits",
     "bf16_bits_to_f64", "round_bf16", "lowrank_constants", "lowrank_factor",
     "lowrank_noise_int", "lowrank_noise_f32", "lowrank_noise_bf16", "transformer_list",
