@@ -1089,7 +1089,7 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
                "squaring pass");
     if (net && j == 1) {
       IFNSO_CUDA(mlp_infer(net->prm, net->K, net->wfix, net->scale, net->stats, d_mats, p.scal, n,
-                           reinterpret_cast<float*>(ws + ly.off_rows), stream),
+                           reinterpret_cast<float*>(ws + ly.off_rows), kRowSlots, stream),
                  "coefficient proposal");
     }
     IFNSO_CUDA(mark(plan, stream, false), "timing event");

@@ -182,7 +182,7 @@ cudaError_t mlp_eval(const float* prm, int K, const float* wfix, const float* sc
                      const int64_t* offs, const int32_t* hs, const int32_t* idx, int n, float* e_mlp, float* e_fix,
                      float* coef_out, int32_t* fallback, cudaStream_t s);
 cudaError_t mlp_infer(const float* prm, int K, const float* wfix, const float* scale, const float* stats,
-                      const MatInfo* mats, MatScalars* scal, int n, float* coef_rows, cudaStream_t s);
+                      const MatInfo* mats, MatScalars* scal, int n, float* coef_rows, int row_stride, cudaStream_t s);
 
 void count_launch(int n = 1);
 

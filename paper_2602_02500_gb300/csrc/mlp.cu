@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256) k_mlp_eval(const float* prm, int K, int L
 // identity weight c0 = 1 + sum w_l (FP64).
 __global__ void __launch_bounds__(256) k_mlp_infer(const float* prm, int K, int L, const float* wfix,
                                                    const float* scale, const float* stats, const MatInfo* mats,
-                                                   MatScalars* scal, int n, float* coef_rows) {
+                                                   MatScalars* scal, int n, float* coef_rows, int row_stride) {
   extern __shared__ float sm[];
   const Offs o(K);
   float* W2s = sm;
@@ -473,11 +473,11 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* prm, int K, int 
   for (int l = 0; l < L; ++l) {
     float wl = fb ? wfix[l] : wfix[l] + scale[l] * out[1 + l];
     if (!isfinite(wl)) wl = wfix[l];
-    if (lane == 0) coef_rows[static_cast<int64_t>(m) * K + 1 + l] = wl;
+    if (lane == 0) coef_rows[static_cast<int64_t>(m) * row_stride + 1 + l] = wl;
     c0 += static_cast<double>(wl);
   }
   if (lane == 0) {
-    coef_rows[static_cast<int64_t>(m) * K] = 1.f;
+    coef_rows[static_cast<int64_t>(m) * row_stride] = 1.f;
     scal[m].c0 = c0;
     scal[m].spare[1] = fb ? 1.0 : 0.0;
   }
@@ -556,7 +556,7 @@ cudaError_t mlp_eval(const float* prm, int K, const float* wfix, const float* sc
 }
 
 cudaError_t mlp_infer(const float* prm, int K, const float* wfix, const float* scale, const float* stats,
-                      const MatInfo* mats, MatScalars* scal, int n, float* coef_rows, cudaStream_t s) {
+                      const MatInfo* mats, MatScalars* scal, int n, float* coef_rows, int row_stride, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -564,7 +564,8 @@ cudaError_t mlp_infer(const float* prm, int K, const float* wfix, const float* s
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_mlp_infer<<<(n + 7) / 8, 256, eval_smem(), s>>>(prm, K, K - 1, wfix, scale, stats, mats, scal, n, coef_rows);
+  k_mlp_infer<<<(n + 7) / 8, 256, eval_smem(), s>>>(prm, K, K - 1, wfix, scale, stats, mats, scal, n, coef_rows,
+                                                    row_stride);
   count_launch();
   return cudaGetLastError();
 }
