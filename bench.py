@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="time eager calls instead of a captured CUDA graph of one step")
     return ap.parse_args()
 
 
@@ -82,6 +84,28 @@ def workload_list(wl):
 
 def oriented(r, c):
     return (min(r, c), max(r, c))
+
+
+def rank_seed0(rank):
+    """First seed of rank `rank`'s list: every rank orthogonalises its own list
+    of independent matrices (weak scaling, no data-path collective)."""
+    return rank * 100000
+
+
+def max_over_ranks_of(dist, value, device):
+    """The largest of the ranks' values (the whole job ends with the slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, ms_max):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank * steps / (ms_max / 1000.0)
 
 
 def load_peaks():
@@ -278,11 +302,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(dist, v, device)
 
     wl = WORKLOADS[args.workload]
     shapes = workload_list(wl)
@@ -291,7 +311,7 @@ def main():
     hw = [oriented(r, c) for _, r, c in shapes]
     hmax = max(h for h, _ in hw)
     wmax = max(w for _, w in hw)
-    seed0 = rank * 100000
+    seed0 = rank_seed0(rank)
     xs = make_inputs(F, torch, shapes, seed0, device)
     ys = [torch.empty_like(x) for x in xs]
     batch = F.Batch(xs)
@@ -312,6 +332,23 @@ def main():
     if np.any(st & F.IFNSO_DEV_TIMEOUT):
         raise RuntimeError("device wait timed out during warm-up")
 
+    def make_step(fn):
+        """The step as a CUDA graph replay (captured once, after warm-up) or as
+        eager calls; returns (callable, launches per step or None)."""
+        if not args.graph:
+            return fn, None
+        n_before = F.launch_count()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        return g.replay, F.launch_count() - n_before
+
+    ifnso_step, ifnso_launches = make_step(lambda: plan.orthogonalize(batch, coef, ys, ws=ws))
+    ifnso_step()
+    torch.cuda.synchronize()
+    plan.pass_times()
+
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
@@ -321,40 +358,51 @@ def main():
     n0 = F.launch_count()
     e0.record(stream)
     for _ in range(args.steps):
-        plan.orthogonalize(batch, coef, ys, ws=ws)
+        ifnso_step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    launches = F.launch_count() - n0
+    launches = ifnso_launches * args.steps if ifnso_launches is not None else F.launch_count() - n0
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     clk = clocks.stop()
     pass_ms, calls = plan.pass_times()
     ms_step = ms_total / args.steps
-    value = world * n * args.steps / (ms_total / 1000.0)
+    value = whole_job_rate(world, n, args.steps, ms_total)
     fl = sum(flops_ifnso(h, w, L) for h, w in hw)
     tflops = world * fl * args.steps / (ms_total / 1000.0) / 1e12
 
-    # the dominant kernel: the squaring pass (L - 1 launches per step)
+    # the dominant kernel: the squaring pass with split operands (the first k of
+    # the L - 1 squarings; the others run with plain FP16 operands)
     peaks, peak_src = load_peaks()
-    sq = pass_ms[2:2 + (L - 1)] if L > 1 else np.array([])
-    sq_launch_ms = float(np.sum(sq)) / max(1, calls * (L - 1)) if L > 1 else None
+    mode = plan.get(F.IFNSO_OPT_PRECISION)
+    k_split = {F.IFNSO_PREC_SPLIT: L - 1, F.IFNSO_PREC_MIXED: max(0, L - 8)}.get(mode, 0)
+    per_step = [float(x) / max(1, calls) for x in pass_ms]
+    sq = per_step[2:2 + (L - 1)] if L > 1 else []
+    sq_split, sq_plain = sq[:k_split], sq[k_split:]
     sq_alg = sum(2 * h ** 3 for h, _ in hw)  # algorithmic FLOPs per squaring launch
-    split = plan.get(F.IFNSO_OPT_PRECISION) == F.IFNSO_PREC_SPLIT
     hp = [((h + 255) // 256) * 256 for h, _ in hw]
-    sq_exec = sum(((p // 256) * (p // 256 + 1) // 2) * 2 * (2 * 128 * 256 * p) * (3 if split else 1) for p in hp)
-    traffic = load_traffic().get(f"{args.workload}:squaring")
+    exec_one = sum(((p // 256) * (p // 256 + 1) // 2) * 2 * (2 * 128 * 256 * p) for p in hp)
+    dominant = "split" if sum(sq_split) >= sum(sq_plain) else "plain"
+    dom = sq_split if dominant == "split" else sq_plain
+    sq_launch_ms = float(np.mean(dom)) if dom else None
+    sq_exec = exec_one * (3 if dominant == "split" else 1)
+    traffic = load_traffic().get(f"{args.workload}:squaring_{dominant}")
     roof = None
     if sq_launch_ms:
         ach = sq_alg / (sq_launch_ms / 1000.0) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic,
-                "kernel": "tc_gemm_kernel squaring pass (D_{l+1} = 2 D_l - D_l^2, P -= w D_{l+1})",
-                "launch_ms": sq_launch_ms, "algorithmic_flop_per_launch": sq_alg,
-                "executed_flop_per_launch": sq_exec,
+                "kernel": f"tc_gemm_kernel squaring pass, {dominant} operands "
+                          "(D_{l+1} = 2 D_l - D_l^2 with the P update fused)",
+                "launch_ms": sq_launch_ms, "launches_per_step": len(dom),
+                "algorithmic_flop_per_launch": sq_alg, "executed_flop_per_launch": sq_exec,
                 "executed_tflops": sq_exec / (sq_launch_ms / 1000.0) / 1e12,
                 "peak_source": f"bf16_tflops_sustained ({peak_src})",
-                "pass_ms_per_step": [float(x) / max(1, calls) for x in pass_ms]}
+                "squarings": {"split": len(sq_split), "plain": len(sq_plain),
+                              "split_ms": float(np.mean(sq_split)) if sq_split else None,
+                              "plain_ms": float(np.mean(sq_plain)) if sq_plain else None},
+                "pass_ms_per_step": per_step}
 
     # 5-step quintic Newton-Schulz on the same list
     nsplan = F.Plan(hmax, wmax, "bf16", L=1)
@@ -363,15 +411,18 @@ def main():
     for _ in range(max(args.warmup, 3)):
         nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
     torch.cuda.synchronize()
+    ns_step, _ = make_step(lambda: nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws))
+    ns_step()
+    torch.cuda.synchronize()
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
+        ns_step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ns_ms = max_over_ranks(e0.elapsed_time(e1))
-    ns_value = world * n * args.steps / (ns_ms / 1000.0)
+    ns_value = whole_job_rate(world, n, args.steps, ns_ms)
     ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
     del nsws, zs
 
@@ -402,7 +453,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1))
-        e2e = {"value": world * n * args.steps / (e2e_ms / 1000.0), "unit": "matrices/s",
+        e2e = {"value": whole_job_rate(world, n, args.steps, e2e_ms), "unit": "matrices/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "ms_per_step": e2e_ms / args.steps}
         plan.pass_times()
 
@@ -417,9 +468,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": args.workload + ": " + wl["desc"], "L": L,
-                       "precision": "split fp16/bf16 hi+lo operands" if split else "plain",
+                       "precision": {F.IFNSO_PREC_PLAIN: "plain FP16 squarings, BF16 P",
+                                     F.IFNSO_PREC_SPLIT: "split FP16 hi+lo squarings, BF16 hi+lo P",
+                                     F.IFNSO_PREC_MIXED: f"mixed: first {k_split} squarings split FP16 hi+lo, "
+                                                         f"last {L - 1 - k_split} plain FP16, BF16 hi+lo P"}.get(mode),
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
                        "l2": "inputs larger than L2 (no flush)",
+                       "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
                        "coefficients": "learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 schedule)"},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,

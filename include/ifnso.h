@@ -68,7 +68,17 @@ typedef enum {
   /* Measurement aid: when non-zero, every ifnso_orthogonalize / ns_iterate
    * call records a CUDA event on its stream before its first launch and after
    * each pass; ifnso_pass_times() returns the per-pass durations. */
-  IFNSO_OPT_TIMING = 5
+  IFNSO_OPT_TIMING = 5,
+  /* Limit, in milliseconds, of every pipeline wait inside the tensor-core
+   * kernels (0, the default, means 4000).  A wait that runs out makes the CTA
+   * record IFNSO_DEV_TIMEOUT for its matrix, let its copies and products
+   * land, free its tensor memory and return. */
+  IFNSO_OPT_WAIT_LIMIT_MS = 6,
+  /* Testing aid for the failure path: when non-zero, the first CTA of the
+   * Gram pass loads nothing, so that its waits run out (after the wait
+   * limit) and the call reports IFNSO_DEV_TIMEOUT.  No memory is accessed out
+   * of bounds and nothing is left running. */
+  IFNSO_OPT_INJECT_STALL = 7
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };

@@ -28,6 +28,8 @@ struct ifnso_plan {
   int scale = IFNSO_SCALE_GRAM;
   int max_ctas = 0;
   int stop_after = -1;
+  int wait_ms = 0;       // limit of the kernels' pipeline waits (0: 4 s)
+  int inject_stall = 0;  // testing aid: the Gram pass's first CTA loads nothing
   int num_sms = 0;
   // metadata of the last batch (pinned host copy, uploaded into the workspace)
   uint64_t sig = 0;
@@ -904,6 +906,13 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
     case IFNSO_OPT_TIMING:
       plan->timing = value != 0;
       break;
+    case IFNSO_OPT_WAIT_LIMIT_MS:
+      if (value < 0 || value > 600000) return fail(IFNSO_ERR_INVALID_ARG, "wait limit %lld ms", (long long)value);
+      plan->wait_ms = static_cast<int>(value);
+      break;
+    case IFNSO_OPT_INJECT_STALL:
+      plan->inject_stall = value != 0;
+      break;
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -921,6 +930,8 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_MAX_CTAS: *value = plan->max_ctas; return IFNSO_OK;
     case IFNSO_OPT_STOP_AFTER: *value = plan->stop_after; return IFNSO_OK;
     case IFNSO_OPT_TIMING: *value = plan->timing ? 1 : 0; return IFNSO_OK;
+    case IFNSO_OPT_WAIT_LIMIT_MS: *value = plan->wait_ms; return IFNSO_OK;
+    case IFNSO_OPT_INJECT_STALL: *value = plan->inject_stall; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }
@@ -1044,10 +1055,13 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   const WorkItem* app = reinterpret_cast<const WorkItem*>(ws + ly.off_items_app);
   const Prec& pc = ly.prec;
   p.p_split = pc.p_split;
+  p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
   p.probs = probs + ly.pi_gram;
   p.items = sym;
   p.n_items = static_cast<int32_t>(ly.n_sym);
+  p.inject = plan->inject_stall;
   IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "Gram pass");
+  p.inject = 0;
   const ifnso_mlp* net = coeffs->mlp;
   if (net) {
     // until the network has spoken, the scalars see the fixed coefficients

@@ -100,6 +100,8 @@ struct TcParams {
                        // 2 P read and two terms subtracted, 3 P read and one term subtracted,
                        // 4 P written from c0 I, w_1 T_0 / o (read) and two terms
   int32_t feat;        // EPI_SQR: accumulate sum (D_l^2)_ij^2 into MatScalars::spare[0]
+  int32_t inject;      // testing aid: CTA 0's producer loads nothing, so its waits run out
+  uint32_t wait_ms;    // limit of every pipeline wait (0: the default of ptx.cuh)
   int32_t pad2;
   MatScalars* scal;
   CoefTable coef;

@@ -432,6 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  const unsigned long long tmo = p.wait_ms ? p.wait_ms * 1000000ull : kWaitTimeoutNs;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -442,7 +443,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       int cur_mat = 0;
       int last_prob = -1;
       bool ok = true;
-      for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x) {
+      // testing aid: CTA 0 loads nothing, its consumers' bounded waits run out
+      const int first = (p.inject && blockIdx.x == 0) ? p.n_items : static_cast<int>(blockIdx.x);
+      for (int it = first; it < p.n_items && ok; it += gridDim.x) {
         const WorkItem wi = p.items[it];
         const TcProblem& pr = p.probs[wi.prob];
         cur_mat = pr.mat;
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int a_mn = pr.a_mn, b_mn = pr.b_mn;
         const int n_kb = pr.n_kb;
         for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, tmo)) {
             ok = false;
             break;
           }
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         cur_mat = pr.mat;
         const int acc = local & 1;
         const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
-        if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag)) {
+        if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, tmo)) {
           ok = false;
           break;
         }
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const uint32_t idesc = idesc_f16(kIsBf16, BM, BN, a_mn, b_mn);
         const int n_kb = pr.n_kb;
         for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait(full_bar(stage), phase, abort_flag)) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag, tmo)) {
             ok = false;
             break;
           }
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
       // one lane waits, the warp follows its verdict (tcgen05.ld needs a converged warp)
       int ready = 0;
-      if (lane == 0) ready = mbar_wait(tfull_bar(acc), acc_phase, abort_flag) ? 1 : 0;
+      if (lane == 0) ready = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, tmo) ? 1 : 0;
       ready = __shfl_sync(0xffffffffu, ready, 0);
       if (!ready) {
         if (lane == 0) set_timeout(p.scal, pr.mat);
