@@ -40,6 +40,7 @@ struct ifnso_plan {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::vector<cudaEvent_t>> ev_calls;
+  std::vector<std::vector<cudaEvent_t>> ev_graph;  // recorded by captured calls (kept for replays)
   std::mutex mu;
 };
 
@@ -84,20 +85,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-// Record a timing event on `stream` if the plan times its passes.
+// Record a timing event on `stream` if the plan times its passes.  During
+// stream capture the event becomes a record node of the graph (external
+// record) and stays reserved for that graph: every replay records it again.
 cudaError_t mark(ifnso_plan* plan, cudaStream_t stream, bool first) {
   if (!plan->timing) return cudaSuccess;
-  if (first) plan->ev_calls.emplace_back();
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(stream, &cap);
+  if (r != cudaSuccess) return r;
+  const bool captured = cap == cudaStreamCaptureStatusActive;
+  auto& calls = captured ? plan->ev_graph : plan->ev_calls;
+  if (first) calls.emplace_back();
   cudaEvent_t e;
-  if (!plan->ev_pool.empty()) {
+  if (!plan->ev_pool.empty()) {  // (a captured event never returns to the pool)
     e = plan->ev_pool.back();
     plan->ev_pool.pop_back();
   } else {
-    cudaError_t r = cudaEventCreate(&e);
+    r = cudaEventCreate(&e);
     if (r != cudaSuccess) return r;
   }
-  plan->ev_calls.back().push_back(e);
-  return cudaEventRecord(e, stream);
+  calls.back().push_back(e);
+  return cudaEventRecordWithFlags(e, stream, captured ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 // 2D tiled tensor map, 128-byte swizzle, zero fill outside the tensor.
@@ -938,8 +946,9 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
 
 ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
   if (!plan) return IFNSO_OK;
-  for (auto& c : plan->ev_calls)
-    for (cudaEvent_t e : c) cudaEventDestroy(e);
+  for (auto* list : {&plan->ev_calls, &plan->ev_graph})
+    for (auto& c : *list)
+      for (cudaEvent_t e : c) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
   if (plan->meta_host) {
     cudaDeviceSynchronize();
@@ -1266,18 +1275,24 @@ ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_pass
   std::lock_guard<std::mutex> lk(plan->mu);
   for (int k = 0; k < max_passes; ++k) ms_out[k] = 0.0;
   *n_passes = 0;
-  if (n_calls) *n_calls = static_cast<int32_t>(plan->ev_calls.size());
-  for (auto& c : plan->ev_calls) {
-    if (c.size() < 2) continue;
-    IFNSO_CUDA(cudaEventSynchronize(c.back()), "cudaEventSynchronize");
-    const int np = static_cast<int>(c.size()) - 1;
-    *n_passes = np;
-    for (int k = 0; k < np && k < max_passes; ++k) {
-      float ms = 0.f;
-      IFNSO_CUDA(cudaEventElapsedTime(&ms, c[k], c[k + 1]), "cudaEventElapsedTime");
-      ms_out[k] += ms;
+  int ncalls = 0;
+  // eager calls since the last query, then each captured call once (its
+  // events hold the durations of the graph's latest replay)
+  for (auto* list : {&plan->ev_calls, &plan->ev_graph}) {
+    for (auto& c : *list) {
+      if (c.size() < 2) continue;
+      IFNSO_CUDA(cudaEventSynchronize(c.back()), "cudaEventSynchronize");
+      const int np = static_cast<int>(c.size()) - 1;
+      *n_passes = np;
+      ++ncalls;
+      for (int k = 0; k < np && k < max_passes; ++k) {
+        float ms = 0.f;
+        IFNSO_CUDA(cudaEventElapsedTime(&ms, c[k], c[k + 1]), "cudaEventElapsedTime");
+        ms_out[k] += ms;
+      }
     }
   }
+  if (n_calls) *n_calls = ncalls;
   for (auto& c : plan->ev_calls)
     for (cudaEvent_t e : c) plan->ev_pool.push_back(e);
   plan->ev_calls.clear();
