@@ -237,13 +237,14 @@ void sym_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return shp[a].hpad * shp[a].w > shp[b].hpad * shp[b].w;
   });
+  // one item per upper 256 x 256 block (I <= J): its two 128-row halves go
+  // to the two CTAs of a cluster
   for (int m : order) {
     const int nb = static_cast<int>(shp[m].hpad / 256);
     for (int I = 0; I < nb; ++I)
       for (int J = I; J < nb; ++J)
-        for (int half = 0; half < 2; ++half)
-          items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * I + half),
-                                   static_cast<uint16_t>(J), static_cast<uint16_t>(I == J ? 1 : 0)});
+        items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * I), static_cast<uint16_t>(J),
+                                 static_cast<uint16_t>(I == J ? 1 : 0)});
   }
 }
 
@@ -253,12 +254,14 @@ void app_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return shp[a].hpad * shp[a].w > shp[b].hpad * shp[b].w;
   });
+  // one item per pair of 128-row tiles sharing a 256-column block (rows past
+  // h are computed on zero padding and not stored)
   for (int m : order) {
-    const int tms = static_cast<int>((shp[m].h + BM - 1) / BM);
+    const int pairs = static_cast<int>((shp[m].h + 2 * BM - 1) / (2 * BM));
     const int tns = static_cast<int>((shp[m].w + BN - 1) / BN);
     for (int tn = 0; tn < tns; ++tn)
-      for (int tm = 0; tm < tms; ++tm)
-        items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(tm),
+      for (int pr = 0; pr < pairs; ++pr)
+        items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * pr),
                                  static_cast<uint16_t>(tn), 0});
   }
 }
@@ -434,9 +437,11 @@ ifnso_status ensure_meta_host(ifnso_plan* plan, size_t bytes, cudaStream_t strea
   return IFNSO_OK;
 }
 
+// Largest number of two-CTA clusters a pass may use.
 int grid_for(const ifnso_plan* plan, size_t items) {
   int g = plan->num_sms;
   if (plan->max_ctas > 0 && plan->max_ctas < g) g = plan->max_ctas;
+  g /= 2;
   if (static_cast<size_t>(g) > items) g = static_cast<int>(items);
   return g < 1 ? 1 : g;
 }

@@ -77,8 +77,10 @@ struct TcProblem {
 static_assert(alignof(TcProblem) % 64 == 0 && sizeof(TcProblem) % alignof(TcProblem) == 0,
               "TcProblem arrays must keep every tensor map 64-byte aligned");
 
-// A 128 x 256 output tile of one problem.  flags bit 0: the tile lies in a
-// diagonal 256 x 256 block (computed in full, no mirrored store).
+// A pair of 128 x 256 output tiles of one problem: rows [128 tm, 128 tm + 256)
+// (tm even; CTA r of the cluster computes tile tm + r), columns
+// [256 tn, 256 tn + 256).  flags bit 0: a diagonal 256 x 256 block (computed
+// in full, no mirrored store).
 struct WorkItem {
   uint16_t prob;
   uint16_t tm;
@@ -125,7 +127,9 @@ struct MatInfo {
 
 // ------------------------------------------------------------ launchers
 // (defined in tc_gemm.cu / simt.cu / learn.cu; called by api.cu)
-cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int grid, cudaStream_t s);
+// Launches clusters of two CTAs (at most max_clusters, at most one per item;
+// items are pairs of tiles, see WorkItem).
+cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s);
 int tc_smem_bytes(int na, int nb);
 
 cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,

@@ -4,7 +4,9 @@
 // One launch runs one pass of Algorithm 1 (Sec. 2.4) for every matrix of a
 // batch: the Gram product T_0 = A A^T, one squaring T_{l+1} = T_l^2 (in the
 // D basis, D_{l+1} = 2 D_l - D_l^2), or the final product Y = Y' A / sqrt(o).
-// Each CTA (one per SM) walks a static list of 128 x 256 output tiles.
+// Clusters of two CTAs (one CTA per SM) walk a static list of pairs of
+// 128 x 256 output tiles that share their B operand: each CTA computes one
+// tile of the pair and TMA-multicasts its half of the shared B tile to both.
 //
 // Warp roles (320 threads):
 //   warp 0      TMA producer: K blocks of 64 of every operand source into a
@@ -393,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   using PR = Products<NA, NB>;
   constexpr int S = C::stages;
   constexpr uint32_t kIsBf16 = (EPI == EPI_SQR) ? 0u : 1u;  // D_l are FP16, all else BF16
+  constexpr uint16_t kPair = 0x3;                           // both CTAs of the cluster
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -410,11 +413,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // A cluster of two CTAs computes the two 128-row halves of one 128 x 256
+  // pair of tiles: both need the same B tile, which each CTA loads half of and
+  // multicasts to both.
+  const int crank = static_cast<int>(cluster_ctarank());
+  const int cid = static_cast<int>(cluster_id_x());
+  const int ncl = static_cast<int>(cluster_count_x());
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 1);
+      mbar_init(empty_bar(s), 2);  // freed by the MMAs of both CTAs (their B halves live here)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
@@ -431,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
   const uint32_t tmem_base = *tmem_slot;
   const unsigned long long tmo = p.wait_ms ? p.wait_ms * 1000000ull : kWaitTimeoutNs;
 
@@ -443,9 +453,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       int cur_mat = 0;
       int last_prob = -1;
       bool ok = true;
-      // testing aid: CTA 0 loads nothing, its consumers' bounded waits run out
-      const int first = (p.inject && blockIdx.x == 0) ? p.n_items : static_cast<int>(blockIdx.x);
-      for (int it = first; it < p.n_items && ok; it += gridDim.x) {
+      // testing aid: the first CTA loads nothing, so the waits of both CTAs of its cluster run out
+      const int first = (p.inject && cid == 0 && crank == 0) ? p.n_items : cid;
+      for (int it = first; it < p.n_items && ok; it += ncl) {
         const WorkItem wi = p.items[it];
         const TcProblem& pr = p.probs[wi.prob];
         cur_mat = pr.mat;
@@ -458,13 +468,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         const int a_mn = pr.a_mn, b_mn = pr.b_mn;
         const int n_kb = pr.n_kb;
+        const int tm = wi.tm + crank;
         for (int kb = 0; kb < n_kb; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, tmo)) {
             ok = false;
             break;
           }
           const uint32_t fb = full_bar(stage);
-          mbar_arrive_expect_tx(fb, C::stage_bytes);
+          mbar_arrive_expect_tx(fb, C::stage_bytes);  // own A + both halves of B
           const uint32_t st = base + stage * C::stage_bytes;
           const int k0 = kb * BK;
 #pragma unroll
@@ -472,10 +483,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint32_t dst = st + a * kTileA;
             const void* m = &pr.mapA[a];
             if (!a_mn) {
-              tma_load_2d(dst, m, fb, k0, wi.tm * BM);
+              tma_load_2d(dst, m, fb, k0, tm * BM);
             } else {
-              tma_load_2d(dst, m, fb, wi.tm * BM, k0);
-              tma_load_2d(dst + 8192, m, fb, wi.tm * BM + 64, k0);
+              tma_load_2d(dst, m, fb, tm * BM, k0);
+              tma_load_2d(dst + 8192, m, fb, tm * BM + 64, k0);
             }
           }
 #pragma unroll
@@ -483,11 +494,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint32_t dst = st + NA * kTileA + b * kTileB;
             const void* m = &pr.mapB[b];
             if (!b_mn) {
-              tma_load_2d(dst, m, fb, k0, wi.tn * BN);
-              tma_load_2d(dst + 16384, m, fb, k0, wi.tn * BN + 128);
+              // this CTA's half: rows [128 crank, 128 crank + 128) of the B tile
+              tma_load_2d_mc(dst + 16384 * crank, m, fb, k0, wi.tn * BN + 128 * crank, kPair);
             } else {
+              // this CTA's half: MN chunks 2 crank and 2 crank + 1 of the B tile
 #pragma unroll
-              for (int j = 0; j < 4; ++j) tma_load_2d(dst + 8192 * j, m, fb, wi.tn * BN + 64 * j, k0);
+              for (int j = 2 * crank; j < 2 * crank + 2; ++j)
+                tma_load_2d_mc(dst + 8192 * j, m, fb, wi.tn * BN + 64 * j, k0, kPair);
             }
           }
           ++filled[stage];
@@ -501,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         set_timeout(p.scal, cur_mat);
         // let the copies already issued land before the CTA exits
         for (int s = 0; s < S; ++s)
-          if (filled[s]) mbar_wait_bounded(full_bar(s), (filled[s] - 1u) & 1u);
+          if (filled[s]) mbar_wait_bounded(full_bar(s), (filled[s] - 1u) & 1u, tmo);
       }
     }
   } else if (warp == 1) {
@@ -512,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       int local = 0;
       int cur_mat = 0;
       bool ok = true;
-      for (int it = blockIdx.x; it < p.n_items && ok; it += gridDim.x, ++local) {
+      for (int it = cid; it < p.n_items && ok; it += ncl, ++local) {
         const WorkItem wi = p.items[it];
         const TcProblem& pr = p.probs[wi.prob];
         cur_mat = pr.mat;
@@ -547,7 +560,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
               umma_f16(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
             }
           }
-          umma_commit(empty_bar(stage));  // frees the stage once these MMAs have read it
+          // frees the stage in both CTAs once these MMAs have read it
+          umma_commit_mc(empty_bar(stage), kPair);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -559,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       if (!ok) set_timeout(p.scal, cur_mat);
       // make sure no MMA is still writing TMEM or reading shared memory
       umma_commit(drain_bar);
-      mbar_wait_bounded(drain_bar, 0);
+      mbar_wait_bounded(drain_bar, 0, tmo);
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
@@ -568,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     const int half = (warp - 2) >> 2;  // which 128 of the tile's 256 columns
     const int row_in_tile = q * 32 + lane;
     int local = 0;
-    for (int it = blockIdx.x; it < p.n_items; it += gridDim.x, ++local) {
+    for (int it = cid; it < p.n_items; it += ncl, ++local) {
       const WorkItem wi = p.items[it];
       const TcProblem& pr = p.probs[wi.prob];
       const int acc = local & 1;
@@ -583,7 +597,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       tc_fence_after();
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN);
-      const int r = wi.tm * BM + row_in_tile;
+      const int r = (wi.tm + crank) * BM + row_in_tile;
       EpiAcc ea{0.f, 0.f};
 #pragma unroll 1
       for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
@@ -625,21 +639,52 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
   }
+  // neither CTA leaves while the other may still multicast into it or arrive on its barriers
+  cluster_sync();
 }
 
 template <int NA, int NB, int EPI>
-cudaError_t launch_one(const TcParams& p, int grid, cudaStream_t s) {
+cudaError_t launch_one(const TcParams& p, int max_clusters, cudaStream_t s) {
   using C = Cfg<NA, NB>;
   auto kern = tc_gemm_kernel<NA, NB, EPI>;
-  static bool attr_done = false;  // set once per process (per instantiation)
-  if (!attr_done) {
+  static int active_clusters = 0;  // per process and instantiation
+  if (active_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem);
     if (e != cudaSuccess) return e;
-    attr_done = true;
+    cudaLaunchConfig_t q = {};
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = 2;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.gridDim = dim3(2, 1, 1);
+    q.blockDim = dim3(kThreads, 1, 1);
+    q.dynamicSmemBytes = C::smem;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &q);
+    if (e != cudaSuccess) return e;
+    active_clusters = n > 0 ? n : 1;
   }
-  kern<<<grid, kThreads, C::smem, s>>>(p);
+  int clusters = active_clusters < max_clusters ? active_clusters : max_clusters;
+  if (clusters > p.n_items) clusters = p.n_items;
+  if (clusters < 1) clusters = 1;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * clusters, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = C::smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, p);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace
@@ -651,23 +696,23 @@ int tc_smem_bytes(int na, int nb) {
   return -1;
 }
 
-cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int grid, cudaStream_t s) {
+cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s) {
   if (p.n_items == 0) return cudaSuccess;
   switch (epi) {
     case EPI_GRAM:
-      return launch_one<1, 1, EPI_GRAM>(p, grid, s);
+      return launch_one<1, 1, EPI_GRAM>(p, max_clusters, s);
     case EPI_SQR:
-      if (na == 2) return launch_one<2, 2, EPI_SQR>(p, grid, s);
-      return launch_one<1, 1, EPI_SQR>(p, grid, s);
+      if (na == 2) return launch_one<2, 2, EPI_SQR>(p, max_clusters, s);
+      return launch_one<1, 1, EPI_SQR>(p, max_clusters, s);
     case EPI_APPLY:
-      if (na == 2) return launch_one<2, 1, EPI_APPLY>(p, grid, s);
-      return launch_one<1, 1, EPI_APPLY>(p, grid, s);
+      if (na == 2) return launch_one<2, 1, EPI_APPLY>(p, max_clusters, s);
+      return launch_one<1, 1, EPI_APPLY>(p, max_clusters, s);
     case EPI_NS_GRAM:
-      return launch_one<1, 1, EPI_NS_GRAM>(p, grid, s);
+      return launch_one<1, 1, EPI_NS_GRAM>(p, max_clusters, s);
     case EPI_NS_SQR:
-      return launch_one<1, 1, EPI_NS_SQR>(p, grid, s);
+      return launch_one<1, 1, EPI_NS_SQR>(p, max_clusters, s);
     case EPI_NS_APPLY:
-      return launch_one<1, 1, EPI_NS_APPLY>(p, grid, s);
+      return launch_one<1, 1, EPI_NS_APPLY>(p, max_clusters, s);
     default:
       return cudaErrorInvalidValue;
   }
