@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="muon_1b", choices=sorted(WORKLOADS))
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
+    ap.add_argument("--cta-group", type=int, default=1, choices=[1, 2],
+                    help="tensor-core passes: MMAs of the CTA pair (2) or per-CTA MMAs with B multicast (1)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
@@ -322,6 +324,7 @@ def main():
 
     plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision)
     plan.set(F.IFNSO_OPT_TIMING, 1)
+    plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
     ws = F.Workspace(plan.workspace_bytes(batch), device=device)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -406,6 +409,7 @@ def main():
 
     # 5-step quintic Newton-Schulz on the same list
     nsplan = F.Plan(hmax, wmax, "bf16", L=1)
+    nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
     nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
     zs = [torch.empty_like(x) for x in xs]
     for _ in range(max(args.warmup, 3)):
@@ -475,6 +479,8 @@ def main():
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
                        "l2": "inputs larger than L2 (no flush)",
                        "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
+                       "mma": ("tcgen05 MMAs of the CTA pair (M = 256)" if args.cta_group == 2
+                               else "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters"),
                        "coefficients": "learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 schedule)"},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,

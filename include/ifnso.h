@@ -78,7 +78,18 @@ typedef enum {
    * Gram pass loads nothing, so that its waits run out (after the wait
    * limit) and the call reports IFNSO_DEV_TIMEOUT.  No memory is accessed out
    * of bounds and nothing is left running. */
-  IFNSO_OPT_INJECT_STALL = 7
+  IFNSO_OPT_INJECT_STALL = 7,
+  /* How the two CTAs of a cluster share the B operand of a pair of output
+   * tiles in the tensor-core passes (the results agree bit for bit on every
+   * case tested):
+   * 1 (default): each CTA issues its own M = 128 MMAs and multicasts its half
+   *    of B to both CTAs.
+   * 2: MMAs of the CTA pair, M = 256 (tcgen05 cta_group::2); each CTA keeps
+   *    its own half of B, so an SM takes in a third fewer operand bytes per
+   *    product, but the odd CTA's stage completions reach the issuing CTA
+   *    through a release-ordered remote arrive per stage, which limits the
+   *    rate of stages. */
+  IFNSO_OPT_CTA_GROUP = 8
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };
@@ -216,7 +227,9 @@ ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_pass
  * ifnso_orthogonalize.  which: 0 = T_0 then P (FP32), 1/2 = D buffer 0 hi/lo
  * (FP16, or FP32 for F32 plans), 3/4 = D buffer 1 hi/lo, 5 = the FP32
  * coefficient row (c_0, w_1..w_L) the proposal network chose for the matrix
- * (ld = 32). */
+ * (ld = 32).  BF16 plans keep these symmetric matrices on their 256 x 256
+ * blocks on and above the diagonal only: element (i, j) with
+ * i / 256 > j / 256 is the one at (j, i); the memory below is unspecified. */
 ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch,
                                   void* workspace, int32_t index, int32_t which, void** ptr,
                                   int64_t* ld);

@@ -30,6 +30,7 @@ struct ifnso_plan {
   int stop_after = -1;
   int wait_ms = 0;       // limit of the kernels' pipeline waits (0: 4 s)
   int inject_stall = 0;  // testing aid: the Gram pass's first CTA loads nothing
+  int cta_group = 1;     // tensor-core passes: per-CTA MMAs (1) or MMAs of the CTA pair (2)
   int num_sms = 0;
   // metadata of the last batch (pinned host copy, uploaded into the workspace)
   uint64_t sig = 0;
@@ -553,12 +554,17 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
       TcProblem& q = pr[ly.pi_sqr + par * n + i];
       const void* shi = mi.d[2 * par];
       const void* slo = mi.d[2 * par + 1];
-      if (!map_k(&q.mapA[0], f16_t(), shi, hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (D hi)");
+      // D_l is symmetric and stored on its upper blocks: A and B rows of a
+      // tile read K blocks left of their diagonal block through mapT
+      if (!map_k(&q.mapA[0], f16_t(), shi, hp, hp, hp) || !map_mn(&q.mapT[0], f16_t(), shi, hp, hp, hp))
+        return fail(IFNSO_ERR_CUDA, "tensor map (D hi)");
       q.mapB[0] = q.mapA[0];
       if (ly.split) {
-        if (!map_k(&q.mapA[1], f16_t(), slo, hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (D lo)");
+        if (!map_k(&q.mapA[1], f16_t(), slo, hp, hp, hp) || !map_mn(&q.mapT[1], f16_t(), slo, hp, hp, hp))
+          return fail(IFNSO_ERR_CUDA, "tensor map (D lo)");
         q.mapB[1] = q.mapA[1];
       }
+      q.sym = kSymA | kSymB;
       q.n_kb = static_cast<int32_t>(hp / BK);
       q.mat = i;
       q.ld_aux = q.ld_out = hp;
@@ -571,9 +577,14 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     // apply: A operand P (BF16 hi/lo in D buffer (L-1) % 2), B operand the input
     TcProblem& a = pr[ly.pi_apply + i];
     const int fb = (ly.L - 1) % 2;
-    if (!map_k(&a.mapA[0], bf16_t(), mi.d[2 * fb], hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (P hi)");
-    if (ly.split && !map_k(&a.mapA[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp))
+    // P is symmetric and stored on its upper blocks
+    if (!map_k(&a.mapA[0], bf16_t(), mi.d[2 * fb], hp, hp, hp) ||
+        !map_mn(&a.mapT[0], bf16_t(), mi.d[2 * fb], hp, hp, hp))
+      return fail(IFNSO_ERR_CUDA, "tensor map (P hi)");
+    if (ly.split && (!map_k(&a.mapA[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp) ||
+                     !map_mn(&a.mapT[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp)))
       return fail(IFNSO_ERR_CUDA, "tensor map (P lo)");
+    a.sym = kSymA;
     if (!s.trans) {
       // Y = P A: B(n, k) = A[k][n], contiguous along n
       ok = map_mn(&a.mapB[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
@@ -715,8 +726,10 @@ ifnso_status build_ns_meta(const Layout& ly, const ifnso_batch_desc* b, void* co
       a.ld_aux = xl;
     }
     TcProblem& q = pr[ly.pi_ns_sqr + i];
-    if (!map_k(&q.mapA[0], bf16_t(), mi.s, hp, hp, hp)) return fail(IFNSO_ERR_CUDA, "tensor map (NS S)");
+    if (!map_k(&q.mapA[0], bf16_t(), mi.s, hp, hp, hp) || !map_mn(&q.mapT[0], bf16_t(), mi.s, hp, hp, hp))
+      return fail(IFNSO_ERR_CUDA, "tensor map (NS S)");
     q.mapB[0] = q.mapA[0];
+    q.sym = kSymA | kSymB;
     q.n_kb = static_cast<int32_t>(hp / BK);
     q.mat = i;
     q.ld_aux = q.ld_out = hp;
@@ -745,10 +758,16 @@ ifnso_status ns_set_apply_source(const Layout& ly, uint8_t* meta, int use_b) {
   TcProblem* pr = reinterpret_cast<TcProblem*>(meta + ly.off_probs);
   for (int i = 0; i < n; ++i) {
     const int64_t hp = ly.shp[i].hpad;
-    CUtensorMap m;
-    if (!map_k(&m, bf16_t(), use_b ? mats[i].b : mats[i].s, hp, hp, hp))
+    CUtensorMap m, mt;
+    const void* src = use_b ? mats[i].b : mats[i].s;
+    if (!map_k(&m, bf16_t(), src, hp, hp, hp) || !map_mn(&mt, bf16_t(), src, hp, hp, hp))
       return fail(IFNSO_ERR_CUDA, "tensor map (NS apply operand)");
-    for (int st = 0; st < ly.steps; ++st) pr[ly.pi_ns_apply + st * n + i].mapA[0] = m;
+    for (int st = 0; st < ly.steps; ++st) {
+      TcProblem& a = pr[ly.pi_ns_apply + st * n + i];
+      a.mapA[0] = m;
+      a.mapT[0] = mt;
+      a.sym = kSymA;  // B and S are symmetric, stored on their upper blocks
+    }
   }
   return IFNSO_OK;
 }
@@ -926,6 +945,10 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
     case IFNSO_OPT_INJECT_STALL:
       plan->inject_stall = value != 0;
       break;
+    case IFNSO_OPT_CTA_GROUP:
+      if (value != 1 && value != 2) return fail(IFNSO_ERR_INVALID_ARG, "cta group %lld", (long long)value);
+      plan->cta_group = static_cast<int>(value);
+      break;
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -945,6 +968,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_TIMING: *value = plan->timing ? 1 : 0; return IFNSO_OK;
     case IFNSO_OPT_WAIT_LIMIT_MS: *value = plan->wait_ms; return IFNSO_OK;
     case IFNSO_OPT_INJECT_STALL: *value = plan->inject_stall; return IFNSO_OK;
+    case IFNSO_OPT_CTA_GROUP: *value = plan->cta_group; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }
@@ -1070,6 +1094,7 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   const Prec& pc = ly.prec;
   p.p_split = pc.p_split;
   p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
+  p.cta_group = plan->cta_group;
   p.probs = probs + ly.pi_gram;
   p.items = sym;
   p.n_items = static_cast<int32_t>(ly.n_sym);
@@ -1219,6 +1244,8 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
     return IFNSO_OK;
   }
   TcParams p{};
+  p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
+  p.cta_group = plan->cta_group;
   p.scal = scal;
   p.ns_a = a;
   p.ns_b = b;

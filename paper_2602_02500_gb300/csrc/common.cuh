@@ -52,11 +52,18 @@ __device__ __forceinline__ double coef_at(const CoefTable& t, int m, int l) {
   return t.f32 ? static_cast<double>(t.f32[static_cast<int64_t>(m) * t.stride + l]) : t.d64[l];
 }
 
+// Symmetric h_pad x h_pad intermediates (T_0, D_l, P, and S, B of the
+// Newton-Schulz baseline) are stored on their 256 x 256 blocks on and above
+// the diagonal only: element (i, k) with i / 256 > k / 256 is read as (k, i).
+constexpr int kSymA = 1;  // TcProblem::sym: A operand is such a buffer
+constexpr int kSymB = 2;  // B operand is such a buffer (then the same one as A)
+
 // One matrix product of a tensor-core pass.  The tensor maps live in global
 // memory (64-byte aligned) and are read by TMA directly.
 struct TcProblem {
   CUtensorMap mapA[2];  // A-operand sources (rows of the output tile)
   CUtensorMap mapB[2];  // B-operand sources (columns of the output tile)
+  CUtensorMap mapT[2];  // the symmetric operand buffers read transposed (boxes 64 x 64)
   int32_t n_kb;         // number of 64-wide K blocks
   int32_t mat;          // matrix index (scalars, coefficients, status)
   int32_t a_mn;         // 1: A operand is MN-major in memory (TMA boxes 64 x 64)
@@ -64,7 +71,7 @@ struct TcProblem {
   int32_t out_trans;    // apply: tile element (r, c) is written to out[c][r]
   int32_t rows_out;     // valid extent of out0 in its own layout
   int32_t cols_out;
-  int32_t pad0;
+  int32_t sym;          // kSymA | kSymB
   int64_t ld_out;       // leading dimension of out0/out1 (elements)
   int64_t ld_aux;       // leading dimension of aux0/aux1 and pacc (elements)
   void* out0;
@@ -79,8 +86,9 @@ static_assert(alignof(TcProblem) % 64 == 0 && sizeof(TcProblem) % alignof(TcProb
 
 // A pair of 128 x 256 output tiles of one problem: rows [128 tm, 128 tm + 256)
 // (tm even; CTA r of the cluster computes tile tm + r), columns
-// [256 tn, 256 tn + 256).  flags bit 0: a diagonal 256 x 256 block (computed
-// in full, no mirrored store).
+// [256 tn, 256 tn + 256).  flags bit 0: a diagonal 256 x 256 block of a
+// symmetric output (stands for itself only; the others also for their
+// transpose, which is not stored).
 struct WorkItem {
   uint16_t prob;
   uint16_t tm;
@@ -104,7 +112,8 @@ struct TcParams {
   int32_t feat;        // EPI_SQR: accumulate sum (D_l^2)_ij^2 into MatScalars::spare[0]
   int32_t inject;      // testing aid: CTA 0's producer loads nothing, so its waits run out
   uint32_t wait_ms;    // limit of every pipeline wait (0: the default of ptx.cuh)
-  int32_t pad2;
+  int32_t cta_group;   // 2: MMAs of the CTA pair (M = 256, B halves stay in each CTA);
+                       // 1: per-CTA MMAs with the B tile multicast to both CTAs
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;
@@ -128,9 +137,9 @@ struct MatInfo {
 // ------------------------------------------------------------ launchers
 // (defined in tc_gemm.cu / simt.cu / learn.cu; called by api.cu)
 // Launches clusters of two CTAs (at most max_clusters, at most one per item;
-// items are pairs of tiles, see WorkItem).
+// items are pairs of tiles, see WorkItem), in the MMA mode p.cta_group.
 cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s);
-int tc_smem_bytes(int na, int nb);
+int tc_smem_bytes(int na, int nb, int cta_group);
 
 cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,
                          int64_t out_stride, int grid_x, cudaStream_t s);

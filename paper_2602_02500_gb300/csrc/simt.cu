@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* s
   for (int64_t e8 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e8 < n / 8;
        e8 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = e8 / row8, j0 = (e8 - i * row8) * 8;
+    // the tensor-core path stores symmetric intermediates on the 256 x 256
+    // blocks on and above the diagonal only (T_0 in, D_1 / P out)
+    if (!f32 && (i >> 8) > (j0 >> 8)) continue;
     const int64_t e = i * hp + j0;
     const float4 g0 = reinterpret_cast<const float4*>(gp + e)[0];
     const float4 g1 = reinterpret_cast<const float4*>(gp + e)[1];

@@ -5,20 +5,32 @@
 // batch: the Gram product T_0 = A A^T, one squaring T_{l+1} = T_l^2 (in the
 // D basis, D_{l+1} = 2 D_l - D_l^2), or the final product Y = Y' A / sqrt(o).
 // Clusters of two CTAs (one CTA per SM) walk a static list of pairs of
-// 128 x 256 output tiles that share their B operand: each CTA computes one
-// tile of the pair and TMA-multicasts its half of the shared B tile to both.
+// 128 x 256 output tiles that share their B operand; each CTA owns one tile
+// of the pair (its 128 rows of A, its accumulator) and loads half of the
+// shared B tile.  Two ways to use that half (template parameter CG):
+//   CG = 1  each CTA issues its own M = 128 MMAs and TMA-multicasts its half
+//           of B to both CTAs, so each shared memory holds the whole B tile;
+//   CG = 2  the even CTA issues M = 256 MMAs of the CTA pair
+//           (tcgen05 cta_group::2) that read A and B from both shared
+//           memories: each CTA stores only its own half of B, so an SM takes
+//           in 32 KB (not 48 KB) per 64-wide K block of a plain product.  The
+//           odd CTA's TMA completions reach the issuer through a relay
+//           thread that arrives on the even CTA's stage barrier.
 //
 // Warp roles (320 threads):
 //   warp 0      TMA producer: K blocks of 64 of every operand source into a
 //               ring of shared-memory stages (128-byte swizzle).
 //   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
-//               and MMA issuer: tcgen05.mma M=128, N=256, K=16, kind::f16.
+//               and MMA issuer: tcgen05.mma M=128 (CG 1) or 256 (CG 2, even
+//               CTA; the odd CTA's warp 1 is the relay), N=256, K=16.
 //   warps 2..9  epilogue (two warps per TMEM lane quadrant, 128 columns each):
 //               tcgen05.ld of the accumulator, fused elementwise math of the
 //               pass, stores to global memory.
 // The two accumulators let the epilogue of tile t overlap the main loop of
-// tile t + 1.  Symmetric outputs (T_0, D_l, P) are computed on the upper
-// 256 x 256 blocks only and stored twice (direct and mirrored).
+// tile t + 1.  Symmetric results (T_0, D_l, P) are computed and stored on
+// the upper 256 x 256 blocks only; where a pass reads one as an operand, the
+// K blocks left of the tile's diagonal block are loaded from the stored block
+// across the diagonal (MN-major boxes; the MMA layout bits follow per K block).
 //
 // Every wait is bounded (ptx.cuh): on a timeout the CTA raises a shared
 // abort flag, records IFNSO_DEV_TIMEOUT in the matrix status word, lets its
@@ -36,15 +48,17 @@ namespace {
 constexpr int kEpiWarps = 8;                  // two per TMEM lane quadrant, 128 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr uint32_t kTileA = BM * BK * 2;  // 16 KB: 128 rows x 64 K of 16-bit values
-constexpr uint32_t kTileB = BN * BK * 2;  // 32 KB: 256 rows x 64 K
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStageLd = 33;                               // padded row of a transpose buffer
 constexpr uint32_t kStageBytes = kEpiWarps * 32 * kStageLd * 4;  // one 32 x 33 float buffer per epilogue warp
 constexpr int kDevTimeout = 4;  // IFNSO_DEV_TIMEOUT
 
-template <int NA, int NB>
+template <int NA, int NB, int CG>
 struct Cfg {
-  static constexpr uint32_t stage_bytes = NA * kTileA + NB * kTileB;
+  // B tile held by one CTA: all 256 rows (CG 1, half of them multicast by the
+  // peer) or its own 128-row half (CG 2)
+  static constexpr uint32_t tile_b = (CG == 2 ? BN / 2 : BN) * BK * 2;
+  static constexpr uint32_t stage_bytes = NA * kTileA + NB * tile_b;
   static constexpr int stages_fit = static_cast<int>((200u * 1024u) / stage_bytes);
   static constexpr int stages = stages_fit > 6 ? 6 : stages_fit;
   // tiles + 1 KB alignment slack + barriers / flags + epilogue transpose buffers
@@ -73,182 +87,224 @@ __device__ __forceinline__ void set_timeout(MatScalars* scal, int mat) {
 }
 
 // ---------------------------------------------------------------- epilogues
+//
+// The accumulator arrives with one output row per lane (tcgen05.ld 32x32b:
+// lane t of a warp holds row t of a 32 x 32 block).  Global memory is
+// accessed with the lanes spread along rows instead (8 lanes x 16 bytes per
+// row of 32 FP32 values, 4 lanes x 16 bytes per row of 32 16-bit values), so
+// that one warp instruction writes or reads whole row segments of 4 or 8
+// rows.  The two layouts are exchanged through the warp's 32 x 33 float
+// buffer; every access pattern below touches 32 distinct banks.
 
-__device__ __forceinline__ void load_h32(const __half* src, float* d) {
-  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+template <typename T>
+struct Blk;
+template <>
+struct Blk<float> {
+  static constexpr int kPer = 4;         // values per 16-byte access
+  static constexpr int kLanesPerRow = 8;
+  static constexpr int kRowsPerPass = 4;
+  static constexpr int kPasses = 8;
+};
+template <>
+struct Blk<__half> {
+  static constexpr int kPer = 8;
+  static constexpr int kLanesPerRow = 4;
+  static constexpr int kRowsPerPass = 8;
+  static constexpr int kPasses = 4;
+};
+template <>
+struct Blk<__nv_bfloat16> : Blk<__half> {};
+
+// One lane's share of a 32 x 32 block in the global (row-spread) layout.
+struct RawBlk {
+  uint4 q[8];
+};
+
+template <typename T>
+__device__ __forceinline__ void unpack16(const uint4& u, float* x);
+template <>
+__device__ __forceinline__ void unpack16<float>(const uint4& u, float* x) {
+  x[0] = __uint_as_float(u.x);
+  x[1] = __uint_as_float(u.y);
+  x[2] = __uint_as_float(u.z);
+  x[3] = __uint_as_float(u.w);
+}
+template <>
+__device__ __forceinline__ void unpack16<__half>(const uint4& u, float* x) {
+  const __half2* h = reinterpret_cast<const __half2*>(&u);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint4 u = s4[j];
-    const __half2* h2 = reinterpret_cast<const __half2*>(&u);
+  for (int t = 0; t < 4; ++t) {
+    const float2 f = __half22float2(h[t]);
+    x[2 * t] = f.x;
+    x[2 * t + 1] = f.y;
+  }
+}
+template <>
+__device__ __forceinline__ void unpack16<__nv_bfloat16>(const uint4& u, float* x) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float2 f = __half22float2(h2[t]);
-      d[8 * j + 2 * t] = f.x;
-      d[8 * j + 2 * t + 1] = f.y;
+  for (int t = 0; t < 4; ++t) {
+    const float2 f = __bfloat1622float2(h[t]);
+    x[2 * t] = f.x;
+    x[2 * t + 1] = f.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ uint4 pack16(const float* x);
+template <>
+__device__ __forceinline__ uint4 pack16<float>(const float* x) {
+  return make_uint4(__float_as_uint(x[0]), __float_as_uint(x[1]), __float_as_uint(x[2]), __float_as_uint(x[3]));
+}
+template <>
+__device__ __forceinline__ uint4 pack16<__half>(const float* x) {
+  uint4 u;
+  __half2* h = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) h[t] = __floats2half2_rn(x[2 * t], x[2 * t + 1]);
+  return u;
+}
+template <>
+__device__ __forceinline__ uint4 pack16<__nv_bfloat16>(const float* x) {
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) h[t] = __floats2bfloat162_rn(x[2 * t], x[2 * t + 1]);
+  return u;
+}
+
+// Row (within the block) and first column of this lane's accesses in pass s.
+template <typename T>
+__device__ __forceinline__ int blk_row(int s) {
+  return s * Blk<T>::kRowsPerPass + (threadIdx.x & 31) / Blk<T>::kLanesPerRow;
+}
+template <typename T>
+__device__ __forceinline__ int blk_col() {
+  return ((threadIdx.x & 31) % Blk<T>::kLanesPerRow) * Blk<T>::kPer;
+}
+
+// Issue the loads of the 32 x 32 block at src (row-major, leading dimension
+// ld, 16-byte aligned rows); the values are used after blk_unpack.
+template <typename T>
+__device__ __forceinline__ void blk_load(RawBlk& raw, const T* src, int64_t ld) {
+#pragma unroll
+  for (int s = 0; s < Blk<T>::kPasses; ++s)
+    raw.q[s] = *reinterpret_cast<const uint4*>(src + static_cast<int64_t>(blk_row<T>(s)) * ld + blk_col<T>());
+}
+
+// Same, for a block that may reach past `rows` x `cols` (zero there); vec:
+// the rows are 16-byte aligned.  Warp-uniform arguments.
+template <typename T>
+__device__ __forceinline__ void blk_load_bounded(RawBlk& raw, const T* src, int64_t ld, int rows, int cols,
+                                                 bool vec) {
+  const int cc = blk_col<T>();
+#pragma unroll
+  for (int s = 0; s < Blk<T>::kPasses; ++s) {
+    const int i = blk_row<T>(s);
+    raw.q[s] = make_uint4(0u, 0u, 0u, 0u);
+    if (i >= rows || cc >= cols) continue;
+    const T* p = src + static_cast<int64_t>(i) * ld + cc;
+    if (vec && cc + Blk<T>::kPer <= cols) {
+      raw.q[s] = *reinterpret_cast<const uint4*>(p);
+    } else {
+      T* e = reinterpret_cast<T*>(&raw.q[s]);
+#pragma unroll
+      for (int k = 0; k < Blk<T>::kPer; ++k)
+        if (cc + k < cols) e[k] = p[k];
     }
   }
 }
 
-__device__ __forceinline__ void load_b32(const __nv_bfloat16* src, float* d) {
-  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+// Move a loaded block through the staging buffer so that lane t receives
+// block row t (TRANS: block column t) in d[0..31].
+template <typename T, bool TRANS = false>
+__device__ __forceinline__ void blk_unpack(const RawBlk& raw, float* st, float* d) {
+  const int lane = threadIdx.x & 31;
+  const int cc = blk_col<T>();
+  __syncwarp();
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint4 u = s4[j];
-    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+  for (int s = 0; s < Blk<T>::kPasses; ++s) {
+    float x[Blk<T>::kPer];
+    unpack16<T>(raw.q[s], x);
+    const int i = blk_row<T>(s);
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float2 f = __bfloat1622float2(h2[t]);
-      d[8 * j + 2 * t] = f.x;
-      d[8 * j + 2 * t + 1] = f.y;
-    }
+    for (int k = 0; k < Blk<T>::kPer; ++k) st[i * kStageLd + cc + k] = x[k];
   }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 32; ++j) d[j] = TRANS ? st[j * kStageLd + lane] : st[lane * kStageLd + j];
 }
 
-__device__ __forceinline__ void store_h32(__half* dst, const float* v) {
-  uint4* d4 = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint4 u;
-    __half2* h2 = reinterpret_cast<__half2*>(&u);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) h2[t] = __floats2half2_rn(v[8 * j + 2 * t], v[8 * j + 2 * t + 1]);
-    d4[j] = u;
-  }
-}
-
-__device__ __forceinline__ void store_b32(__nv_bfloat16* dst, const float* v) {
-  uint4* d4 = reinterpret_cast<uint4*>(dst);
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    uint4 u;
-    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&u);
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      h2[t] = __floats2bfloat162_rn(v[8 * j + 2 * t], v[8 * j + 2 * t + 1]);
-    d4[j] = u;
-  }
-}
-
-// Per-warp 32 x 32 transpose through shared memory (rows padded to 33
-// floats: conflict-free in both directions).  Lane t holds v[0..31] = row
-// t of a 32 x 32 block; afterwards it holds w[0..31] = column t.  Every lane
-// of the warp must call it.
-
-__device__ __forceinline__ void warp_transpose(float* st, const float* v, float* w) {
+// Lane t's 32 values become row t of the staged block.
+__device__ __forceinline__ void blk_put(float* st, const float* v) {
   const int lane = threadIdx.x & 31;
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < 32; ++j) st[lane * kStageLd + j] = v[j];
   __syncwarp();
-#pragma unroll
-  for (int i = 0; i < 32; ++i) w[i] = st[i * kStageLd + lane];
 }
 
-template <typename T>
-__device__ __forceinline__ void store_row32(T* dst, const float* v);
-template <>
-__device__ __forceinline__ void store_row32<float>(float* dst, const float* v) {
-  float4* d4 = reinterpret_cast<float4*>(dst);
+// Store the staged block (TRANS: its transpose) at dst: block row i (TRANS:
+// block column i) goes to dst + i * ld.  Rows 16-byte aligned.
+template <typename T, bool TRANS>
+__device__ __forceinline__ void blk_store(T* dst, int64_t ld, const float* st) {
+  const int cc = blk_col<T>();
 #pragma unroll
-  for (int j = 0; j < 8; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-}
-template <>
-__device__ __forceinline__ void store_row32<__half>(__half* dst, const float* v) {
-  store_h32(dst, v);
-}
-template <>
-__device__ __forceinline__ void store_row32<__nv_bfloat16>(__nv_bfloat16* dst, const float* v) {
-  store_b32(dst, v);
-}
-
-// Store a 32-wide row chunk of a symmetric h_pad x h_pad result at
-// (r, c0..c0+31) and, for tiles off the diagonal blocks, at (c0..c0+31, r):
-// the mirrored chunk is transposed through shared memory so that every lane
-// writes one contiguous 32-element row segment.  `mirror` is warp-uniform.
-template <typename T>
-__device__ __forceinline__ void store_sym(T* buf, int64_t ld, int r, int c0, const float* v,
-                                          bool mirror, float* st) {
-  store_row32<T>(buf + static_cast<int64_t>(r) * ld + c0, v);
-  if (mirror) {
-    float w[32];
-    warp_transpose(st, v, w);
-    const int lane = threadIdx.x & 31;
-    store_row32<T>(buf + static_cast<int64_t>(c0 + lane) * ld + (r - lane), w);
+  for (int s = 0; s < Blk<T>::kPasses; ++s) {
+    const int i = blk_row<T>(s);
+    float x[Blk<T>::kPer];
+#pragma unroll
+    for (int k = 0; k < Blk<T>::kPer; ++k) x[k] = TRANS ? st[(cc + k) * kStageLd + i] : st[i * kStageLd + cc + k];
+    *reinterpret_cast<uint4*>(dst + static_cast<int64_t>(i) * ld + cc) = pack16<T>(x);
   }
 }
 
-// Bounds-checked BF16 store of a 32-wide chunk of an output tile (row r,
-// columns c0..c0+31).  With out_trans the tile is the transpose of the
-// output: the chunk is transposed through shared memory and lane t writes
-// output row c0 + t, columns (r - lane)..(r - lane + 31).  Warp-uniform call.
-__device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r, int c0, const float* v,
-                                               float* st) {
+// Same, clipped to `rows` x `cols` of the destination; vec: 16-byte aligned rows.
+template <typename T, bool TRANS>
+__device__ __forceinline__ void blk_store_bounded(T* dst, int64_t ld, const float* st, int rows, int cols,
+                                                  bool vec) {
+  const int cc = blk_col<T>();
+#pragma unroll
+  for (int s = 0; s < Blk<T>::kPasses; ++s) {
+    const int i = blk_row<T>(s);
+    if (i >= rows || cc >= cols) continue;
+    float x[Blk<T>::kPer];
+#pragma unroll
+    for (int k = 0; k < Blk<T>::kPer; ++k) x[k] = TRANS ? st[(cc + k) * kStageLd + i] : st[i * kStageLd + cc + k];
+    T* p = dst + static_cast<int64_t>(i) * ld + cc;
+    if (vec && cc + Blk<T>::kPer <= cols) {
+      *reinterpret_cast<uint4*>(p) = pack16<T>(x);
+    } else {
+      const uint4 u = pack16<T>(x);
+      const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+      for (int k = 0; k < Blk<T>::kPer; ++k)
+        if (cc + k < cols) p[k] = e[k];
+    }
+  }
+}
+
+// Store the 32 x 32 block whose rows are lanes' v (rows r0.., columns c0..)
+// into an h_pad x h_pad buffer.  Symmetric results are computed and stored on
+// the upper 256 x 256 blocks only; their readers take the rest from there.
+template <typename T>
+__device__ __forceinline__ void store_blk(T* buf, int64_t ld, int r0, int c0, const float* v, float* st) {
+  blk_put(st, v);
+  blk_store<T, false>(buf + static_cast<int64_t>(r0) * ld + c0, ld, st);
+}
+
+// BF16 output block of the tile (rows r0.., columns c0..), clipped to the
+// output; with out_trans the tile is the transpose of the output.
+__device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r0, int c0, const float* v, float* st) {
   __nv_bfloat16* out = static_cast<__nv_bfloat16*>(pr.out0);
-  const bool vec_ld = (pr.ld_out & 7) == 0;
-  if (!pr.out_trans) {
-    if (r >= pr.rows_out) return;
-    __nv_bfloat16* o = out + static_cast<int64_t>(r) * pr.ld_out + c0;
-    if (c0 + 32 <= pr.cols_out && vec_ld) {
-      store_b32(o, v);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < pr.cols_out) o[j] = __float2bfloat16_rn(v[j]);
-    }
-  } else {
-    float w[32];
-    warp_transpose(st, v, w);
-    const int lane = threadIdx.x & 31;
-    const int orow = c0 + lane, ocol = r - lane;
-    if (orow >= pr.rows_out) return;
-    __nv_bfloat16* o = out + static_cast<int64_t>(orow) * pr.ld_out + ocol;
-    if (ocol + 32 <= pr.cols_out && vec_ld) {
-      store_b32(o, w);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (ocol + i < pr.cols_out) o[i] = __float2bfloat16_rn(w[i]);
-    }
-  }
-}
-
-// Load the 32 values of the NS iterate X at the positions a chunk of the
-// output tile is written to (same layout rules as store_out_bf16; zero
-// outside the matrix).  Warp-uniform call.
-__device__ __forceinline__ void load_x_bf16(const TcProblem& pr, int r, int c0, float* x, float* st) {
-  const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(pr.aux0);
-  const bool vec_ld = (pr.ld_aux & 7) == 0;
-  if (!pr.out_trans) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) x[j] = 0.f;
-    if (r >= pr.rows_out) return;
-    const __nv_bfloat16* s = X + static_cast<int64_t>(r) * pr.ld_aux + c0;
-    if (c0 + 32 <= pr.cols_out && vec_ld) {
-      load_b32(s, x);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (c0 + j < pr.cols_out) x[j] = __bfloat162float(s[j]);
-    }
-  } else {
-    // lane t reads row c0 + t of X, columns (r - lane)..+31, then the block is transposed
-    const int lane = threadIdx.x & 31;
-    const int xrow = c0 + lane, xcol = r - lane;
-    float u[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) u[i] = 0.f;
-    if (xrow < pr.rows_out) {
-      const __nv_bfloat16* s = X + static_cast<int64_t>(xrow) * pr.ld_aux + xcol;
-      if (xcol + 32 <= pr.cols_out && vec_ld) {
-        load_b32(s, u);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (xcol + i < pr.cols_out) u[i] = __bfloat162float(s[i]);
-      }
-    }
-    warp_transpose(st, u, x);
-  }
+  const bool vec = (pr.ld_out & 7) == 0;
+  blk_put(st, v);
+  if (!pr.out_trans)
+    blk_store_bounded<__nv_bfloat16, false>(out + static_cast<int64_t>(r0) * pr.ld_out + c0, pr.ld_out, st,
+                                            pr.rows_out - r0, pr.cols_out - c0, vec);
+  else
+    blk_store_bounded<__nv_bfloat16, true>(out + static_cast<int64_t>(c0) * pr.ld_out + r0, pr.ld_out, st,
+                                           pr.rows_out - c0, pr.cols_out - r0, vec);
 }
 
 struct EpiAcc {
@@ -256,27 +312,68 @@ struct EpiAcc {
   float tr;  // trace contribution (EPI_GRAM)
 };
 
+// Operand blocks an epilogue reads besides the accumulator, loaded before
+// the accumulator so that their latency overlaps the TMEM load.
+struct EpiIn {
+  RawBlk a;  // D_l hi (squaring), S (NS squaring), X (NS apply)
+  RawBlk b;  // D_l lo (squaring, split operands)
+  RawBlk c;  // P, or T_0 (squaring)
+};
+
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProblem& pr,
-                                               const WorkItem& wi, int r, int c0, float* v,
-                                               EpiAcc& ea, float* st) {
-  const bool mirror = (wi.flags & 1) == 0;
+__device__ __forceinline__ void epilogue_load(const TcParams& p, const TcProblem& pr, int r0, int c0, EpiIn& in) {
+  if constexpr (EPI == EPI_SQR) {
+    const int64_t off = static_cast<int64_t>(r0) * pr.ld_aux + c0;
+    blk_load<__half>(in.a, static_cast<const __half*>(pr.aux0) + off, pr.ld_aux);
+    if (p.read_lo) blk_load<__half>(in.b, static_cast<const __half*>(pr.aux1) + off, pr.ld_aux);
+    if (p.p_mode >= 2) blk_load<float>(in.c, pr.pacc + off, pr.ld_aux);
+  } else if constexpr (EPI == EPI_NS_SQR) {
+    blk_load<__nv_bfloat16>(in.a, static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r0) * pr.ld_aux + c0,
+                            pr.ld_aux);
+  } else if constexpr (EPI == EPI_NS_APPLY) {
+    const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(pr.aux0);
+    const bool vec = (pr.ld_aux & 7) == 0;
+    if (!pr.out_trans)
+      blk_load_bounded<__nv_bfloat16>(in.a, X + static_cast<int64_t>(r0) * pr.ld_aux + c0, pr.ld_aux,
+                                      pr.rows_out - r0, pr.cols_out - c0, vec);
+    else
+      blk_load_bounded<__nv_bfloat16>(in.a, X + static_cast<int64_t>(c0) * pr.ld_aux + r0, pr.ld_aux,
+                                      pr.rows_out - c0, pr.cols_out - r0, vec);
+  }
+}
+
+// Fused elementwise work of a pass on one 32 x 32 block of the tile: u is
+// the accumulator block whose TMEM load has been issued (lane t: row r0 + t,
+// columns c0..c0+31); the wait for it comes as late as possible.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProblem& pr, const WorkItem& wi, int r0,
+                                               int c0, uint32_t (&u)[32], const EpiIn& in, EpiAcc& ea,
+                                               float* st) {
+  (void)wi;
+  const int r = r0 + static_cast<int>(threadIdx.x & 31);  // this lane's row
+  float v[32];
+  auto take = [&]() {
+    IFNSO_TMEM_WAIT_LD(u);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = u2f(u[j]);
+  };
+  if constexpr (EPI != EPI_SQR) take();
   if constexpr (EPI == EPI_GRAM) {
-    store_sym<float>(pr.pacc, pr.ld_aux, r, c0, v, mirror, st);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       ea.ss = fmaf(v[j], v[j], ea.ss);
       if (c0 + j == r) ea.tr += v[j];
     }
+    store_blk<float>(pr.pacc, pr.ld_aux, r0, c0, v, st);
   } else if constexpr (EPI == EPI_SQR) {
     float d[32], lo[32];
-    const int64_t off = static_cast<int64_t>(r) * pr.ld_aux + c0;
-    load_h32(static_cast<const __half*>(pr.aux0) + off, d);
+    blk_unpack<__half>(in.a, st, d);
     if (p.read_lo) {
-      load_h32(static_cast<const __half*>(pr.aux1) + off, lo);
+      blk_unpack<__half>(in.b, st, lo);
 #pragma unroll
       for (int j = 0; j < 32; ++j) d[j] += lo[j];
     }
+    take();
     // P = (1 + sum w) I - sum_l w_l D_l is accumulated two terms at a time:
     // p_mode 1 (first squaring) writes P = c0 I - w_l D_l - w_{l+1} D_{l+1},
     // p_mode 2 subtracts w_l D_l + w_{l+1} D_{l+1}, p_mode 3 only
@@ -289,7 +386,6 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     const float w = static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l));
     const float wp = (p.p_mode == 1 || p.p_mode == 2 || p.p_mode == 4)
                          ? static_cast<float>(coef_at(p.coef, pr.mat, p.coef_l - 1)) : 0.f;
-    float* P = pr.pacc + off;
     float pv[32];
     if (p.p_mode == 4) {
       // P = c0 I - w_1 D_1 - w_l D_l - w_{l+1} D_{l+1} with D_1 = T_0 / o read
@@ -297,25 +393,11 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       const float c0f = static_cast<float>(p.scal[pr.mat].c0);
       const float w1 = static_cast<float>(coef_at(p.coef, pr.mat, 1));
       const float inv = p.scal[pr.mat].inv_s2;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float4 t = reinterpret_cast<const float4*>(P)[j];
-        pv[4 * j] = t.x;
-        pv[4 * j + 1] = t.y;
-        pv[4 * j + 2] = t.z;
-        pv[4 * j + 3] = t.w;
-      }
+      blk_unpack<float>(in.c, st, pv);
 #pragma unroll
       for (int j = 0; j < 32; ++j) pv[j] = fmaf(-w1, pv[j] * inv, (c0 + j == r) ? c0f : 0.f);
     } else if (p.p_mode >= 2) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        float4 t = reinterpret_cast<const float4*>(P)[j];
-        pv[4 * j] = t.x;
-        pv[4 * j + 1] = t.y;
-        pv[4 * j + 2] = t.z;
-        pv[4 * j + 3] = t.w;
-      }
+      blk_unpack<float>(in.c, st, pv);
     } else {
       const float c0f = p.p_mode == 1 ? static_cast<float>(p.scal[pr.mat].c0) : 0.f;
 #pragma unroll
@@ -329,10 +411,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     }
     if (!p.final_pass) {
       if (p.p_mode != 0) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          reinterpret_cast<float4*>(P)[j] =
-              make_float4(pv[4 * j], pv[4 * j + 1], pv[4 * j + 2], pv[4 * j + 3]);
+        store_blk<float>(pr.pacc, pr.ld_aux, r0, c0, pv, st);
       }
       if (p.write_lo) {
 #pragma unroll
@@ -341,10 +420,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
           lo[j] = v[j] - hi;
           v[j] = hi;
         }
-        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
-        store_sym<__half>(static_cast<__half*>(pr.out1), pr.ld_out, r, c0, lo, mirror, st);
+        store_blk<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r0, c0, v, st);
+        store_blk<__half>(static_cast<__half*>(pr.out1), pr.ld_out, r0, c0, lo, st);
       } else {
-        store_sym<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
+        store_blk<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r0, c0, v, st);
       }
     } else {
       if (p.p_split) {
@@ -354,48 +433,52 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
           lo[j] = pv[j] - hi;
           pv[j] = hi;
         }
-        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror, st);
-        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out1), pr.ld_out, r, c0, lo, mirror, st);
+        store_blk<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r0, c0, pv, st);
+        store_blk<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out1), pr.ld_out, r0, c0, lo, st);
       } else {
-        store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, pv, mirror, st);
+        store_blk<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r0, c0, pv, st);
       }
     }
   } else if constexpr (EPI == EPI_APPLY) {
     const float s = p.scal[pr.mat].inv_s;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] *= s;
-    store_out_bf16(pr, r, c0, v, st);
+    store_out_bf16(pr, r0, c0, v, st);
   } else if constexpr (EPI == EPI_NS_GRAM) {
     const float s2 = p.ns_step == 0 ? p.scal[pr.mat].inv_s2 : 1.0f;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] *= s2;
-    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
+    store_blk<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r0, c0, v, st);
   } else if constexpr (EPI == EPI_NS_SQR) {
     float s[32];
-    load_b32(static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r) * pr.ld_aux + c0, s);
+    blk_unpack<__nv_bfloat16>(in.a, st, s);
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(p.ns_c, v[j], p.ns_b * s[j]);
-    store_sym<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r, c0, v, mirror, st);
+    store_blk<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r0, c0, v, st);
   } else if constexpr (EPI == EPI_NS_APPLY) {
     const float sc = p.ns_step == 0 ? p.scal[pr.mat].inv_s : 1.0f;
     float x[32];
-    load_x_bf16(pr, r, c0, x, st);
+    if (!pr.out_trans)
+      blk_unpack<__nv_bfloat16, false>(in.a, st, x);
+    else
+      blk_unpack<__nv_bfloat16, true>(in.a, st, x);
     const float ka = p.ns_a * sc, kb = p.ns_bcoef * sc;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(ka, x[j], kb * v[j]);
-    store_out_bf16(pr, r, c0, v, st);
+    store_out_bf16(pr, r0, c0, v, st);
   }
 }
 
 // ---------------------------------------------------------------- kernel
 
-template <int NA, int NB, int EPI>
+template <int NA, int NB, int EPI, int CG>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-  using C = Cfg<NA, NB>;
+  using C = Cfg<NA, NB, CG>;
   using PR = Products<NA, NB>;
   constexpr int S = C::stages;
   constexpr uint32_t kIsBf16 = (EPI == EPI_SQR) ? 0u : 1u;  // D_l are FP16, all else BF16
   constexpr uint16_t kPair = 0x3;                           // both CTAs of the cluster
+  constexpr bool kCl = (CG == 2);                           // barriers see arrivals of the peer CTA
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -413,29 +496,36 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  // A cluster of two CTAs computes the two 128-row halves of one 128 x 256
-  // pair of tiles: both need the same B tile, which each CTA loads half of and
-  // multicasts to both.
+  // A cluster of two CTAs computes the two 128-row halves of one 256 x 256
+  // pair of tiles: both need the same B tile, which each CTA loads half of
+  // (and, CG 1, multicasts to both).
   const int crank = static_cast<int>(cluster_ctarank());
   const int cid = static_cast<int>(cluster_id_x());
   const int ncl = static_cast<int>(cluster_count_x());
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), 2);  // freed by the MMAs of both CTAs (their B halves live here)
+      if constexpr (CG == 2) {
+        // even CTA: its own copies (expect_tx) + the relay of the odd CTA's copies
+        mbar_init(full_bar(s), crank == 0 ? 2 : 1);
+        mbar_init(empty_bar(s), 1);  // freed by the pair's MMAs (one commit, multicast)
+      } else {
+        mbar_init(full_bar(s), 1);
+        mbar_init(empty_bar(s), 2);  // freed by the MMAs of both CTAs (their B halves live here)
+      }
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 32 * kEpiWarps);
+      // CG 2: one arrival per epilogue warp of either CTA (the even CTA's issuer waits)
+      mbar_init(tempty_bar(a), CG == 2 ? 2 * kEpiWarps : 32 * kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), kTmemCols);
-    tmem_relinquish();
+    tmem_alloc<CG>(smem_u32(tmem_slot), kTmemCols);
+    tmem_relinquish<CG>();
   }
   tc_fence_before();
   __syncthreads();
@@ -465,23 +555,32 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           for (int a = 0; a < NA; ++a) tmap_acquire(&pr.mapA[a]);
 #pragma unroll
           for (int b = 0; b < NB; ++b) tmap_acquire(&pr.mapB[b]);
+          if (pr.sym) {
+#pragma unroll
+            for (int a = 0; a < (NA > NB ? NA : NB); ++a) tmap_acquire(&pr.mapT[a]);
+          }
         }
-        const int a_mn = pr.a_mn, b_mn = pr.b_mn;
         const int n_kb = pr.n_kb;
         const int tm = wi.tm + crank;
         for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, tmo)) {
+          if (!mbar_wait<kCl>(empty_bar(stage), phase ^ 1u, abort_flag, tmo)) {
             ok = false;
             break;
           }
           const uint32_t fb = full_bar(stage);
-          mbar_arrive_expect_tx(fb, C::stage_bytes);  // own A + both halves of B
+          // CG 1: own A + both halves of B; CG 2: own A + own half of B
+          mbar_arrive_expect_tx(fb, C::stage_bytes);
           const uint32_t st = base + stage * C::stage_bytes;
           const int k0 = kb * BK;
+          // K blocks left of the diagonal block of a symmetric operand come
+          // from the stored block across the diagonal, read MN-major
+          const bool at = (pr.sym & kSymA) && (kb >> 2) < (wi.tm >> 1);
+          const bool bt = (pr.sym & kSymB) && (kb >> 2) < wi.tn;
+          const int a_mn = pr.a_mn | at, b_mn = pr.b_mn | bt;
 #pragma unroll
           for (int a = 0; a < NA; ++a) {
             const uint32_t dst = st + a * kTileA;
-            const void* m = &pr.mapA[a];
+            const void* m = at ? &pr.mapT[a] : &pr.mapA[a];
             if (!a_mn) {
               tma_load_2d(dst, m, fb, k0, tm * BM);
             } else {
@@ -491,9 +590,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
 #pragma unroll
           for (int b = 0; b < NB; ++b) {
-            const uint32_t dst = st + NA * kTileA + b * kTileB;
-            const void* m = &pr.mapB[b];
-            if (!b_mn) {
+            const uint32_t dst = st + NA * kTileA + b * C::tile_b;
+            const void* m = bt ? &pr.mapT[b] : &pr.mapB[b];
+            if constexpr (CG == 2) {
+              // this CTA's half only, at the start of its B tile
+              if (!b_mn) {
+                tma_load_2d(dst, m, fb, k0, wi.tn * BN + 128 * crank);
+              } else {
+                tma_load_2d(dst, m, fb, wi.tn * BN + 128 * crank, k0);
+                tma_load_2d(dst + 8192, m, fb, wi.tn * BN + 128 * crank + 64, k0);
+              }
+            } else if (!b_mn) {
               // this CTA's half: rows [128 crank, 128 crank + 128) of the B tile
               tma_load_2d_mc(dst + 16384 * crank, m, fb, k0, wi.tn * BN + 128 * crank, kPair);
             } else {
@@ -518,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && (CG == 1 || crank == 0)) {
       // ------------------------------------------------ MMA issuer
       int stage = 0;
       uint32_t phase = 0;
@@ -531,56 +638,87 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         cur_mat = pr.mat;
         const int acc = local & 1;
         const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
-        if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, tmo)) {
+        if (!mbar_wait<kCl>(tempty_bar(acc), acc_phase ^ 1u, abort_flag, tmo)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
-        const uint32_t a_mn = static_cast<uint32_t>(pr.a_mn), b_mn = static_cast<uint32_t>(pr.b_mn);
-        const uint32_t idesc = idesc_f16(kIsBf16, BM, BN, a_mn, b_mn);
         const int n_kb = pr.n_kb;
         for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait(full_bar(stage), phase, abort_flag, tmo)) {
+          if (!mbar_wait<kCl>(full_bar(stage), phase, abort_flag, tmo)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t st = base + stage * C::stage_bytes;
+          // the layout the producer chose for this K block
+          const uint32_t a_mn = static_cast<uint32_t>(pr.a_mn | ((pr.sym & kSymA) && (kb >> 2) < (wi.tm >> 1)));
+          const uint32_t b_mn = static_cast<uint32_t>(pr.b_mn | ((pr.sym & kSymB) && (kb >> 2) < wi.tn));
+          const uint32_t idesc = idesc_f16(kIsBf16, CG * BM, BN, a_mn, b_mn);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
 #pragma unroll
             for (int q = 0; q < PR::n; ++q) {
               const uint32_t sa = st + PR::a(q) * kTileA;
-              const uint32_t sb = st + NA * kTileA + PR::b(q) * kTileB;
+              const uint32_t sb = st + NA * kTileA + PR::b(q) * C::tile_b;
               const uint64_t ad = a_mn ? sdesc_sw128(sa + k * 2048, 8192, 1024)
                                        : sdesc_sw128(sa + k * 32, 16, 1024);
               const uint64_t bd = b_mn ? sdesc_sw128(sb + k * 2048, 8192, 1024)
                                        : sdesc_sw128(sb + k * 32, 16, 1024);
-              umma_f16(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
+              umma_f16<CG>(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
             }
           }
           // frees the stage in both CTAs once these MMAs have read it
-          umma_commit_mc(empty_bar(stage), kPair);
+          umma_commit_mc<CG>(empty_bar(stage), kPair);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
           }
         }
         if (!ok) break;
-        umma_commit(tfull_bar(acc));  // accumulator ready for the epilogue
+        // accumulator ready for the epilogue (of both CTAs when the MMAs are the pair's)
+        if constexpr (CG == 2)
+          umma_commit_mc<CG>(tfull_bar(acc), kPair);
+        else
+          umma_commit<CG>(tfull_bar(acc));
       }
       if (!ok) set_timeout(p.scal, cur_mat);
       // make sure no MMA is still writing TMEM or reading shared memory
-      umma_commit(drain_bar);
+      umma_commit<CG>(drain_bar);
       mbar_wait_bounded(drain_bar, 0, tmo);
+    } else if (CG == 2 && lane == 0) {
+      // ------------------------------------------------ relay (odd CTA of a pair)
+      // Passes the completion of this CTA's copies of each stage on to the even
+      // CTA's stage barrier, where the issuer of the pair's MMAs waits.
+      int stage = 0;
+      uint32_t phase = 0;
+      int cur_mat = 0;
+      bool ok = true;
+      for (int it = cid; it < p.n_items && ok; it += ncl) {
+        const WorkItem wi = p.items[it];
+        const TcProblem& pr = p.probs[wi.prob];
+        cur_mat = pr.mat;
+        const int n_kb = pr.n_kb;
+        for (int kb = 0; kb < n_kb; ++kb) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_remote(mapa_shared(full_bar(stage), 0));
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) set_timeout(p.scal, cur_mat);
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
     float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256) + (warp - 2) * 32 * kStageLd;
     const int q = warp & 3;            // TMEM lane quadrant this warp may access
     const int half = (warp - 2) >> 2;  // which 128 of the tile's 256 columns
-    const int row_in_tile = q * 32 + lane;
     int local = 0;
     for (int it = cid; it < p.n_items; it += ncl, ++local) {
       const WorkItem wi = p.items[it];
@@ -589,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
       // one lane waits, the warp follows its verdict (tcgen05.ld needs a converged warp)
       int ready = 0;
-      if (lane == 0) ready = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, tmo) ? 1 : 0;
+      if (lane == 0) ready = mbar_wait<kCl>(tfull_bar(acc), acc_phase, abort_flag, tmo) ? 1 : 0;
       ready = __shfl_sync(0xffffffffu, ready, 0);
       if (!ready) {
         if (lane == 0) set_timeout(p.scal, pr.mat);
@@ -597,20 +735,30 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       tc_fence_after();
       const uint32_t tbase = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(acc * BN);
-      const int r = (wi.tm + crank) * BM + row_in_tile;
+      const int r0 = (wi.tm + crank) * BM + q * 32;  // first of this warp's 32 rows
       EpiAcc ea{0.f, 0.f};
 #pragma unroll 1
       for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
+        const int c0 = wi.tn * BN + ch * 32;
+        EpiIn in;
+        epilogue_load<EPI>(p, pr, r0, c0, in);
         uint32_t u[32];
         IFNSO_TMEM_LD32(tbase + static_cast<uint32_t>(ch * 32), u);
-        IFNSO_TMEM_WAIT_LD(u);
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = u2f(u[j]);
-        epilogue_chunk<EPI>(p, pr, wi, r, wi.tn * BN + ch * 32, v, ea, stage);
+        epilogue_chunk<EPI>(p, pr, wi, r0, c0, u, in, ea, stage);
       }
       tc_fence_before();
-      mbar_arrive(tempty_bar(acc));
+      if constexpr (CG == 2) {
+        // the issuer of the pair's MMAs (even CTA) waits for the epilogues of both CTAs
+        __syncwarp();
+        if (lane == 0) {
+          if (crank == 0)
+            mbar_arrive(tempty_bar(acc));
+          else
+            mbar_arrive_remote(mapa_shared(tempty_bar(acc), 0));
+        }
+      } else {
+        mbar_arrive(tempty_bar(acc));
+      }
       if constexpr (EPI == EPI_GRAM) {
         float ss = ea.ss, tr = ea.tr;
 #pragma unroll
@@ -635,18 +783,21 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   }
 
   __syncthreads();
+  // CG 2: the odd CTA's TMEM is written by MMAs issued in the even CTA, whose
+  // issuer has drained them by now; release the pair's TMEM only after that
+  if constexpr (CG == 2) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, kTmemCols);
+    tmem_dealloc<CG>(tmem_base, kTmemCols);
   }
   // neither CTA leaves while the other may still multicast into it or arrive on its barriers
   cluster_sync();
 }
 
-template <int NA, int NB, int EPI>
+template <int NA, int NB, int EPI, int CG>
 cudaError_t launch_one(const TcParams& p, int max_clusters, cudaStream_t s) {
-  using C = Cfg<NA, NB>;
-  auto kern = tc_gemm_kernel<NA, NB, EPI>;
+  using C = Cfg<NA, NB, CG>;
+  auto kern = tc_gemm_kernel<NA, NB, EPI, CG>;
   static int active_clusters = 0;  // per process and instantiation
   if (active_clusters == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::smem);
@@ -687,35 +838,44 @@ cudaError_t launch_one(const TcParams& p, int max_clusters, cudaStream_t s) {
   return e;
 }
 
+template <int CG>
+cudaError_t dispatch(int epi, int na, const TcParams& p, int max_clusters, cudaStream_t s) {
+  switch (epi) {
+    case EPI_GRAM:
+      return launch_one<1, 1, EPI_GRAM, CG>(p, max_clusters, s);
+    case EPI_SQR:
+      if (na == 2) return launch_one<2, 2, EPI_SQR, CG>(p, max_clusters, s);
+      return launch_one<1, 1, EPI_SQR, CG>(p, max_clusters, s);
+    case EPI_APPLY:
+      if (na == 2) return launch_one<2, 1, EPI_APPLY, CG>(p, max_clusters, s);
+      return launch_one<1, 1, EPI_APPLY, CG>(p, max_clusters, s);
+    case EPI_NS_GRAM:
+      return launch_one<1, 1, EPI_NS_GRAM, CG>(p, max_clusters, s);
+    case EPI_NS_SQR:
+      return launch_one<1, 1, EPI_NS_SQR, CG>(p, max_clusters, s);
+    case EPI_NS_APPLY:
+      return launch_one<1, 1, EPI_NS_APPLY, CG>(p, max_clusters, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
-int tc_smem_bytes(int na, int nb) {
-  if (na == 1 && nb == 1) return Cfg<1, 1>::smem;
-  if (na == 2 && nb == 2) return Cfg<2, 2>::smem;
-  if (na == 2 && nb == 1) return Cfg<2, 1>::smem;
+int tc_smem_bytes(int na, int nb, int cta_group) {
+  const bool pair = (cta_group == 2);
+  if (na == 1 && nb == 1) return pair ? Cfg<1, 1, 2>::smem : Cfg<1, 1, 1>::smem;
+  if (na == 2 && nb == 2) return pair ? Cfg<2, 2, 2>::smem : Cfg<2, 2, 1>::smem;
+  if (na == 2 && nb == 1) return pair ? Cfg<2, 1, 2>::smem : Cfg<2, 1, 1>::smem;
   return -1;
 }
 
 cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s) {
+  (void)nb;  // the operand counts of each pass are fixed by (epi, na)
   if (p.n_items == 0) return cudaSuccess;
-  switch (epi) {
-    case EPI_GRAM:
-      return launch_one<1, 1, EPI_GRAM>(p, max_clusters, s);
-    case EPI_SQR:
-      if (na == 2) return launch_one<2, 2, EPI_SQR>(p, max_clusters, s);
-      return launch_one<1, 1, EPI_SQR>(p, max_clusters, s);
-    case EPI_APPLY:
-      if (na == 2) return launch_one<2, 1, EPI_APPLY>(p, max_clusters, s);
-      return launch_one<1, 1, EPI_APPLY>(p, max_clusters, s);
-    case EPI_NS_GRAM:
-      return launch_one<1, 1, EPI_NS_GRAM>(p, max_clusters, s);
-    case EPI_NS_SQR:
-      return launch_one<1, 1, EPI_NS_SQR>(p, max_clusters, s);
-    case EPI_NS_APPLY:
-      return launch_one<1, 1, EPI_NS_APPLY>(p, max_clusters, s);
-    default:
-      return cudaErrorInvalidValue;
-  }
+  if (p.cta_group == 2) return dispatch<2>(epi, na, p, max_clusters, s);
+  if (p.cta_group == 1) return dispatch<1>(epi, na, p, max_clusters, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace ifnso

@@ -51,3 +51,15 @@ def to_np(t):
 def rel(a, b):
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def sym_upper(G, block=256):
+    """The symmetric matrix a BF16 plan keeps on its upper block x block blocks
+    (element (i, j) with i // block > j // block is read at (j, i))."""
+    G = np.array(G, dtype=np.float64, copy=True)
+    n = G.shape[0]
+    bi = np.arange(n)[:, None] // block
+    bj = np.arange(n)[None, :] // block
+    low = bi > bj
+    G[low] = G.T[low]
+    return G

@@ -9,14 +9,14 @@ import pytest
 import synth
 from oracle import ifnso as O
 from oracle import ns as ONS
-from tests.gpu_util import coeffs, lib, rel, to_dev, to_np
+from tests.gpu_util import coeffs, lib, rel, sym_upper, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-5, "bf16": 2e-2}
 
 
-def run_ifnso(mats, L, dtype, precision=None, scale=None, stop_after=None, plan_shape=None):
+def run_ifnso(mats, L, dtype, precision=None, scale=None, stop_after=None, plan_shape=None, cta_group=None):
     import torch
 
     F = lib()
@@ -27,6 +27,8 @@ def run_ifnso(mats, L, dtype, precision=None, scale=None, stop_after=None, plan_
     plan = F.Plan(*(plan_shape or (hmax, wmax)), dtype, L=L, precision=precision, scale=scale)
     if stop_after is not None:
         plan.set(F.IFNSO_OPT_STOP_AFTER, stop_after)
+    if cta_group is not None:
+        plan.set(F.IFNSO_OPT_CTA_GROUP, cta_group)
     b = F.Batch(xs)
     w = coeffs(L)
     plan.orthogonalize(b, np.r_[1.0, w], ys)
@@ -79,7 +81,7 @@ def test_bf16_gram(shape):
     M = synth.gaussian(2, *shape)
     F, plan, b, xs, ys, w = run_ifnso([M], 4, "bf16", stop_after=0)
     ptr, ld = plan.workspace_view(b, 0, 0)
-    G = F.tensor_at(ptr, (ld, ld), torch.float32, plan._last_ws.buf).double().cpu().numpy()
+    G = sym_upper(F.tensor_at(ptr, (ld, ld), torch.float32, plan._last_ws.buf).double().cpu().numpy())
     A = O.orient(to_np(xs[0]))[0]
     h = A.shape[0]
     ref = A @ A.T
@@ -101,6 +103,7 @@ def test_bf16_prep(precision):
     if precision == "split":
         ptr2, _ = plan.workspace_view(b, 0, 2)
         D = D + F.tensor_at(ptr2, (ld, ld), torch.float16, plan._last_ws.buf).double().cpu().numpy()
+    D = sym_upper(D)
     A = to_np(xs[0])
     G = A @ A.T
     ref = G / np.linalg.norm(G)
@@ -120,6 +123,38 @@ def test_bf16_ifnso(shape, L, precision):
     ref = O.ifnso_alg1(A, w)
     err = rel(to_np(ys[0]), ref)
     assert err < TOL["bf16"], err
+
+
+@pytest.mark.parametrize("L,precision", [(4, "plain"), (14, "mixed"), (3, "split")])
+@pytest.mark.parametrize("shape", [(256, 512), (392, 136), (640, 1000), (1000, 640)])
+def test_bf16_cta_groups(shape, L, precision):
+    """Per-CTA MMAs (B multicast) and MMAs of the CTA pair give the same
+    products up to the rounding order of the accumulation."""
+    M = synth.gaussian(40, *shape)
+    out = {}
+    for cg in (1, 2):
+        F, plan, b, xs, ys, w = run_ifnso([M], L, "bf16", precision=precision, cta_group=cg)
+        assert plan.get(F.IFNSO_OPT_CTA_GROUP) == cg
+        st, _, _ = plan.device_status(1)
+        assert st[0] == 0
+        out[cg] = to_np(ys[0])
+        assert rel(out[cg], O.ifnso_alg1(to_np(xs[0]), w)) < TOL["bf16"]
+    assert rel(out[1], out[2]) < 1e-3
+
+
+@pytest.mark.parametrize("cg", [1, 2])
+def test_bf16_ns_cta_groups(cg):
+    import torch
+
+    F = lib()
+    M = synth.gaussian(41, 392, 136)
+    x = to_dev(M, "bf16")
+    y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
+    plan = F.Plan(136, 392, "bf16", L=1)
+    plan.set(F.IFNSO_OPT_CTA_GROUP, cg)
+    plan.ns_iterate(F.Batch([x]), ONS.MUON_ABC, 5, [y])
+    torch.cuda.synchronize()
+    assert rel(to_np(y), ONS.ns_generic(to_np(x), ONS.MUON_ABC, 5)) < 5e-2
 
 
 def test_bf16_batch_heterogeneous():
