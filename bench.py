@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
     ap.add_argument("--cta-group", type=int, default=1, choices=[1, 2],
                     help="tensor-core passes: MMAs of the CTA pair (2) or per-CTA MMAs with B multicast (1)")
+    ap.add_argument("--groups", type=int, default=0,
+                    help="end-to-end run: groups whose copies overlap the passes (0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
@@ -430,7 +432,9 @@ def main():
     ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
     del nsws, zs
 
-    # end to end through the C ABI with host buffers: H2D inputs, the call, D2H outputs
+    # end to end through the C ABI with host buffers: ifnso_orthogonalize_host
+    # uploads the inputs, runs the passes and downloads the results, group by
+    # group on overlapping streams
     e2e = None
     if not args.no_e2e:
         hin = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
@@ -440,13 +444,9 @@ def main():
         bi = sum(x.numel() * x.element_size() for x in xs)
 
         def e2e_step():
-            for h_, x in zip(hin, xs):
-                x.copy_(h_, non_blocking=True)
-            plan.orthogonalize(batch, coef, ys, ws=ws)
-            for h_, y in zip(hout, ys):
-                h_.copy_(y, non_blocking=True)
+            plan.orthogonalize_host(hin, batch, coef, ys, hout, groups=args.groups, ws=ws)
 
-        for _ in range(2):
+        for _ in range(max(args.warmup, 3)):
             e2e_step()
         torch.cuda.synchronize()
         barrier()
@@ -458,7 +458,9 @@ def main():
         barrier()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1))
         e2e = {"value": whole_job_rate(world, n, args.steps, e2e_ms), "unit": "matrices/s",
-               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "ms_per_step": e2e_ms / args.steps}
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "ms_per_step": e2e_ms / args.steps,
+               "api": "ifnso_orthogonalize_host, page-locked host buffers, "
+                      + (f"{args.groups} groups" if args.groups > 0 else "default grouping")}
         plan.pass_times()
 
     cpu = None

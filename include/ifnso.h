@@ -186,6 +186,30 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
                                  const ifnso_coeffs* coeffs, void* const* out,
                                  void* workspace, size_t workspace_bytes, ifnso_stream_t stream);
 
+/* ifnso_orthogonalize (Algorithm 1, Sec. 2.4) for matrices held in host
+ * memory; the copies and their overlap with the passes have no counterpart
+ * in the paper.  host_in[i] holds matrix i in the layout dev_batch gives it
+ * (rows[i] x cols[i], leading dimension ld[i], the plan's dtype); the call
+ * copies it to dev_batch->in[i] (device memory the caller owns), runs every
+ * pass, and copies the result from dev_out[i] (device, as `out` of
+ * ifnso_orthogonalize) to host_out[i] (host, rows[i] x cols[i] contiguous).
+ * The batch is cut into `groups` contiguous groups of about equal work (0
+ * means 8; at most the batch count; F32 plans use one): the uploads run on a
+ * copy stream of the plan, the downloads on another, and each group's passes
+ * start as soon as its inputs have arrived, so the call costs about the
+ * larger of the copies and the passes rather than their sum.  Host buffers
+ * must be page-locked for the copies to overlap anything.  Asynchronous:
+ * everything the call does is ordered after earlier work on `stream` and
+ * before later work on it; the host buffers must stay untouched until then.
+ * Per-pass timing events (IFNSO_OPT_TIMING) and IFNSO_OPT_STOP_AFTER do not
+ * apply.  Errors: IFNSO_ERR_INVALID_ARG for a NULL or misaligned pointer or
+ * any argument ifnso_orthogonalize rejects; IFNSO_ERR_CUDA if a copy or a
+ * launch fails (copies already queued then still run). */
+ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_in,
+                                      const ifnso_batch_desc* dev_batch, const ifnso_coeffs* coeffs,
+                                      void* const* dev_out, void* const* host_out, void* workspace,
+                                      size_t workspace_bytes, int32_t groups, ifnso_stream_t stream);
+
 /* The comparison baseline, Newton-Schulz: X_0 = A/||A||_F (Eq. constraint),
  * then `steps` times X <- sum_n poly[n] (X X^T)^n X (Eq. general_eq_matrix):
  * degree 3 takes poly = (a, b) (the classical iteration is (1.5, -0.5),

@@ -42,6 +42,12 @@ struct ifnso_plan {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::vector<cudaEvent_t>> ev_calls;
   std::vector<std::vector<cudaEvent_t>> ev_graph;  // recorded by captured calls (kept for replays)
+  // ifnso_orthogonalize_host: copy streams and the events that order them
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_last = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_done;
+  int groups = 1;  // groups the item lists of the cached metadata are built for
+  std::vector<size_t> sym_off, app_off;  // first work item of each group
   std::mutex mu;
 };
 
@@ -231,40 +237,70 @@ Prec resolve_prec(const ifnso_plan* p) {
   return r;
 }
 
-void sym_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
-  // heavy matrices first (longer K first for the Gram; equal for squarings)
-  std::vector<int> order(shp.size());
-  for (size_t i = 0; i < shp.size(); ++i) order[i] = static_cast<int>(i);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return shp[a].hpad * shp[a].w > shp[b].hpad * shp[b].w;
-  });
-  // one item per upper 256 x 256 block (I <= J): its two 128-row halves go
-  // to the two CTAs of a cluster
-  for (int m : order) {
-    const int nb = static_cast<int>(shp[m].hpad / 256);
-    for (int I = 0; I < nb; ++I)
-      for (int J = I; J < nb; ++J)
-        items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * I), static_cast<uint16_t>(J),
-                                 static_cast<uint16_t>(I == J ? 1 : 0)});
+// Matrices [b[g], b[g + 1]) form group g: contiguous index ranges of about
+// equal work (h_pad^2 w each), at most `groups` of them, none empty.
+std::vector<int> group_bounds(const std::vector<Shape>& shp, int groups) {
+  const int n = static_cast<int>(shp.size());
+  std::vector<int> b{0};
+  double total = 0.0;
+  for (const Shape& s : shp) total += static_cast<double>(s.hpad) * s.hpad * s.w;
+  double acc = 0.0;
+  for (int i = 0; i + 1 < n; ++i) {
+    acc += static_cast<double>(shp[i].hpad) * shp[i].hpad * shp[i].w;
+    const int g = static_cast<int>(b.size());
+    if (g < groups && acc >= total * g / groups) b.push_back(i + 1);
   }
+  b.push_back(n);
+  return b;
 }
 
-void app_items(const std::vector<Shape>& shp, std::vector<WorkItem>& items) {
-  std::vector<int> order(shp.size());
-  for (size_t i = 0; i < shp.size(); ++i) order[i] = static_cast<int>(i);
+// Matrices of [first, last), heaviest first (longer K first for the Gram and
+// the product; equal for squarings).
+std::vector<int> heavy_first(const std::vector<Shape>& shp, int first, int last) {
+  std::vector<int> order;
+  for (int i = first; i < last; ++i) order.push_back(i);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return shp[a].hpad * shp[a].w > shp[b].hpad * shp[b].w;
   });
-  // one item per pair of 128-row tiles sharing a 256-column block (rows past
-  // h are computed on zero padding and not stored)
-  for (int m : order) {
-    const int pairs = static_cast<int>((shp[m].h + 2 * BM - 1) / (2 * BM));
-    const int tns = static_cast<int>((shp[m].w + BN - 1) / BN);
-    for (int tn = 0; tn < tns; ++tn)
-      for (int pr = 0; pr < pairs; ++pr)
-        items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * pr),
-                                 static_cast<uint16_t>(tn), 0});
+  return order;
+}
+
+// Work items of the symmetric passes, group after group; off[g] = first item of group g.
+void sym_items(const std::vector<Shape>& shp, const std::vector<int>& gb, std::vector<WorkItem>& items,
+               std::vector<size_t>* off = nullptr) {
+  if (off) off->clear();
+  for (size_t g = 0; g + 1 < gb.size(); ++g) {
+    if (off) off->push_back(items.size());
+    // one item per upper 256 x 256 block (I <= J): its two 128-row halves go
+    // to the two CTAs of a cluster
+    for (int m : heavy_first(shp, gb[g], gb[g + 1])) {
+      const int nb = static_cast<int>(shp[m].hpad / 256);
+      for (int I = 0; I < nb; ++I)
+        for (int J = I; J < nb; ++J)
+          items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * I),
+                                   static_cast<uint16_t>(J), static_cast<uint16_t>(I == J ? 1 : 0)});
+    }
   }
+  if (off) off->push_back(items.size());
+}
+
+void app_items(const std::vector<Shape>& shp, const std::vector<int>& gb, std::vector<WorkItem>& items,
+               std::vector<size_t>* off = nullptr) {
+  if (off) off->clear();
+  for (size_t g = 0; g + 1 < gb.size(); ++g) {
+    if (off) off->push_back(items.size());
+    // one item per pair of 128-row tiles sharing a 256-column block (rows past
+    // h are computed on zero padding and not stored)
+    for (int m : heavy_first(shp, gb[g], gb[g + 1])) {
+      const int pairs = static_cast<int>((shp[m].h + 2 * BM - 1) / (2 * BM));
+      const int tns = static_cast<int>((shp[m].w + BN - 1) / BN);
+      for (int tn = 0; tn < tns; ++tn)
+        for (int pr = 0; pr < pairs; ++pr)
+          items.push_back(WorkItem{static_cast<uint16_t>(m), static_cast<uint16_t>(2 * pr),
+                                   static_cast<uint16_t>(tn), 0});
+    }
+  }
+  if (off) off->push_back(items.size());
 }
 
 Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns, int steps, int K) {
@@ -292,8 +328,9 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   }
   if (!ly.f32) {
     std::vector<WorkItem> a, b;
-    sym_items(shp, a);
-    app_items(shp, b);
+    const std::vector<int> all{0, static_cast<int>(shp.size())};
+    sym_items(shp, all, a);
+    app_items(shp, all, b);
     ly.n_sym = a.size();
     ly.n_app = b.size();
   }
@@ -460,7 +497,7 @@ CUtensorMapDataType f16_t() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 
 // ---------------------------------------------------------------- IFNSO metadata
 ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void* const* out, uint8_t* ws,
-                              const double* host_coef, int K, uint8_t* meta) {
+                              const double* host_coef, int K, const std::vector<int>& gb, uint8_t* meta) {
   memset(meta, 0, ly.meta_bytes);
   const int n = ly.count;
   MatInfo* mats = reinterpret_cast<MatInfo*>(meta + ly.off_mats);
@@ -606,8 +643,8 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     a.out0 = mi.out;
   }
   std::vector<WorkItem> sy, ap;
-  sym_items(ly.shp, sy);
-  app_items(ly.shp, ap);
+  sym_items(ly.shp, gb, sy);
+  app_items(ly.shp, gb, ap);
   memcpy(meta + ly.off_items_sym, sy.data(), sy.size() * sizeof(WorkItem));
   memcpy(meta + ly.off_items_app, ap.data(), ap.size() * sizeof(WorkItem));
   return IFNSO_OK;
@@ -737,8 +774,9 @@ ifnso_status build_ns_meta(const Layout& ly, const ifnso_batch_desc* b, void* co
     q.out0 = mi.b;
   }
   std::vector<WorkItem> sy, ap;
-  sym_items(ly.shp, sy);
-  app_items(ly.shp, ap);
+  const std::vector<int> all{0, n};
+  sym_items(ly.shp, all, sy);
+  app_items(ly.shp, all, ap);
   memcpy(meta + ly.off_items_sym, sy.data(), sy.size() * sizeof(WorkItem));
   memcpy(meta + ly.off_items_app, ap.data(), ap.size() * sizeof(WorkItem));
   return IFNSO_OK;
@@ -879,6 +917,225 @@ ifnso_status mlp_ensure_batch(ifnso_mlp* m, int batch) {
   return IFNSO_OK;
 }
 
+// Arguments of an IFNSO call (shapes into shp).
+ifnso_status check_call(const ifnso_plan* plan, const ifnso_batch_desc* batch, const ifnso_coeffs* coeffs,
+                        void* const* out, std::vector<Shape>& shp) {
+  ifnso_status st = read_batch(plan, batch, shp);
+  if (st != IFNSO_OK) return st;
+  if (!coeffs || coeffs->K != plan->L + 1 ||
+      (coeffs->host ? 1 : 0) + (coeffs->device ? 1 : 0) + (coeffs->mlp ? 1 : 0) != 1)
+    return fail(IFNSO_ERR_INVALID_ARG, "coefficients: need K = %d and exactly one of host/device/mlp", plan->L + 1);
+  if (coeffs->mlp) {
+    if (coeffs->mlp->K != coeffs->K) return fail(IFNSO_ERR_INVALID_ARG, "coefficient network has K = %d", coeffs->mlp->K);
+    if (plan->L < 3) return fail(IFNSO_ERR_INVALID_ARG, "proposed coefficients need L >= 3");
+    if (plan->dtype != IFNSO_BF16) return fail(IFNSO_ERR_UNSUPPORTED, "proposed coefficients need a BF16 plan");
+  }
+  if (!out) return fail(IFNSO_ERR_INVALID_ARG, "out is NULL");
+  for (int i = 0; i < batch->count; ++i) {
+    if (!out[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is NULL", i);
+    if (out[i] == batch->in[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] aliases the input", i);
+    if (reinterpret_cast<uintptr_t>(out[i]) % 16 != 0)
+      return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is not 16-byte aligned", i);
+  }
+  return IFNSO_OK;
+}
+
+// Copy streams and events of ifnso_orthogonalize_host (created on first use).
+ifnso_status ensure_copy_streams(ifnso_plan* plan, int groups) {
+  if (!plan->s_in) {
+    IFNSO_CUDA(cudaStreamCreateWithFlags(&plan->s_in, cudaStreamNonBlocking), "cudaStreamCreate");
+    IFNSO_CUDA(cudaStreamCreateWithFlags(&plan->s_out, cudaStreamNonBlocking), "cudaStreamCreate");
+    IFNSO_CUDA(cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming), "cudaEventCreate");
+    IFNSO_CUDA(cudaEventCreateWithFlags(&plan->ev_last, cudaEventDisableTiming), "cudaEventCreate");
+  }
+  for (auto* v : {&plan->ev_in, &plan->ev_done})
+    while (static_cast<int>(v->size()) < groups) {
+      cudaEvent_t e;
+      IFNSO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+      v->push_back(e);
+    }
+  return IFNSO_OK;
+}
+
+// Build and upload the metadata of an IFNSO call unless the cached copy
+// already describes it (item lists grouped by gb).
+ifnso_status upload_ifnso_meta(ifnso_plan* plan, const Layout& ly, const ifnso_batch_desc* batch, void* const* out,
+                               uint8_t* ws, const ifnso_coeffs* coeffs, const std::vector<int>& gb,
+                               cudaStream_t stream) {
+  const int groups = static_cast<int>(gb.size()) - 1;
+  const uint64_t sig = batch_sig(plan, batch, out, ws, coeffs, nullptr, 0, 0, 1000 + groups);
+  if (plan->sig_valid && plan->sig == sig) return IFNSO_OK;
+  ifnso_status st;
+  if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
+  uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
+  if ((st = build_ifnso_meta(ly, batch, out, ws, coeffs->host, coeffs->K, gb, meta)) != IFNSO_OK) return st;
+  IFNSO_CUDA(cudaMemcpyAsync(ws, meta, ly.meta_bytes, cudaMemcpyHostToDevice, stream), "metadata upload");
+  std::vector<WorkItem> tmp;
+  sym_items(ly.shp, gb, tmp, &plan->sym_off);
+  tmp.clear();
+  app_items(ly.shp, gb, tmp, &plan->app_off);
+  plan->sig = sig;
+  plan->sig_valid = true;
+  plan->groups = groups;
+  return IFNSO_OK;
+}
+
+// What the passes of one IFNSO call share.
+struct Run {
+  ifnso_plan* plan;
+  const Layout* ly;
+  uint8_t* ws;
+  const ifnso_coeffs* coeffs;
+  int hpad_max;
+  cudaStream_t stream;
+  bool whole;  // the whole batch in one go: per-pass timing events and IFNSO_OPT_STOP_AFTER apply
+};
+
+// Coefficient rows of matrix `first` onwards (the SIMT kernels index a group from 0).
+CoefTable shifted(CoefTable t, int first) {
+  if (t.f32) t.f32 += static_cast<int64_t>(first) * t.stride;
+  return t;
+}
+
+// FP32 plans: every pass of Algorithm 1 on the whole batch with the SIMT kernels.
+ifnso_status run_f32(const Run& r) {
+  ifnso_plan* plan = r.plan;
+  const Layout& ly = *r.ly;
+  uint8_t* ws = r.ws;
+  cudaStream_t stream = r.stream;
+  const int n = ly.count;
+  const int L = ly.L;
+  const int frob = plan->scale == IFNSO_SCALE_FROB;
+  MatInfo* d_mats = reinterpret_cast<MatInfo*>(ws + ly.off_mats);
+  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
+  IFNSO_CUDA(mark(plan, stream, true), "timing event");
+  SgParams p = base_params<SgParams>(ws, ly, r.coeffs);
+  const SgProblem* probs = reinterpret_cast<const SgProblem*>(ws + ly.off_probs);
+  int max_h = 0, max_w = 0;
+  for (auto& s : ly.shp) {
+    max_h = std::max<int>(max_h, static_cast<int>(s.h));
+    max_w = std::max<int>(max_w, static_cast<int>(s.w));
+  }
+  // the Gram is computed over the whole padded h_pad x h_pad block (zeros beyond h)
+  p.probs = probs + ly.pi_gram;
+  IFNSO_CUDA(sg_launch(EPI_GRAM, p, n, r.hpad_max, r.hpad_max, stream), "FP32 Gram");
+  IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
+  if (plan->stop_after == 0) return IFNSO_OK;
+  IFNSO_CUDA(launch_prep(d_mats, n, r.hpad_max, p.scal, p.coef, L, 0, 1, stream), "prep");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
+  if (plan->stop_after == 1) return IFNSO_OK;
+  for (int j = 1; j <= L - 1; ++j) {
+    const int par = (j - 1) % 2;
+    p.probs = probs + ly.pi_sqr + par * n;
+    p.coef_l = j + 1;
+    p.final_pass = (j == L - 1);
+    IFNSO_CUDA(sg_launch(EPI_SQR, p, n, r.hpad_max, r.hpad_max, stream), "FP32 squaring");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
+    if (plan->stop_after == 1 + j) return IFNSO_OK;
+  }
+  p.probs = probs + ly.pi_apply;
+  p.coef_l = 0;
+  p.final_pass = 0;
+  IFNSO_CUDA(sg_launch(EPI_APPLY, p, n, max_h, max_w, stream), "FP32 apply");
+  IFNSO_CUDA(mark(plan, stream, false), "timing event");
+  return IFNSO_OK;
+}
+
+// BF16 plans: every pass of Algorithm 1 for matrices [first, first + count),
+// whose work items are [sym0, sym1) and [app0, app1) of the metadata's lists.
+ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1, size_t app0, size_t app1) {
+  ifnso_plan* plan = r.plan;
+  const Layout& ly = *r.ly;
+  uint8_t* ws = r.ws;
+  cudaStream_t stream = r.stream;
+  const int L = ly.L;
+  const int frob = plan->scale == IFNSO_SCALE_FROB;
+  const bool whole = r.whole;
+  MatInfo* d_mats = reinterpret_cast<MatInfo*>(ws + ly.off_mats) + first;
+  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal + first * sizeof(MatScalars), 0, count * sizeof(MatScalars), stream),
+             "scalar reset");
+  auto mark_pass = [&](bool start) { return whole ? mark(plan, stream, start) : cudaSuccess; };
+  auto stop = [&](int stage) { return whole && plan->stop_after == stage; };
+  IFNSO_CUDA(mark_pass(true), "timing event");
+  TcParams p = base_params<TcParams>(ws, ly, r.coeffs);
+  // the tensor-core passes address scalars and coefficient rows by matrix
+  // index; the SIMT kernels by position in the group
+  MatScalars* scal = p.scal + first;
+  const CoefTable coef = shifted(p.coef, first);
+  const TcProblem* probs = reinterpret_cast<const TcProblem*>(ws + ly.off_probs);
+  const WorkItem* sym = reinterpret_cast<const WorkItem*>(ws + ly.off_items_sym) + sym0;
+  const WorkItem* app = reinterpret_cast<const WorkItem*>(ws + ly.off_items_app) + app0;
+  const size_t n_sym = sym1 - sym0, n_app = app1 - app0;
+  const int n = ly.count;
+  const Prec& pc = ly.prec;
+  p.p_split = pc.p_split;
+  p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
+  p.cta_group = plan->cta_group;
+  p.probs = probs + ly.pi_gram;
+  p.items = sym;
+  p.n_items = static_cast<int32_t>(n_sym);
+  p.inject = plan->inject_stall;
+  IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, n_sym), stream), "Gram pass");
+  p.inject = 0;
+  const ifnso_mlp* net = r.coeffs->mlp;
+  if (net) {
+    // until the network has spoken, the scalars see the fixed coefficients
+    CoefTable fixed{nullptr, net->wslots, r.coeffs->K, 0};
+    IFNSO_CUDA(launch_scalars(d_mats, count, scal, fixed, L, frob, 0, stream), "scalars");
+  } else {
+    IFNSO_CUDA(launch_scalars(d_mats, count, scal, coef, L, frob, 0, stream), "scalars");
+  }
+  IFNSO_CUDA(mark_pass(false), "timing event");
+  if (stop(0)) return IFNSO_OK;
+  // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo)
+  const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
+  IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream), "prep");
+  IFNSO_CUDA(mark_pass(false), "timing event");
+  if (stop(1)) return IFNSO_OK;
+  for (int j = 1; j <= L - 1; ++j) {
+    const int par = (j - 1) % 2;
+    const int split = j <= pc.k_split ? 1 : 0;
+    p.probs = probs + ly.pi_sqr + par * n;
+    p.items = sym;
+    p.n_items = static_cast<int32_t>(n_sym);
+    p.coef_l = j + 1;
+    p.final_pass = (j == L - 1);
+    p.read_lo = split;
+    p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
+    if (!net) {
+      // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
+      // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
+      p.p_mode = j == 1 ? 1 : ((j & 1) ? 2 : (j == L - 1 ? 3 : 0));
+      p.feat = 0;
+    } else {
+      // proposed coefficients: squaring 1 only measures tr(D_1^4); squaring 2
+      // writes P from T_0, D_2 and D_3; even squarings add D_j and D_{j+1};
+      // an odd last squaring adds D_L
+      p.p_mode = j == 1 ? 0 : (j == 2 ? 4 : ((j & 1) == 0 ? 2 : (j == L - 1 ? 3 : 0)));
+      p.feat = j == 1 ? 1 : 0;
+    }
+    IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, n_sym), stream), "squaring pass");
+    if (net && j == 1) {
+      IFNSO_CUDA(mlp_infer(net->prm, net->K, net->wfix, net->scale, net->stats, d_mats, scal, count,
+                           reinterpret_cast<float*>(ws + ly.off_rows) + static_cast<int64_t>(first) * kRowSlots,
+                           kRowSlots, stream),
+                 "coefficient proposal");
+    }
+    IFNSO_CUDA(mark_pass(false), "timing event");
+    if (stop(1 + j)) return IFNSO_OK;
+  }
+  p.probs = probs + ly.pi_apply;
+  p.items = app;
+  p.n_items = static_cast<int32_t>(n_app);
+  p.coef_l = 0;
+  p.final_pass = 0;
+  p.read_lo = p.write_lo = 0;
+  IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream), "apply pass");
+  IFNSO_CUDA(mark_pass(false), "timing event");
+  return IFNSO_OK;
+}
+
 }  // namespace
 
 void ifnso::count_launch(int n) { g_launches += static_cast<uint64_t>(n); }
@@ -979,6 +1236,16 @@ ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
     for (auto& c : *list)
       for (cudaEvent_t e : c) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
+  if (plan->s_in) {
+    cudaStreamSynchronize(plan->s_in);
+    cudaStreamSynchronize(plan->s_out);
+    cudaStreamDestroy(plan->s_in);
+    cudaStreamDestroy(plan->s_out);
+    cudaEventDestroy(plan->ev_start);
+    cudaEventDestroy(plan->ev_last);
+  }
+  for (auto* v : {&plan->ev_in, &plan->ev_done})
+    for (cudaEvent_t e : *v) cudaEventDestroy(e);
   if (plan->meta_host) {
     cudaDeviceSynchronize();
     cudaFreeHost(plan->meta_host);
@@ -1015,147 +1282,86 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   std::lock_guard<std::mutex> lk(plan->mu);
   std::vector<Shape> shp;
-  ifnso_status st = read_batch(plan, batch, shp);
-  if (st != IFNSO_OK) return st;
-  if (!coeffs || coeffs->K != plan->L + 1 ||
-      (coeffs->host ? 1 : 0) + (coeffs->device ? 1 : 0) + (coeffs->mlp ? 1 : 0) != 1)
-    return fail(IFNSO_ERR_INVALID_ARG, "coefficients: need K = %d and exactly one of host/device/mlp", plan->L + 1);
-  if (coeffs->mlp) {
-    if (coeffs->mlp->K != coeffs->K) return fail(IFNSO_ERR_INVALID_ARG, "coefficient network has K = %d", coeffs->mlp->K);
-    if (plan->L < 3) return fail(IFNSO_ERR_INVALID_ARG, "proposed coefficients need L >= 3");
-    if (plan->dtype != IFNSO_BF16) return fail(IFNSO_ERR_UNSUPPORTED, "proposed coefficients need a BF16 plan");
-  }
-  if (!out) return fail(IFNSO_ERR_INVALID_ARG, "out is NULL");
-  for (int i = 0; i < batch->count; ++i) {
-    if (!out[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is NULL", i);
-    if (out[i] == batch->in[i]) return fail(IFNSO_ERR_INVALID_ARG, "out[%d] aliases the input", i);
-    if (reinterpret_cast<uintptr_t>(out[i]) % 16 != 0)
-      return fail(IFNSO_ERR_INVALID_ARG, "out[%d] is not 16-byte aligned", i);
-  }
-  if (batch->count == 0) return IFNSO_OK;
+  ifnso_status st = check_call(plan, batch, coeffs, out, shp);
+  if (st != IFNSO_OK || batch->count == 0) return st;
   if ((st = init_plan_device(plan)) != IFNSO_OK) return st;
   Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
   if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
   uint8_t* ws = static_cast<uint8_t*>(workspace);
-  const uint64_t sig = batch_sig(plan, batch, out, workspace, coeffs, nullptr, 0, 0, 1);
-  if (!plan->sig_valid || plan->sig != sig) {
-    if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
-    uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
-    if ((st = build_ifnso_meta(ly, batch, out, ws, coeffs->host, coeffs->K, meta)) != IFNSO_OK) return st;
-    IFNSO_CUDA(cudaMemcpyAsync(ws, meta, ly.meta_bytes, cudaMemcpyHostToDevice, stream), "metadata upload");
-    plan->sig = sig;
-    plan->sig_valid = true;
-  }
-  const int n = ly.count;
-  const int L = ly.L;
-  const int frob = plan->scale == IFNSO_SCALE_FROB;
-  MatInfo* d_mats = reinterpret_cast<MatInfo*>(ws + ly.off_mats);
+  if ((st = upload_ifnso_meta(plan, ly, batch, out, ws, coeffs, {0, ly.count}, stream)) != IFNSO_OK) return st;
   int hpad_max = 0;
-  for (auto& s : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(s.hpad));
-  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
-  IFNSO_CUDA(mark(plan, stream, true), "timing event");
-  if (ly.f32) {
-    SgParams p = base_params<SgParams>(ws, ly, coeffs);
-    const SgProblem* probs = reinterpret_cast<const SgProblem*>(ws + ly.off_probs);
-    int max_h = 0, max_w = 0;
-    for (auto& s : shp) {
-      max_h = std::max<int>(max_h, static_cast<int>(s.h));
-      max_w = std::max<int>(max_w, static_cast<int>(s.w));
+  for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
+  const Run r{plan, &ly, ws, coeffs, hpad_max, stream, true};
+  if (ly.f32) return run_f32(r);
+  return run_tc(r, 0, ly.count, 0, ly.n_sym, 0, ly.n_app);
+}
+
+ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_in,
+                                      const ifnso_batch_desc* dev_batch, const ifnso_coeffs* coeffs,
+                                      void* const* dev_out, void* const* host_out, void* workspace,
+                                      size_t workspace_bytes, int32_t groups, ifnso_stream_t stream_) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  if (!host_in || !host_out) return fail(IFNSO_ERR_INVALID_ARG, "host_in / host_out is NULL");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(plan->mu);
+  std::vector<Shape> shp;
+  ifnso_status st = check_call(plan, dev_batch, coeffs, dev_out, shp);
+  if (st != IFNSO_OK) return st;
+  for (int i = 0; i < dev_batch->count; ++i)
+    if (!host_in[i] || !host_out[i]) return fail(IFNSO_ERR_INVALID_ARG, "host buffer %d is NULL", i);
+  if (dev_batch->count == 0) return IFNSO_OK;
+  if ((st = init_plan_device(plan)) != IFNSO_OK) return st;
+  Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
+  if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const int n = ly.count;
+  const int want = ly.f32 ? 1 : std::min(groups <= 0 ? 8 : groups, n);
+  const std::vector<int> gb = group_bounds(shp, want);
+  const int ng = static_cast<int>(gb.size()) - 1;
+  if ((st = upload_ifnso_meta(plan, ly, dev_batch, dev_out, ws, coeffs, gb, stream)) != IFNSO_OK) return st;
+  if ((st = ensure_copy_streams(plan, ng)) != IFNSO_OK) return st;
+  const size_t esz = plan->dtype == IFNSO_BF16 ? 2 : 4;
+  // the copies come after everything already queued on `stream`
+  IFNSO_CUDA(cudaEventRecord(plan->ev_start, stream), "cudaEventRecord");
+  IFNSO_CUDA(cudaStreamWaitEvent(plan->s_in, plan->ev_start, 0), "cudaStreamWaitEvent");
+  IFNSO_CUDA(cudaStreamWaitEvent(plan->s_out, plan->ev_start, 0), "cudaStreamWaitEvent");
+  for (int g = 0; g < ng; ++g) {
+    for (int i = gb[g]; i < gb[g + 1]; ++i) {
+      const Shape& s = shp[i];
+      void* dst = const_cast<void*>(dev_batch->in[i]);
+      if (s.ld == s.cols)
+        IFNSO_CUDA(cudaMemcpyAsync(dst, host_in[i], s.rows * s.cols * esz, cudaMemcpyHostToDevice, plan->s_in),
+                   "input upload");
+      else
+        IFNSO_CUDA(cudaMemcpy2DAsync(dst, s.ld * esz, host_in[i], s.ld * esz, s.cols * esz, s.rows,
+                                     cudaMemcpyHostToDevice, plan->s_in),
+                   "input upload");
     }
-    // the Gram is computed over the whole padded h_pad x h_pad block (zeros beyond h)
-    p.probs = probs + ly.pi_gram;
-    IFNSO_CUDA(sg_launch(EPI_GRAM, p, n, hpad_max, hpad_max, stream), "FP32 Gram");
-    IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
-    IFNSO_CUDA(mark(plan, stream, false), "timing event");
-    if (plan->stop_after == 0) return IFNSO_OK;
-    IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, 0, 1, stream), "prep");
-    IFNSO_CUDA(mark(plan, stream, false), "timing event");
-    if (plan->stop_after == 1) return IFNSO_OK;
-    for (int j = 1; j <= L - 1; ++j) {
-      const int par = (j - 1) % 2;
-      p.probs = probs + ly.pi_sqr + par * n;
-      p.coef_l = j + 1;
-      p.final_pass = (j == L - 1);
-      IFNSO_CUDA(sg_launch(EPI_SQR, p, n, hpad_max, hpad_max, stream), "FP32 squaring");
-      IFNSO_CUDA(mark(plan, stream, false), "timing event");
-      if (plan->stop_after == 1 + j) return IFNSO_OK;
-    }
-    p.probs = probs + ly.pi_apply;
-    p.coef_l = 0;
-    p.final_pass = 0;
-    IFNSO_CUDA(sg_launch(EPI_APPLY, p, n, max_h, max_w, stream), "FP32 apply");
-    IFNSO_CUDA(mark(plan, stream, false), "timing event");
-    return IFNSO_OK;
+    IFNSO_CUDA(cudaEventRecord(plan->ev_in[g], plan->s_in), "cudaEventRecord");
   }
-  TcParams p = base_params<TcParams>(ws, ly, coeffs);
-  const TcProblem* probs = reinterpret_cast<const TcProblem*>(ws + ly.off_probs);
-  const WorkItem* sym = reinterpret_cast<const WorkItem*>(ws + ly.off_items_sym);
-  const WorkItem* app = reinterpret_cast<const WorkItem*>(ws + ly.off_items_app);
-  const Prec& pc = ly.prec;
-  p.p_split = pc.p_split;
-  p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
-  p.cta_group = plan->cta_group;
-  p.probs = probs + ly.pi_gram;
-  p.items = sym;
-  p.n_items = static_cast<int32_t>(ly.n_sym);
-  p.inject = plan->inject_stall;
-  IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "Gram pass");
-  p.inject = 0;
-  const ifnso_mlp* net = coeffs->mlp;
-  if (net) {
-    // until the network has spoken, the scalars see the fixed coefficients
-    CoefTable fixed{nullptr, net->wslots, coeffs->K, 0};
-    IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, fixed, L, frob, 0, stream), "scalars");
-  } else {
-    IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
-  }
-  IFNSO_CUDA(mark(plan, stream, false), "timing event");
-  if (plan->stop_after == 0) return IFNSO_OK;
-  // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo)
-  const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
-  IFNSO_CUDA(launch_prep(d_mats, n, hpad_max, p.scal, p.coef, L, prep_lo, 0, stream), "prep");
-  IFNSO_CUDA(mark(plan, stream, false), "timing event");
-  if (plan->stop_after == 1) return IFNSO_OK;
-  for (int j = 1; j <= L - 1; ++j) {
-    const int par = (j - 1) % 2;
-    const int split = j <= pc.k_split ? 1 : 0;
-    p.probs = probs + ly.pi_sqr + par * n;
-    p.items = sym;
-    p.n_items = static_cast<int32_t>(ly.n_sym);
-    p.coef_l = j + 1;
-    p.final_pass = (j == L - 1);
-    p.read_lo = split;
-    p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
-    if (!net) {
-      // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
-      // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
-      p.p_mode = j == 1 ? 1 : ((j & 1) ? 2 : (j == L - 1 ? 3 : 0));
-      p.feat = 0;
-    } else {
-      // proposed coefficients: squaring 1 only measures tr(D_1^4); squaring 2
-      // writes P from T_0, D_2 and D_3; even squarings add D_j and D_{j+1};
-      // an odd last squaring adds D_L
-      p.p_mode = j == 1 ? 0 : (j == 2 ? 4 : ((j & 1) == 0 ? 2 : (j == L - 1 ? 3 : 0)));
-      p.feat = j == 1 ? 1 : 0;
+  int hpad_max = 0;
+  for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
+  const Run r{plan, &ly, ws, coeffs, hpad_max, stream, ly.f32 != 0};
+  for (int g = 0; g < ng; ++g) {
+    IFNSO_CUDA(cudaStreamWaitEvent(stream, plan->ev_in[g], 0), "cudaStreamWaitEvent");
+    if (ly.f32)
+      st = run_f32(r);
+    else
+      st = run_tc(r, gb[g], gb[g + 1] - gb[g], plan->sym_off[g], plan->sym_off[g + 1], plan->app_off[g],
+                  plan->app_off[g + 1]);
+    if (st != IFNSO_OK) return st;
+    IFNSO_CUDA(cudaEventRecord(plan->ev_done[g], stream), "cudaEventRecord");
+    IFNSO_CUDA(cudaStreamWaitEvent(plan->s_out, plan->ev_done[g], 0), "cudaStreamWaitEvent");
+    for (int i = gb[g]; i < gb[g + 1]; ++i) {
+      const Shape& s = shp[i];
+      IFNSO_CUDA(cudaMemcpyAsync(host_out[i], dev_out[i], s.rows * s.cols * esz, cudaMemcpyDeviceToHost,
+                                 plan->s_out),
+                 "output download");
     }
-    IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, ly.n_sym), stream),
-               "squaring pass");
-    if (net && j == 1) {
-      IFNSO_CUDA(mlp_infer(net->prm, net->K, net->wfix, net->scale, net->stats, d_mats, p.scal, n,
-                           reinterpret_cast<float*>(ws + ly.off_rows), kRowSlots, stream),
-                 "coefficient proposal");
-    }
-    IFNSO_CUDA(mark(plan, stream, false), "timing event");
-    if (plan->stop_after == 1 + j) return IFNSO_OK;
   }
-  p.probs = probs + ly.pi_apply;
-  p.items = app;
-  p.n_items = static_cast<int32_t>(ly.n_app);
-  p.coef_l = 0;
-  p.final_pass = 0;
-  p.read_lo = p.write_lo = 0;
-  IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, ly.n_app), stream), "apply pass");
-  IFNSO_CUDA(mark(plan, stream, false), "timing event");
+  // later work on `stream` comes after the last download
+  IFNSO_CUDA(cudaEventRecord(plan->ev_last, plan->s_out), "cudaEventRecord");
+  IFNSO_CUDA(cudaStreamWaitEvent(stream, plan->ev_last, 0), "cudaStreamWaitEvent");
   return IFNSO_OK;
 }
 

@@ -45,7 +45,7 @@ IFNSO_STATIC_NORM_MAX_MATRICES = 1024
 
 EXPORTED = [
     "ifnso_plan_create", "ifnso_plan_set", "ifnso_plan_get", "ifnso_plan_destroy",
-    "ifnso_workspace_bytes", "ifnso_orthogonalize", "ns_iterate", "ns_workspace_bytes",
+    "ifnso_workspace_bytes", "ifnso_orthogonalize", "ifnso_orthogonalize_host", "ns_iterate", "ns_workspace_bytes",
     "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
     "ifnso_frobenius_norm2_static", "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
     "ifnso_launch_count", "ifnso_mlp_param_count", "ifnso_mlp_create", "ifnso_mlp_destroy",
@@ -73,6 +73,8 @@ _sig = {
     "ns_workspace_bytes": (C.c_size_t, [_P, C.POINTER(ifnso_batch_desc)]),
     "ifnso_orthogonalize": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(ifnso_coeffs),
                                       C.POINTER(_P), _P, C.c_size_t, _P]),
+    "ifnso_orthogonalize_host": (C.c_int, [_P, C.POINTER(_P), C.POINTER(ifnso_batch_desc), C.POINTER(ifnso_coeffs),
+                                           C.POINTER(_P), C.POINTER(_P), _P, C.c_size_t, C.c_int32, _P]),
     "ns_iterate": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(C.c_double), C.c_int32, C.c_int32,
                              C.POINTER(_P), _P, C.c_size_t, _P]),
     "ifnso_device_status": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
@@ -233,10 +235,7 @@ class Plan:
         return self._ws
 
     # -------------------------------------------------------------- calls
-    def orthogonalize(self, batch, coeffs, outs, ws=None, stream=None):
-        """Run Algorithm 1 on every matrix of `batch` (Batch) into `outs` (tensors).
-        coeffs: host sequence of K = L + 1 FP64 values (slot 0 ignored) or a
-        CUDA float32 tensor of shape (count, K)."""
+    def _coeffs(self, batch, coeffs):
         torch = _torch()
         K = self.L + 1
         if isinstance(coeffs, torch.Tensor) and coeffs.is_cuda:
@@ -253,6 +252,13 @@ class Plan:
                 raise ValueError(f"host coefficients must have K = {K} values")
             self._cf_keep = arr
             cf = ifnso_coeffs(K, arr.ctypes.data_as(C.POINTER(C.c_double)), None, None)
+        return cf
+
+    def orthogonalize(self, batch, coeffs, outs, ws=None, stream=None):
+        """Run Algorithm 1 on every matrix of `batch` (Batch) into `outs` (tensors).
+        coeffs: host sequence of K = L + 1 FP64 values (slot 0 ignored) or a
+        CUDA float32 tensor of shape (count, K)."""
+        cf = self._coeffs(batch, coeffs)
         need = self.workspace_bytes(batch)
         if ws is None:
             ws = self.workspace(need)
@@ -261,6 +267,25 @@ class Plan:
                                   ws.nbytes, _stream(stream)), "ifnso_orthogonalize")
         self._last_ws = ws
         return outs
+
+    def orthogonalize_host(self, host_in, batch, coeffs, outs, host_out, groups=0, ws=None, stream=None):
+        """Algorithm 1 on matrices in host memory: host_in[i] (page-locked CPU
+        tensors laid out like batch's device tensors) are uploaded into the
+        tensors of `batch`, the results come back from `outs` (device) into
+        host_out (CPU tensors); uploads, passes and downloads of `groups`
+        groups overlap.  Asynchronous on `stream`."""
+        cf = self._coeffs(batch, coeffs)
+        need = self.workspace_bytes(batch)
+        if ws is None:
+            ws = self.workspace(need)
+        n = max(len(outs), 1)
+        hin = (C.c_void_p * n)(*[t.data_ptr() for t in host_in])
+        hout = (C.c_void_p * n)(*[t.data_ptr() for t in host_out])
+        optr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        check(ifnso_orthogonalize_host(self.handle, hin, batch.ref(), C.byref(cf), optr, hout, C.c_void_p(ws.ptr),
+                                       ws.nbytes, int(groups), _stream(stream)), "ifnso_orthogonalize_host")
+        self._last_ws = ws
+        return host_out
 
     def ns_iterate(self, batch, poly, steps, outs, ws=None, stream=None):
         poly = np.ascontiguousarray(np.asarray(poly, dtype=np.float64))

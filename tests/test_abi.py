@@ -120,3 +120,23 @@ def test_cta_group_option(F):
     assert F.ifnso_plan_set(p, F.IFNSO_OPT_CTA_GROUP, 2) == 0
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_CTA_GROUP, C.byref(v)) == 0 and v.value == 2
     F.ifnso_plan_destroy(p)
+
+
+def test_host_entry_argument_checks(F):
+    # NULL host buffers are rejected before any device work
+    st, p = _plan(F, 256, 512, 4)
+    w = (C.c_double * 5)(1.0, 0.1, 0.2, 0.3, 0.4)
+    cf = F.ifnso_coeffs(5, w, None, None)
+    ptrs = (C.c_void_p * 1)(16 * 1024)
+    rows = (C.c_int64 * 1)(256)
+    cols = (C.c_int64 * 1)(512)
+    desc = F.ifnso_batch_desc(1, ptrs, rows, cols, None)
+    outs = (C.c_void_p * 1)(32 * 1024)
+    nulls = (C.c_void_p * 1)(None)
+    assert F.ifnso_orthogonalize_host(p, None, C.byref(desc), C.byref(cf), outs, outs, None, 0, 0,
+                                      None) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_orthogonalize_host(p, nulls, C.byref(desc), C.byref(cf), outs, outs, None, 0, 0,
+                                      None) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_orthogonalize_host(None, nulls, C.byref(desc), C.byref(cf), outs, outs, None, 0, 0,
+                                      None) == F.IFNSO_ERR_INVALID_ARG
+    F.ifnso_plan_destroy(p)
