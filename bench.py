@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
     ap.add_argument("--cta-group", type=int, default=1, choices=[1, 2],
                     help="tensor-core passes: MMAs of the CTA pair (2) or per-CTA MMAs with B multicast (1)")
+    ap.add_argument("--coeffs", default="fixed", choices=["fixed", "mlp"],
+                    help="fixed: the learner's w_1..w_L for every matrix; mlp: per-matrix coefficients "
+                         "proposed inside the call by the coefficient network (trained here first)")
+    ap.add_argument("--mlp-steps", type=int, default=2000)
     ap.add_argument("--groups", type=int, default=0,
                     help="end-to-end run: groups whose copies overlap the passes (0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -323,6 +327,30 @@ def main():
     # fixed coefficients from the library's own GPU learner (Sec. 2.3 / 3.1.1)
     w_full = F.learn_coefficients(L)
     coef = np.r_[1.0, w_full]
+    mlp_info = None
+    if args.coeffs == "mlp":
+        # per-matrix proposals (config 4 network, K = L + 1 outputs), trained on
+        # synthetic spectra; the timed step includes the features, the network
+        # and the coefficient rows inside ifnso_orthogonalize
+        import synth
+
+        n_train = 20000
+        hs_, ws_, sig_, offs_ = [], [], [], [0]
+        for sd in range(n_train):
+            h_, w_, sg_, _ = synth.mlp_spectrum(sd)
+            hs_.append(h_)
+            ws_.append(w_)
+            sig_.append(sg_.astype(np.float32))
+            offs_.append(offs_[-1] + h_)
+        net = F.Mlp(L + 1, w_full, seed=0)
+        net.set_data(torch.tensor(np.concatenate(sig_), device=device),
+                     torch.tensor(offs_, dtype=torch.int64, device=device),
+                     torch.tensor(hs_, dtype=torch.int32, device=device),
+                     torch.tensor(ws_, dtype=torch.int32, device=device), fit=True)
+        curve = net.train(args.mlp_steps, batch=512, lr=1e-3, seed=1).cpu().numpy()
+        coef = net
+        mlp_info = {"train_spectra": n_train, "steps": args.mlp_steps, "batch": 512,
+                    "loss_first_50": float(np.mean(curve[:50])), "loss_last_50": float(np.mean(curve[-50:]))}
 
     plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision)
     plan.set(F.IFNSO_OPT_TIMING, 1)
@@ -483,7 +511,11 @@ def main():
                        "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
                        "mma": ("tcgen05 MMAs of the CTA pair (M = 256)" if args.cta_group == 2
                                else "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters"),
-                       "coefficients": "learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 schedule)"},
+                       "coefficients": ("per-matrix proposals of the coefficient network, computed inside each "
+                                        "call after the first squaring" if args.coeffs == "mlp" else
+                                        "fixed, learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 "
+                                        "schedule)"),
+                       "coefficient_network": mlp_info},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
                     "ifnso_over_ns5": value / ns_value},
