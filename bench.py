@@ -58,8 +58,9 @@ def parse():
     ap.add_argument("--workload", default="muon_1b", choices=sorted(WORKLOADS))
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
-    ap.add_argument("--cta-group", type=int, default=1, choices=[1, 2],
-                    help="tensor-core passes: MMAs of the CTA pair (2) or per-CTA MMAs with B multicast (1)")
+    ap.add_argument("--cta-group", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core passes: MMAs of the CTA pair (2), per-CTA MMAs with B multicast (1), "
+                         "or the library's choice per pass (0)")
     ap.add_argument("--coeffs", default="fixed", choices=["fixed", "mlp"],
                     help="fixed: the learner's w_1..w_L for every matrix; mlp: per-matrix coefficients "
                          "proposed inside the call by the coefficient network (trained here first)")
@@ -509,8 +510,10 @@ def main():
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
                        "l2": "inputs larger than L2 (no flush)",
                        "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
-                       "mma": ("tcgen05 MMAs of the CTA pair (M = 256)" if args.cta_group == 2
-                               else "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters"),
+                       "mma": {0: "tcgen05 MMAs of the CTA pair (M = 256) for the split squarings, per-CTA "
+                                  "MMAs with the B tile multicast in 2-CTA clusters for the other passes",
+                               1: "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters",
+                               2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group],
                        "coefficients": ("per-matrix proposals of the coefficient network, computed inside each "
                                         "call after the first squaring" if args.coeffs == "mlp" else
                                         "fixed, learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 "

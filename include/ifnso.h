@@ -82,13 +82,14 @@ typedef enum {
   /* How the two CTAs of a cluster share the B operand of a pair of output
    * tiles in the tensor-core passes (the results agree bit for bit on every
    * case tested):
-   * 1 (default): each CTA issues its own M = 128 MMAs and multicasts its half
-   *    of B to both CTAs.
+   * 1: each CTA issues its own M = 128 MMAs and multicasts its half of B to
+   *    both CTAs.
    * 2: MMAs of the CTA pair, M = 256 (tcgen05 cta_group::2); each CTA keeps
-   *    its own half of B, so an SM takes in a third fewer operand bytes per
-   *    product, but the odd CTA's stage completions reach the issuing CTA
-   *    through a release-ordered remote arrive per stage, which limits the
-   *    rate of stages. */
+   *    its own half of B (a third fewer operand bytes per SM and product)
+   *    and the odd CTA's copies complete on the even CTA's stage barrier.
+   * 0 (default): 2 for the squarings with split operands, whose three
+   *    products per stage hide the pair's handshakes, 1 for every other
+   *    pass (measured fastest on the 1B list). */
   IFNSO_OPT_CTA_GROUP = 8
 } ifnso_option;
 

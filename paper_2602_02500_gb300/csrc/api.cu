@@ -30,7 +30,7 @@ struct ifnso_plan {
   int stop_after = -1;
   int wait_ms = 0;       // limit of the kernels' pipeline waits (0: 4 s)
   int inject_stall = 0;  // testing aid: the Gram pass's first CTA loads nothing
-  int cta_group = 1;     // tensor-core passes: per-CTA MMAs (1) or MMAs of the CTA pair (2)
+  int cta_group = 0;     // tensor-core passes: 0 auto, 1 per-CTA MMAs, 2 MMAs of the CTA pair
   int num_sms = 0;
   // metadata of the last batch (pinned host copy, uploaded into the workspace)
   uint64_t sig = 0;
@@ -1071,7 +1071,10 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   const Prec& pc = ly.prec;
   p.p_split = pc.p_split;
   p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
-  p.cta_group = plan->cta_group;
+  // auto: MMAs of the CTA pair for the split squarings (three products per
+  // stage hide the pair's handshakes), per-CTA MMAs for every other pass
+  auto cta_group = [&](bool split) { return plan->cta_group ? plan->cta_group : (split ? 2 : 1); };
+  p.cta_group = cta_group(false);
   p.probs = probs + ly.pi_gram;
   p.items = sym;
   p.n_items = static_cast<int32_t>(n_sym);
@@ -1103,6 +1106,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     p.final_pass = (j == L - 1);
     p.read_lo = split;
     p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
+    p.cta_group = cta_group(split != 0);
     if (!net) {
       // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
       // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
@@ -1131,6 +1135,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.coef_l = 0;
   p.final_pass = 0;
   p.read_lo = p.write_lo = 0;
+  p.cta_group = cta_group(false);
   IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream), "apply pass");
   IFNSO_CUDA(mark_pass(false), "timing event");
   return IFNSO_OK;
@@ -1203,7 +1208,7 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       plan->inject_stall = value != 0;
       break;
     case IFNSO_OPT_CTA_GROUP:
-      if (value != 1 && value != 2) return fail(IFNSO_ERR_INVALID_ARG, "cta group %lld", (long long)value);
+      if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "cta group %lld", (long long)value);
       plan->cta_group = static_cast<int>(value);
       break;
     default:
@@ -1451,7 +1456,7 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
   }
   TcParams p{};
   p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
-  p.cta_group = plan->cta_group;
+  p.cta_group = plan->cta_group ? plan->cta_group : 1;
   p.scal = scal;
   p.ns_a = a;
   p.ns_b = b;

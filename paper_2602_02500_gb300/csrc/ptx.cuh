@@ -47,19 +47,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Acquire at cluster scope: for barriers that threads of the peer CTA arrive on.
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
 // Address of the same shared-memory offset in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
   uint32_t r;
@@ -67,22 +54,26 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
   return r;
 }
 
-// Arrive on an mbarrier of another CTA of the cluster (address from mapa_shared).
+// Arrive on an mbarrier of another CTA of the cluster (address from
+// mapa_shared), with the default release at CTA scope: it does not wait for
+// this thread's global stores to be performed cluster-wide.  Used where the
+// arrive only hands back a resource whose accesses are ordered by tcgen05
+// fences (an accumulator drained with tcgen05.ld, then
+// tcgen05.fence::before_thread_sync).
 __device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
-// Wait for the phase with the given parity.  Returns false (and raises the
-// CTA-wide abort flag) if it did not complete within kWaitTimeoutNs, or if
-// another role of the CTA has already aborted.  CLUSTER: acquire at cluster
-// scope (the barrier receives arrivals from the peer CTA).
-template <bool CLUSTER = false>
+// Wait for the phase with the given parity (acquire at CTA scope: every
+// barrier of the pipelines is completed by TMA transactions, tcgen05 commits,
+// or arrivals whose data is ordered by tcgen05 fences).  Returns false (and
+// raises the CTA-wide abort flag) if it did not complete within
+// kWaitTimeoutNs, or if another role of the CTA has already aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           unsigned long long timeout_ns = kWaitTimeoutNs) {
   unsigned long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
-    if (CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u) {
       if (*abort_flag) return false;
       unsigned long long now = globaltimer_ns();
@@ -115,6 +106,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint
       "l"(tmap), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
+// A load into this CTA's shared memory whose completion is counted on an
+// mbarrier of the CTA pair (tcgen05 cta_group::2 kernels): `bar` may be the
+// peer CTA's barrier (a shared::cluster address from mapa_shared).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap, uint32_t bar, int32_t x,
+                                                 int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(tmap), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
 // The same box delivered to the same shared-memory offset of every CTA in
 // `mask` (this GPU's own memory only), completing bytes on each destination
 // CTA's mbarrier at `bar`'s offset.

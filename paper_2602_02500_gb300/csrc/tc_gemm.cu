@@ -14,15 +14,15 @@
 //           (tcgen05 cta_group::2) that read A and B from both shared
 //           memories: each CTA stores only its own half of B, so an SM takes
 //           in 32 KB (not 48 KB) per 64-wide K block of a plain product.  The
-//           odd CTA's TMA completions reach the issuer through a relay
-//           thread that arrives on the even CTA's stage barrier.
+//           odd CTA's TMA loads complete on the even CTA's stage barrier,
+//           which the even CTA arms with the bytes of both.
 //
 // Warp roles (320 threads):
 //   warp 0      TMA producer: K blocks of 64 of every operand source into a
 //               ring of shared-memory stages (128-byte swizzle).
 //   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
 //               and MMA issuer: tcgen05.mma M=128 (CG 1) or 256 (CG 2, even
-//               CTA; the odd CTA's warp 1 is the relay), N=256, K=16.
+//               CTA only), N=256, K=16.
 //   warps 2..9  epilogue (two warps per TMEM lane quadrant, 128 columns each):
 //               tcgen05.ld of the accumulator, fused elementwise math of the
 //               pass, stores to global memory.
@@ -478,7 +478,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   constexpr int S = C::stages;
   constexpr uint32_t kIsBf16 = (EPI == EPI_SQR) ? 0u : 1u;  // D_l are FP16, all else BF16
   constexpr uint16_t kPair = 0x3;                           // both CTAs of the cluster
-  constexpr bool kCl = (CG == 2);                           // barriers see arrivals of the peer CTA
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -506,8 +505,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       if constexpr (CG == 2) {
-        // even CTA: its own copies (expect_tx) + the relay of the odd CTA's copies
-        mbar_init(full_bar(s), crank == 0 ? 2 : 1);
+        // even CTA: armed with the bytes of both CTAs' copies (the odd CTA's
+        // stage barriers are not used)
+        mbar_init(full_bar(s), 1);
         mbar_init(empty_bar(s), 1);  // freed by the pair's MMAs (one commit, multicast)
       } else {
         mbar_init(full_bar(s), 1);
@@ -563,13 +563,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const int n_kb = pr.n_kb;
         const int tm = wi.tm + crank;
         for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait<kCl>(empty_bar(stage), phase ^ 1u, abort_flag, tmo)) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, tmo)) {
             ok = false;
             break;
           }
           const uint32_t fb = full_bar(stage);
-          // CG 1: own A + both halves of B; CG 2: own A + own half of B
-          mbar_arrive_expect_tx(fb, C::stage_bytes);
+          if constexpr (CG == 1)
+            mbar_arrive_expect_tx(fb, C::stage_bytes);  // own A + both halves of B
+          else if (crank == 0)
+            mbar_arrive_expect_tx(fb, 2 * C::stage_bytes);  // A and the B half of both CTAs
+          // CG 2, odd CTA: the copies complete on the even CTA's barrier
+          const uint32_t pb = (CG == 2 && crank == 1) ? mapa_shared(fb, 0) : fb;
+          auto load = [&](uint32_t dst, const void* m, int32_t x, int32_t y) {
+            if (CG == 2 && crank == 1)
+              tma_load_2d_pair(dst, m, pb, x, y);
+            else
+              tma_load_2d(dst, m, fb, x, y);
+          };
           const uint32_t st = base + stage * C::stage_bytes;
           const int k0 = kb * BK;
           // K blocks left of the diagonal block of a symmetric operand come
@@ -582,10 +592,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             const uint32_t dst = st + a * kTileA;
             const void* m = at ? &pr.mapT[a] : &pr.mapA[a];
             if (!a_mn) {
-              tma_load_2d(dst, m, fb, k0, tm * BM);
+              load(dst, m, k0, tm * BM);
             } else {
-              tma_load_2d(dst, m, fb, tm * BM, k0);
-              tma_load_2d(dst + 8192, m, fb, tm * BM + 64, k0);
+              load(dst, m, tm * BM, k0);
+              load(dst + 8192, m, tm * BM + 64, k0);
             }
           }
 #pragma unroll
@@ -595,10 +605,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             if constexpr (CG == 2) {
               // this CTA's half only, at the start of its B tile
               if (!b_mn) {
-                tma_load_2d(dst, m, fb, k0, wi.tn * BN + 128 * crank);
+                load(dst, m, k0, wi.tn * BN + 128 * crank);
               } else {
-                tma_load_2d(dst, m, fb, wi.tn * BN + 128 * crank, k0);
-                tma_load_2d(dst + 8192, m, fb, wi.tn * BN + 128 * crank + 64, k0);
+                load(dst, m, wi.tn * BN + 128 * crank, k0);
+                load(dst + 8192, m, wi.tn * BN + 128 * crank + 64, k0);
               }
             } else if (!b_mn) {
               // this CTA's half: rows [128 crank, 128 crank + 128) of the B tile
@@ -619,9 +629,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       }
       if (!ok) {
         set_timeout(p.scal, cur_mat);
-        // let the copies already issued land before the CTA exits
-        for (int s = 0; s < S; ++s)
-          if (filled[s]) mbar_wait_bounded(full_bar(s), (filled[s] - 1u) & 1u, tmo);
+        // let the copies already issued land before the CTA exits (CG 2: the
+        // even CTA's barriers count both CTAs' copies; the odd CTA's last copy
+        // was issued a whole wait limit before it gave up)
+        if (CG == 1 || crank == 0)
+          for (int s = 0; s < S; ++s)
+            if (filled[s]) mbar_wait_bounded(full_bar(s), (filled[s] - 1u) & 1u, tmo);
       }
     }
   } else if (warp == 1) {
@@ -638,7 +651,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         cur_mat = pr.mat;
         const int acc = local & 1;
         const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
-        if (!mbar_wait<kCl>(tempty_bar(acc), acc_phase ^ 1u, abort_flag, tmo)) {
+        if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, tmo)) {
           ok = false;
           break;
         }
@@ -646,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
         const int n_kb = pr.n_kb;
         for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait<kCl>(full_bar(stage), phase, abort_flag, tmo)) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag, tmo)) {
             ok = false;
             break;
           }
@@ -687,32 +700,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       // make sure no MMA is still writing TMEM or reading shared memory
       umma_commit<CG>(drain_bar);
       mbar_wait_bounded(drain_bar, 0, tmo);
-    } else if (CG == 2 && lane == 0) {
-      // ------------------------------------------------ relay (odd CTA of a pair)
-      // Passes the completion of this CTA's copies of each stage on to the even
-      // CTA's stage barrier, where the issuer of the pair's MMAs waits.
-      int stage = 0;
-      uint32_t phase = 0;
-      int cur_mat = 0;
-      bool ok = true;
-      for (int it = cid; it < p.n_items && ok; it += ncl) {
-        const WorkItem wi = p.items[it];
-        const TcProblem& pr = p.probs[wi.prob];
-        cur_mat = pr.mat;
-        const int n_kb = pr.n_kb;
-        for (int kb = 0; kb < n_kb; ++kb) {
-          if (!mbar_wait(full_bar(stage), phase, abort_flag, tmo)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_remote(mapa_shared(full_bar(stage), 0));
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
-          }
-        }
-      }
-      if (!ok) set_timeout(p.scal, cur_mat);
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
@@ -727,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       const uint32_t acc_phase = (static_cast<uint32_t>(local) >> 1) & 1u;
       // one lane waits, the warp follows its verdict (tcgen05.ld needs a converged warp)
       int ready = 0;
-      if (lane == 0) ready = mbar_wait<kCl>(tfull_bar(acc), acc_phase, abort_flag, tmo) ? 1 : 0;
+      if (lane == 0) ready = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, tmo) ? 1 : 0;
       ready = __shfl_sync(0xffffffffu, ready, 0);
       if (!ready) {
         if (lane == 0) set_timeout(p.scal, pr.mat);

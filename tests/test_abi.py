@@ -111,11 +111,11 @@ def test_precision_resolution(F):
 
 
 def test_cta_group_option(F):
-    # default: per-CTA MMAs; 1 and 2 are the only accepted values
+    # default: automatic choice per pass; 0, 1 and 2 are the only accepted values
     st, p = _plan(F, 256, 512, 4)
     v = C.c_int64()
-    assert F.ifnso_plan_get(p, F.IFNSO_OPT_CTA_GROUP, C.byref(v)) == 0 and v.value == 1
-    for bad in (0, 3, -1):
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_CTA_GROUP, C.byref(v)) == 0 and v.value == 0
+    for bad in (3, -1, 4):
         assert F.ifnso_plan_set(p, F.IFNSO_OPT_CTA_GROUP, bad) == F.IFNSO_ERR_INVALID_ARG
     assert F.ifnso_plan_set(p, F.IFNSO_OPT_CTA_GROUP, 2) == 0
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_CTA_GROUP, C.byref(v)) == 0 and v.value == 2
