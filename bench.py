@@ -65,6 +65,8 @@ def parse():
                     help="fixed: the learner's w_1..w_L for every matrix; mlp: per-matrix coefficients "
                          "proposed inside the call by the coefficient network (trained here first)")
     ap.add_argument("--mlp-steps", type=int, default=2000)
+    ap.add_argument("--gram-e4m3", action="store_true",
+                    help="experiment: the first product T_0 = A A^T from an E4M3 copy of A")
     ap.add_argument("--groups", type=int, default=0,
                     help="end-to-end run: groups whose copies overlap the passes (0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -356,6 +358,7 @@ def main():
     plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision)
     plan.set(F.IFNSO_OPT_TIMING, 1)
     plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
+    plan.set(F.IFNSO_OPT_GRAM_E4M3, 1 if args.gram_e4m3 else 0)
     ws = F.Workspace(plan.workspace_bytes(batch), device=device)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
@@ -518,7 +521,8 @@ def main():
                                         "call after the first squaring" if args.coeffs == "mlp" else
                                         "fixed, learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 "
                                         "schedule)"),
-                       "coefficient_network": mlp_info},
+                       "coefficient_network": mlp_info,
+                       "gram": "E4M3 copy of A s, FP32 accumulation (experiment)" if args.gram_e4m3 else "BF16"},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
                     "ifnso_over_ns5": value / ns_value},

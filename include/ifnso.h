@@ -90,7 +90,16 @@ typedef enum {
    * 0 (default): 2 for the squarings with split operands, whose three
    *    products per stage hide the pair's handshakes, 1 for every other
    *    pass (measured fastest on the 1B list). */
-  IFNSO_OPT_CTA_GROUP = 8
+  IFNSO_OPT_CTA_GROUP = 8,
+  /* Experiment on the first product (BF16 plans): when non-zero, T_0 = A A^T
+   * is computed from an E4M3 copy of A s, s the power of two that maps
+   * max |A_ij| into (224, 448] (rounded to nearest even, saturating), with
+   * FP32 accumulation and T_0 = (A s)(A s)^T / s^2; the squarings and the
+   * final product are unchanged.  E4M3 keeps 3 mantissa bits, so T_0 carries
+   * a relative rounding error of about 2^-5 per input element.  The
+   * workspace grows by h x round_up(w, 16) bytes per matrix.  0 (default):
+   * the BF16 Gram. */
+  IFNSO_OPT_GRAM_E4M3 = 9
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };

@@ -31,6 +31,7 @@ struct ifnso_plan {
   int wait_ms = 0;       // limit of the kernels' pipeline waits (0: 4 s)
   int inject_stall = 0;  // testing aid: the Gram pass's first CTA loads nothing
   int cta_group = 0;     // tensor-core passes: 0 auto, 1 per-CTA MMAs, 2 MMAs of the CTA pair
+  int gram_e4m3 = 0;     // Gram from a scaled E4M3 copy of A
   int num_sms = 0;
   // metadata of the last batch (pinned host copy, uploaded into the workspace)
   uint64_t sig = 0;
@@ -122,7 +123,7 @@ bool encode2d(CUtensorMap* map, CUtensorMapDataType dt, const void* ptr, uint64_
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {ld * 2};
+  cuuint64_t strides[1] = {ld * (dt == CU_TENSOR_MAP_DATA_TYPE_UINT8 ? 1u : 2u)};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(map, dt, 2, const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -161,6 +162,7 @@ struct Layout {
   int split = 0;     // the workspace keeps lo buffers (BF16 plans)
   Prec prec{};
   int f32 = 0;
+  int e4m3 = 0;      // per-matrix E4M3 copies of A for the Gram
   int ns = 0;        // Newton-Schulz layout
   int steps = 0;
   std::vector<Shape> shp;
@@ -310,6 +312,7 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   ly.prec = ns ? Prec{0, 0, 0, IFNSO_PREC_PLAIN} : resolve_prec(plan);
   ly.split = ly.prec.ws_lo;
   ly.f32 = plan->dtype == IFNSO_F32;
+  ly.e4m3 = (!ns && !ly.f32 && plan->gram_e4m3) ? 1 : 0;
   ly.ns = ns;
   ly.steps = steps;
   ly.shp = shp;
@@ -364,6 +367,7 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
       } else {
         for (int b = 0; b < 4; ++b)
           if (ly.split || (b & 1) == 0) off = a1k(off + hp2 * 2);
+        if (ly.e4m3) off = a1k(off + static_cast<size_t>(shp[i].h) * round_up(shp[i].w, 16));  // A s, E4M3
       }
     } else {
       const size_t xld = static_cast<size_t>(round_up(shp[i].cols, 8));
@@ -407,6 +411,10 @@ MatInfo mat_info(const Layout& ly, const ifnso_batch_desc* b, void* const* out, 
           mi.d[bb] = p;
           p += a1k(hp2 * 2);
         }
+      }
+      if (ly.e4m3) {
+        mi.a8 = p;
+        mi.a8ld = round_up(s.w, 16);
       }
     }
   } else {
@@ -577,12 +585,19 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     // MN-major when A = M^T (the tall input is read through its own layout).
     TcProblem& g = pr[ly.pi_gram + i];
     bool ok;
-    if (!s.trans) ok = map_k(&g.mapA[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
-    else ok = map_mn(&g.mapA[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+    if (ly.e4m3) {
+      // the E4M3 copy A s is K-major for either orientation; 128 one-byte values per K block
+      ok = encode2d(&g.mapA[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, mi.a8, s.w, s.h, mi.a8ld, 128, 128);
+      g.a_mn = g.b_mn = 0;
+      g.n_kb = static_cast<int32_t>((s.w + 2 * BK - 1) / (2 * BK));
+    } else {
+      if (!s.trans) ok = map_k(&g.mapA[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+      else ok = map_mn(&g.mapA[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+      g.a_mn = g.b_mn = s.trans;
+      g.n_kb = static_cast<int32_t>((s.w + BK - 1) / BK);
+    }
     if (!ok) return fail(IFNSO_ERR_CUDA, "cuTensorMapEncodeTiled failed (matrix %d, input)", i);
     g.mapB[0] = g.mapA[0];
-    g.a_mn = g.b_mn = s.trans;
-    g.n_kb = static_cast<int32_t>((s.w + BK - 1) / BK);
     g.mat = i;
     g.ld_aux = hp;
     g.pacc = mi.gp;
@@ -1079,7 +1094,16 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.items = sym;
   p.n_items = static_cast<int32_t>(n_sym);
   p.inject = plan->inject_stall;
-  IFNSO_CUDA(tc_launch(EPI_GRAM, 1, 1, p, grid_for(plan, n_sym), stream), "Gram pass");
+  if (ly.e4m3) {
+    int max_h = 0, max_w = 0;
+    for (int i = first; i < first + count; ++i) {
+      max_h = std::max<int>(max_h, static_cast<int>(ly.shp[i].h));
+      max_w = std::max<int>(max_w, static_cast<int>(ly.shp[i].w));
+    }
+    IFNSO_CUDA(launch_amax(d_mats, count, scal, std::max(1, 16 * plan->num_sms / count), stream), "max |A|");
+    IFNSO_CUDA(launch_cast_e4m3(d_mats, count, max_h, max_w, scal, stream), "E4M3 copy of A");
+  }
+  IFNSO_CUDA(tc_launch(ly.e4m3 ? EPI_GRAM_F8 : EPI_GRAM, 1, 1, p, grid_for(plan, n_sym), stream), "Gram pass");
   p.inject = 0;
   const ifnso_mlp* net = r.coeffs->mlp;
   if (net) {
@@ -1211,6 +1235,11 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "cta group %lld", (long long)value);
       plan->cta_group = static_cast<int>(value);
       break;
+    case IFNSO_OPT_GRAM_E4M3:
+      if (value != 0 && plan->dtype != IFNSO_BF16)
+        return fail(IFNSO_ERR_UNSUPPORTED, "the E4M3 Gram needs a BF16 plan");
+      plan->gram_e4m3 = value != 0;
+      break;
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -1231,6 +1260,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_WAIT_LIMIT_MS: *value = plan->wait_ms; return IFNSO_OK;
     case IFNSO_OPT_INJECT_STALL: *value = plan->inject_stall; return IFNSO_OK;
     case IFNSO_OPT_CTA_GROUP: *value = plan->cta_group; return IFNSO_OK;
+    case IFNSO_OPT_GRAM_E4M3: *value = plan->gram_e4m3; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }

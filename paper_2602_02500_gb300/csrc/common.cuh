@@ -23,6 +23,7 @@ enum EpiKind : int {
   EPI_NS_GRAM = 3,   // S = X X^T (BF16, direct + mirrored)
   EPI_NS_SQR = 4,    // B = b S + c S^2 (BF16, direct + mirrored)
   EPI_NS_APPLY = 5,  // X <- a X + (B X  or  b S X)
+  EPI_GRAM_F8 = 6,   // T_0 from E4M3 copies of A (kind::f8f6f4), rescaled; else as EPI_GRAM
 };
 
 // Per-matrix scalars kept in the workspace (64 bytes).
@@ -34,9 +35,23 @@ struct MatScalars {
   float inv_s2;    // 1 / s2, rounded once to FP32
   float inv_s;     // 1 / sqrt(s2), rounded once to FP32
   int32_t status;  // IFNSO_DEV_* bits
-  int32_t pad0;
+  uint32_t amax;   // bits of max |A_ij| as a float (E4M3 Gram: its scale); a max of
+                   // non-negative floats is a max of their bit patterns
   double spare[2];
 };
+
+// Power-of-two scale s with max |A_ij| s in (224, 448]: the E4M3 copy of A
+// holds A s (448 is the largest finite E4M3 value).  s is kept within
+// 2^-60..2^60 so that 1/s^2 stays a normal FP32 value; 1 for an all-zero A.
+__device__ __forceinline__ float e4m3_scale(uint32_t amax_bits) {
+  const float amax = __uint_as_float(amax_bits);
+  if (!(amax > 0.f) || !(amax < 3.0e38f)) return 1.f;
+  int e = static_cast<int>(floorf(log2f(448.f / amax)));
+  e = e < -60 ? -60 : (e > 60 ? 60 : e);
+  float s = ldexpf(1.f, e);
+  if (amax * s > 448.f) s *= 0.5f;  // log2f rounded up across a power of two
+  return s;
+}
 static_assert(sizeof(MatScalars) == 64, "MatScalars layout");
 
 // Coefficients w_1..w_L: either one FP64 vector shared by all matrices or an
@@ -132,6 +147,8 @@ struct MatInfo {
   void* s;                 // NS: S = X X^T
   void* b;                 // NS: B = b S + c S^2
   int64_t xld;
+  uint8_t* a8;             // E4M3 Gram: A s (h x w, K-major, leading dimension a8ld bytes)
+  int64_t a8ld;
 };
 
 // ------------------------------------------------------------ launchers
@@ -147,6 +164,11 @@ cudaError_t launch_scalars(const MatInfo* d_mats, int count, MatScalars* scal, C
                            int L, int scale_frob, int from_norm2, cudaStream_t s);
 cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
                         CoefTable coef, int L, int split, int f32, cudaStream_t s);
+// E4M3 Gram: max |A_ij| into MatScalars::amax, then the scaled E4M3 copy of
+// A (M or M^T, K-major) into MatInfo::a8.
+cudaError_t launch_amax(const MatInfo* d_mats, int count, MatScalars* scal, int grid_x, cudaStream_t s);
+cudaError_t launch_cast_e4m3(const MatInfo* d_mats, int count, int max_h, int max_w, MatScalars* scal,
+                             cudaStream_t s);
 
 struct SgProblem {
   const float* A;  // A operand element (i, k) at A[i * sa0 + k * sa1], zero for i >= a_rows

@@ -4,6 +4,7 @@
 // and the FP32 GEMM that carries every product of FP32 plans.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
@@ -78,6 +79,62 @@ __global__ void __launch_bounds__(256) k_norm2(const MatInfo* mats, int bf16, do
   }
   const float s = block_sum(acc, red);
   if (threadIdx.x == 0 && r0 < rows) atomicAdd(out + blockIdx.y * out_stride, static_cast<double>(s));
+}
+
+// ---------------------------------------------------------------- E4M3 Gram input
+// max |M_ij| of every matrix (block (x, m): rows [x chunk, (x + 1) chunk) of
+// matrix m; BF16), as the bit pattern of a non-negative float, into
+// MatScalars::amax of matrix m.
+__global__ void __launch_bounds__(256) k_amax(const MatInfo* mats, MatScalars* scal) {
+  __shared__ float red[32];
+  const MatInfo& mi = mats[blockIdx.y];
+  const int64_t rows = mi.rows, cols = mi.cols, ld = mi.ld;
+  const int64_t chunk = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * chunk;
+  const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
+  const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(mi.in);
+  float mx = 0.f;
+  const int64_t n = (r1 > r0 ? r1 - r0 : 0) * cols;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x)
+    mx = fmaxf(mx, fabsf(__bfloat162float(A[(r0 + e / cols) * ld + e % cols])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    atomicMax(&scal[blockIdx.y].amax, __float_as_uint(m));
+  }
+}
+
+// A s in E4M3 (round to nearest even, saturating at +-448), K-major: A = M for
+// a wide matrix, M^T for a tall one (transposed through a 32 x 33 tile).
+// Block (x, y, m) writes output rows [32 y, 32 y + 32), columns [32 x, 32 x + 32).
+__global__ void __launch_bounds__(256) k_cast_e4m3(const MatInfo* mats, const MatScalars* scal) {
+  __shared__ float tile[32][33];
+  const MatInfo& mi = mats[blockIdx.z];
+  const int h = mi.h, w = mi.w;
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  if (i0 >= h || k0 >= w) return;
+  const __nv_bfloat16* M = static_cast<const __nv_bfloat16*>(mi.in);
+  const float s = e4m3_scale(scal[blockIdx.z].amax);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // source block: rows i0.., columns k0.. of M (wide), or rows k0.., columns i0.. (tall)
+  const int64_t sr0 = mi.trans ? k0 : i0, sc0 = mi.trans ? i0 : k0;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t sr = sr0 + r, sc = sc0 + tx;
+    tile[r][tx] = (sr < mi.rows && sc < mi.cols) ? __bfloat162float(M[sr * mi.ld + sc]) : 0.f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int oi = i0 + r, ok = k0 + tx;
+    if (oi < h && ok < w) {
+      const float v = (mi.trans ? tile[tx][r] : tile[r][tx]) * s;
+      mi.a8[static_cast<int64_t>(oi) * mi.a8ld + ok] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- scalars
@@ -298,6 +355,21 @@ cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScala
   if (gx > 4096) gx = 4096;
   dim3 grid(gx, count);
   k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amax(const MatInfo* d_mats, int count, MatScalars* scal, int grid_x, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_amax<<<dim3(grid_x, count), 256, 0, s>>>(d_mats, scal);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_e4m3(const MatInfo* d_mats, int count, int max_h, int max_w, MatScalars* scal,
+                             cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_cast_e4m3<<<dim3((max_w + 31) / 32, (max_h + 31) / 32, count), 256, 0, s>>>(d_mats, scal);
   count_launch();
   return cudaGetLastError();
 }

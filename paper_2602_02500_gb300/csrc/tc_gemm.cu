@@ -358,7 +358,14 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     for (int j = 0; j < 32; ++j) v[j] = u2f(u[j]);
   };
   if constexpr (EPI != EPI_SQR) take();
-  if constexpr (EPI == EPI_GRAM) {
+  if constexpr (EPI == EPI_GRAM_F8) {
+    // the E4M3 products are of A s: T_0 = (A s)(A s)^T / s^2 (s a power of two)
+    const float sc = e4m3_scale(p.scal[pr.mat].amax);
+    const float inv = 1.f / (sc * sc);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] *= inv;
+  }
+  if constexpr (EPI == EPI_GRAM || EPI == EPI_GRAM_F8) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       ea.ss = fmaf(v[j], v[j], ea.ss);
@@ -476,7 +483,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   using C = Cfg<NA, NB, CG>;
   using PR = Products<NA, NB>;
   constexpr int S = C::stages;
-  constexpr uint32_t kIsBf16 = (EPI == EPI_SQR) ? 0u : 1u;  // D_l are FP16, all else BF16
+  // D_l are FP16, the E4M3 Gram's operands E4M3 (format code 0 of its kind), all else BF16
+  constexpr uint32_t kIsBf16 = (EPI == EPI_SQR || EPI == EPI_GRAM_F8) ? 0u : 1u;
+  constexpr bool kF8 = (EPI == EPI_GRAM_F8);
+  constexpr int kBKe = kF8 ? 2 * BK : BK;  // elements per 128-byte K block
   constexpr uint16_t kPair = 0x3;                           // both CTAs of the cluster
 
   extern __shared__ uint8_t smem_raw[];
@@ -581,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
               tma_load_2d(dst, m, fb, x, y);
           };
           const uint32_t st = base + stage * C::stage_bytes;
-          const int k0 = kb * BK;
+          const int k0 = kb * kBKe;
           // K blocks left of the diagonal block of a symmetric operand come
           // from the stored block across the diagonal, read MN-major
           const bool at = (pr.sym & kSymA) && (kb >> 2) < (wi.tm >> 1);
@@ -679,7 +689,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                                        : sdesc_sw128(sa + k * 32, 16, 1024);
               const uint64_t bd = b_mn ? sdesc_sw128(sb + k * 2048, 8192, 1024)
                                        : sdesc_sw128(sb + k * 32, 16, 1024);
-              umma_f16<CG>(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
+              if constexpr (kF8)
+                umma_e4m3<CG>(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
+              else
+                umma_f16<CG>(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
             }
           }
           // frees the stage in both CTAs once these MMAs have read it
@@ -746,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       } else {
         mbar_arrive(tempty_bar(acc));
       }
-      if constexpr (EPI == EPI_GRAM) {
+      if constexpr (EPI == EPI_GRAM || EPI == EPI_GRAM_F8) {
         float ss = ea.ss, tr = ea.tr;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -830,6 +843,8 @@ cudaError_t dispatch(int epi, int na, const TcParams& p, int max_clusters, cudaS
   switch (epi) {
     case EPI_GRAM:
       return launch_one<1, 1, EPI_GRAM, CG>(p, max_clusters, s);
+    case EPI_GRAM_F8:
+      return launch_one<1, 1, EPI_GRAM_F8, CG>(p, max_clusters, s);
     case EPI_SQR:
       if (na == 2) return launch_one<2, 2, EPI_SQR, CG>(p, max_clusters, s);
       return launch_one<1, 1, EPI_SQR, CG>(p, max_clusters, s);

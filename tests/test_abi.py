@@ -140,3 +140,15 @@ def test_host_entry_argument_checks(F):
     assert F.ifnso_orthogonalize_host(None, nulls, C.byref(desc), C.byref(cf), outs, outs, None, 0, 0,
                                       None) == F.IFNSO_ERR_INVALID_ARG
     F.ifnso_plan_destroy(p)
+
+
+def test_gram_e4m3_option(F):
+    st, p = _plan(F, 256, 512, 4)
+    v = C.c_int64()
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_GRAM_E4M3, C.byref(v)) == 0 and v.value == 0
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_GRAM_E4M3, 1) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_GRAM_E4M3, C.byref(v)) == 0 and v.value == 1
+    F.ifnso_plan_destroy(p)
+    st, p = _plan(F, 256, 512, 4, dtype=0)  # F32 plans have no E4M3 Gram
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_GRAM_E4M3, 1) == F.IFNSO_ERR_UNSUPPORTED
+    F.ifnso_plan_destroy(p)

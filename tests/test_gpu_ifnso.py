@@ -193,3 +193,68 @@ def test_bf16_ns(shape):
         ref = ONS.ns_generic(to_np(x), poly, steps)
         # BF16 storage of X, X X^T and B every step: 5e-2 relative
         assert rel(to_np(y), ref) < 5e-2
+
+
+# --------------------------------------------------------------- E4M3 Gram (experiment)
+def e4m3_round(x):
+    """Round to the nearest E4M3 value, ties to even, saturating at +-448
+    (E4M3: 3 mantissa bits, normals down to 2^-6, subnormal spacing 2^-9)."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -6)))
+    q = 2.0 ** (e - 3)
+    r = np.round(a / q) * q
+    return np.sign(x) * np.minimum(r, 448.0)
+
+
+def e4m3_scale(amax):
+    """The power of two s with amax * s in (224, 448]."""
+    s = 2.0 ** np.floor(np.log2(448.0 / amax))
+    return s / 2 if amax * s > 448.0 else s
+
+
+@pytest.mark.parametrize("shape", [(256, 512), (392, 136), (640, 1000), (1000, 640)])
+def test_bf16_gram_e4m3(shape):
+    """T_0 from the E4M3 copy of A s equals the FP64 Gram of the rounded copy / s^2."""
+    import torch
+
+    F = lib()
+    M = synth.gaussian(80, *shape)
+    x = to_dev(M, "bf16")
+    h, w = min(shape), max(shape)
+    plan = F.Plan(h, w, "bf16", L=4)
+    plan.set(F.IFNSO_OPT_GRAM_E4M3, 1)
+    plan.set(F.IFNSO_OPT_STOP_AFTER, 0)
+    b = F.Batch([x])
+    y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
+    plan.orthogonalize(b, np.r_[1.0, coeffs(4)], [y])
+    torch.cuda.synchronize()
+    ptr, ld = plan.workspace_view(b, 0, 0)
+    G = sym_upper(F.tensor_at(ptr, (ld, ld), torch.float32, plan._last_ws.buf).double().cpu().numpy())
+    A = O.orient(to_np(x))[0]
+    s = e4m3_scale(np.max(np.abs(A)))
+    Aq = e4m3_round(A * s)
+    ref = (Aq @ Aq.T) / (s * s)
+    assert rel(G[:h, :h], ref) < 1e-5
+    st, s2, tr = plan.device_status(1)
+    assert st[0] == 0 and abs(s2[0] - np.linalg.norm(ref)) / np.linalg.norm(ref) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(256, 512), (392, 136)])
+def test_bf16_ifnso_gram_e4m3_end_to_end(shape):
+    """The whole path with the E4M3 Gram, against Algorithm 1 on the BF16 input:
+    the error the 3-bit mantissa of the first product costs (reported)."""
+    M = synth.gaussian(81, *shape)
+    F = lib()
+    import torch
+
+    x = to_dev(M, "bf16")
+    y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
+    plan = F.Plan(min(shape), max(shape), "bf16", L=4)
+    plan.set(F.IFNSO_OPT_GRAM_E4M3, 1)
+    w = coeffs(4)
+    plan.orthogonalize(F.Batch([x]), np.r_[1.0, w], [y])
+    torch.cuda.synchronize()
+    err = rel(to_np(y), O.ifnso_alg1(to_np(x), w))
+    print(f"E4M3 Gram {shape}: relative error {err:.3e}")
+    assert err < 0.1
