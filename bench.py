@@ -65,6 +65,8 @@ def parse():
                     help="fixed: the learner's w_1..w_L for every matrix; mlp: per-matrix coefficients "
                          "proposed inside the call by the coefficient network (trained here first)")
     ap.add_argument("--mlp-steps", type=int, default=2000)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip ifnso_plan_autotune (MMA mode per pass kind) before timing")
     ap.add_argument("--gram-e4m3", action="store_true",
                     help="experiment: the first product T_0 = A A^T from an E4M3 copy of A")
     ap.add_argument("--groups", type=int, default=0,
@@ -361,6 +363,11 @@ def main():
     plan.set(F.IFNSO_OPT_GRAM_E4M3, 1 if args.gram_e4m3 else 0)
     ws = F.Workspace(plan.workspace_bytes(batch), device=device)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if args.autotune and args.cta_group == 0:
+        # untimed set-up: per-CTA vs CTA-pair MMAs per pass kind on this list
+        modes = plan.autotune(batch, coef, ys, reps=2, ws=ws)
+        tuned = dict(zip(["gram", "split_squaring", "plain_squaring", "product"], modes))
     for _ in range(max(args.warmup, 3)):
         plan.orthogonalize(batch, coef, ys, ws=ws)
     torch.cuda.synchronize()
@@ -513,10 +520,13 @@ def main():
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
                        "l2": "inputs larger than L2 (no flush)",
                        "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
-                       "mma": {0: "tcgen05 MMAs of the CTA pair (M = 256) for the split squarings, per-CTA "
-                                  "MMAs with the B tile multicast in 2-CTA clusters for the other passes",
-                               1: "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters",
-                               2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group],
+                       "mma": ({k: ("CTA pair (M = 256)" if v == 2 else "per CTA, B multicast")
+                                for k, v in tuned.items()} if tuned else
+                               {0: "tcgen05 MMAs of the CTA pair (M = 256) for the split squarings, per-CTA "
+                                   "MMAs with the B tile multicast in 2-CTA clusters for the other passes",
+                                1: "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters",
+                                2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group]),
+                       "autotuned": tuned is not None,
                        "coefficients": ("per-matrix proposals of the coefficient network, computed inside each "
                                         "call after the first squaring" if args.coeffs == "mlp" else
                                         "fixed, learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 "

@@ -87,8 +87,9 @@ typedef enum {
    * 2: MMAs of the CTA pair, M = 256 (tcgen05 cta_group::2); each CTA keeps
    *    its own half of B (a third fewer operand bytes per SM and product)
    *    and the odd CTA's copies complete on the even CTA's stage barrier.
-   * 0 (default): 2 for the squarings with split operands, whose three
-   *    products per stage hide the pair's handshakes, 1 for every other
+   * 0 (default): the modes ifnso_plan_autotune chose, per pass kind; before
+   *    any autotuning, 2 for the squarings with split operands, whose three
+   *    products per stage hide the pair's handshakes, and 1 for every other
    *    pass (measured fastest on the 1B list). */
   IFNSO_OPT_CTA_GROUP = 8,
   /* Experiment on the first product (BF16 plans): when non-zero, T_0 = A A^T
@@ -215,6 +216,23 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
  * apply.  Errors: IFNSO_ERR_INVALID_ARG for a NULL or misaligned pointer or
  * any argument ifnso_orthogonalize rejects; IFNSO_ERR_CUDA if a copy or a
  * launch fails (copies already queued then still run). */
+/* Autotuning of the tensor-core launches for one batch (no counterpart in
+ * the paper): runs ifnso_orthogonalize 1 + reps times with every pass forced
+ * to per-CTA MMAs, and 1 + reps times forced to MMAs of the CTA pair
+ * (IFNSO_OPT_CTA_GROUP 1 and 2), times every pass with CUDA events (the
+ * first call of each set is not counted), and keeps in the plan, per pass
+ * kind, the faster mode.  The kinds are the Gram, the split squarings, the
+ * plain squarings and the final product.  Later calls with
+ * IFNSO_OPT_CTA_GROUP = 0 (the default) use those modes.  `chosen` (host,
+ * 4 entries, or NULL) receives them in that order.  Same arguments and rules as
+ * ifnso_orthogonalize; `out` holds a valid result afterwards.  Synchronises
+ * `stream`.  BF16 plans only (IFNSO_ERR_UNSUPPORTED otherwise); reps in
+ * [1, 100]. */
+ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch,
+                                 const ifnso_coeffs* coeffs, void* const* out, void* workspace,
+                                 size_t workspace_bytes, int32_t reps, int32_t* chosen,
+                                 ifnso_stream_t stream);
+
 ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_in,
                                       const ifnso_batch_desc* dev_batch, const ifnso_coeffs* coeffs,
                                       void* const* dev_out, void* const* host_out, void* workspace,

@@ -20,6 +20,11 @@
 
 using namespace ifnso;
 
+namespace {
+// pass kinds of the tensor-core path, as ifnso_plan_autotune reports them
+constexpr int kGram = 0, kSplit = 1, kPlain = 2, kApply = 3, kKinds = 4;
+}  // namespace
+
 struct ifnso_plan {
   int64_t h = 0, w = 0;
   int dtype = IFNSO_BF16;
@@ -32,6 +37,8 @@ struct ifnso_plan {
   int inject_stall = 0;  // testing aid: the Gram pass's first CTA loads nothing
   int cta_group = 0;     // tensor-core passes: 0 auto, 1 per-CTA MMAs, 2 MMAs of the CTA pair
   int gram_e4m3 = 0;     // Gram from a scaled E4M3 copy of A
+  bool tuned = false;    // ifnso_plan_autotune chose cg_kind
+  int cg_kind[4] = {1, 2, 1, 1};  // MMA mode per pass kind (Gram, split squaring, plain squaring, product)
   int num_sms = 0;
   // metadata of the last batch (pinned host copy, uploaded into the workspace)
   uint64_t sig = 0;
@@ -1086,10 +1093,15 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   const Prec& pc = ly.prec;
   p.p_split = pc.p_split;
   p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
-  // auto: MMAs of the CTA pair for the split squarings (three products per
-  // stage hide the pair's handshakes), per-CTA MMAs for every other pass
-  auto cta_group = [&](bool split) { return plan->cta_group ? plan->cta_group : (split ? 2 : 1); };
-  p.cta_group = cta_group(false);
+  // automatic: the autotuned mode of each pass kind, else MMAs of the CTA pair
+  // for the split squarings (three products per stage hide the pair's
+  // handshakes) and per-CTA MMAs for every other pass
+  auto cta_group = [&](int kind) {
+    if (plan->cta_group) return plan->cta_group;
+    if (plan->tuned) return plan->cg_kind[kind];
+    return kind == kSplit ? 2 : 1;
+  };
+  p.cta_group = cta_group(kGram);
   p.probs = probs + ly.pi_gram;
   p.items = sym;
   p.n_items = static_cast<int32_t>(n_sym);
@@ -1130,7 +1142,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     p.final_pass = (j == L - 1);
     p.read_lo = split;
     p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
-    p.cta_group = cta_group(split != 0);
+    p.cta_group = cta_group(split ? kSplit : kPlain);
     if (!net) {
       // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
       // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
@@ -1159,10 +1171,57 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.coef_l = 0;
   p.final_pass = 0;
   p.read_lo = p.write_lo = 0;
-  p.cta_group = cta_group(false);
+  p.cta_group = cta_group(kApply);
   IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream), "apply pass");
   IFNSO_CUDA(mark_pass(false), "timing event");
   return IFNSO_OK;
+}
+
+// ifnso_pass_times with the plan's mutex held.
+ifnso_status pass_times_locked(ifnso_plan* plan, double* ms_out, int32_t max_passes, int32_t* n_passes,
+                               int32_t* n_calls) {
+  for (int k = 0; k < max_passes; ++k) ms_out[k] = 0.0;
+  *n_passes = 0;
+  int ncalls = 0;
+  // eager calls since the last query, then each captured call once (its
+  // events hold the durations of the graph's latest replay)
+  for (auto* list : {&plan->ev_calls, &plan->ev_graph}) {
+    for (auto& c : *list) {
+      if (c.size() < 2) continue;
+      IFNSO_CUDA(cudaEventSynchronize(c.back()), "cudaEventSynchronize");
+      const int np = static_cast<int>(c.size()) - 1;
+      *n_passes = np;
+      ++ncalls;
+      for (int k = 0; k < np && k < max_passes; ++k) {
+        float ms = 0.f;
+        IFNSO_CUDA(cudaEventElapsedTime(&ms, c[k], c[k + 1]), "cudaEventElapsedTime");
+        ms_out[k] += ms;
+      }
+    }
+  }
+  if (n_calls) *n_calls = ncalls;
+  for (auto& c : plan->ev_calls)
+    for (cudaEvent_t e : c) plan->ev_pool.push_back(e);
+  plan->ev_calls.clear();
+  return IFNSO_OK;
+}
+
+// ifnso_orthogonalize with the plan's mutex held.
+ifnso_status orthogonalize_locked(ifnso_plan* plan, const ifnso_batch_desc* batch, const ifnso_coeffs* coeffs,
+                                  void* const* out, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  std::vector<Shape> shp;
+  ifnso_status st = check_call(plan, batch, coeffs, out, shp);
+  if (st != IFNSO_OK || batch->count == 0) return st;
+  if ((st = init_plan_device(plan)) != IFNSO_OK) return st;
+  Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
+  if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  if ((st = upload_ifnso_meta(plan, ly, batch, out, ws, coeffs, {0, ly.count}, stream)) != IFNSO_OK) return st;
+  int hpad_max = 0;
+  for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
+  const Run r{plan, &ly, ws, coeffs, hpad_max, stream, true};
+  if (ly.f32) return run_f32(r);
+  return run_tc(r, 0, ly.count, 0, ly.n_sym, 0, ly.n_app);
 }
 
 }  // namespace
@@ -1314,21 +1373,62 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
                                  void* const* out, void* workspace, size_t workspace_bytes,
                                  ifnso_stream_t stream_) {
   if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  return orthogonalize_locked(plan, batch, coeffs, out, workspace, workspace_bytes,
+                              reinterpret_cast<cudaStream_t>(stream_));
+}
+
+ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch, const ifnso_coeffs* coeffs,
+                                 void* const* out, void* workspace, size_t workspace_bytes, int32_t reps,
+                                 int32_t* chosen, ifnso_stream_t stream_) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  if (reps < 1 || reps > 100) return fail(IFNSO_ERR_INVALID_ARG, "reps %d must be in [1, 100]", reps);
+  if (plan->dtype != IFNSO_BF16) return fail(IFNSO_ERR_UNSUPPORTED, "autotuning applies to BF16 plans");
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   std::lock_guard<std::mutex> lk(plan->mu);
-  std::vector<Shape> shp;
-  ifnso_status st = check_call(plan, batch, coeffs, out, shp);
-  if (st != IFNSO_OK || batch->count == 0) return st;
-  if ((st = init_plan_device(plan)) != IFNSO_OK) return st;
-  Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
-  if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
-  uint8_t* ws = static_cast<uint8_t*>(workspace);
-  if ((st = upload_ifnso_meta(plan, ly, batch, out, ws, coeffs, {0, ly.count}, stream)) != IFNSO_OK) return st;
-  int hpad_max = 0;
-  for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
-  const Run r{plan, &ly, ws, coeffs, hpad_max, stream, true};
-  if (ly.f32) return run_f32(r);
-  return run_tc(r, 0, ly.count, 0, ly.n_sym, 0, ly.n_app);
+  const int L = plan->L;
+  const Prec pc = resolve_prec(plan);
+  // pass index -> kind: 0 Gram, 1 prep (not tuned), 2.. squarings, L + 1 product
+  auto kind_of = [&](int pass) {
+    if (pass == 0) return kGram;
+    if (pass == L + 1) return kApply;
+    if (pass >= 2 && pass <= L) return (pass - 1) <= pc.k_split ? kSplit : kPlain;
+    return -1;
+  };
+  const int saved_cg = plan->cta_group, saved_stop = plan->stop_after;
+  const bool saved_timing = plan->timing, saved_tuned = plan->tuned;
+  plan->stop_after = -1;
+  plan->timing = true;
+  plan->tuned = false;
+  double ms[3][kKinds] = {};
+  ifnso_status st = IFNSO_OK;
+  std::vector<double> pt(L + 2);
+  for (int cg = 1; cg <= 2 && st == IFNSO_OK; ++cg) {
+    plan->cta_group = cg;
+    for (int r = 0; r <= reps && st == IFNSO_OK; ++r) {
+      st = orthogonalize_locked(plan, batch, coeffs, out, workspace, workspace_bytes, stream);
+      if (st != IFNSO_OK) break;
+      int np = 0;
+      // the first call warms up (metadata upload, first touch); the others count
+      st = pass_times_locked(plan, pt.data(), static_cast<int>(pt.size()), &np, nullptr);
+      if (r == 0) continue;
+      for (int k = 0; k < np; ++k)
+        if (kind_of(k) >= 0) ms[cg][kind_of(k)] += pt[k];
+    }
+  }
+  plan->cta_group = saved_cg;
+  plan->stop_after = saved_stop;
+  plan->timing = saved_timing;
+  if (st != IFNSO_OK) {
+    plan->tuned = saved_tuned;
+    return st;
+  }
+  for (int k = 0; k < kKinds; ++k) plan->cg_kind[k] = ms[2][k] < ms[1][k] ? 2 : 1;
+  plan->tuned = true;
+  plan->sig_valid = false;
+  if (chosen)
+    for (int k = 0; k < kKinds; ++k) chosen[k] = plan->cg_kind[k];
+  return IFNSO_OK;
 }
 
 ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_in,
@@ -1546,30 +1646,7 @@ ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_pass
                               int32_t* n_calls) {
   if (!plan || !ms_out || !n_passes || max_passes < 0) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(plan->mu);
-  for (int k = 0; k < max_passes; ++k) ms_out[k] = 0.0;
-  *n_passes = 0;
-  int ncalls = 0;
-  // eager calls since the last query, then each captured call once (its
-  // events hold the durations of the graph's latest replay)
-  for (auto* list : {&plan->ev_calls, &plan->ev_graph}) {
-    for (auto& c : *list) {
-      if (c.size() < 2) continue;
-      IFNSO_CUDA(cudaEventSynchronize(c.back()), "cudaEventSynchronize");
-      const int np = static_cast<int>(c.size()) - 1;
-      *n_passes = np;
-      ++ncalls;
-      for (int k = 0; k < np && k < max_passes; ++k) {
-        float ms = 0.f;
-        IFNSO_CUDA(cudaEventElapsedTime(&ms, c[k], c[k + 1]), "cudaEventElapsedTime");
-        ms_out[k] += ms;
-      }
-    }
-  }
-  if (n_calls) *n_calls = ncalls;
-  for (auto& c : plan->ev_calls)
-    for (cudaEvent_t e : c) plan->ev_pool.push_back(e);
-  plan->ev_calls.clear();
-  return IFNSO_OK;
+  return pass_times_locked(plan, ms_out, max_passes, n_passes, n_calls);
 }
 
 ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch, void* workspace,

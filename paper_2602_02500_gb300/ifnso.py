@@ -46,7 +46,8 @@ IFNSO_STATIC_NORM_MAX_MATRICES = 1024
 
 EXPORTED = [
     "ifnso_plan_create", "ifnso_plan_set", "ifnso_plan_get", "ifnso_plan_destroy",
-    "ifnso_workspace_bytes", "ifnso_orthogonalize", "ifnso_orthogonalize_host", "ns_iterate", "ns_workspace_bytes",
+    "ifnso_workspace_bytes", "ifnso_orthogonalize", "ifnso_orthogonalize_host", "ifnso_plan_autotune", "ns_iterate",
+    "ns_workspace_bytes",
     "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
     "ifnso_frobenius_norm2_static", "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
     "ifnso_launch_count", "ifnso_mlp_param_count", "ifnso_mlp_create", "ifnso_mlp_destroy",
@@ -74,6 +75,8 @@ _sig = {
     "ns_workspace_bytes": (C.c_size_t, [_P, C.POINTER(ifnso_batch_desc)]),
     "ifnso_orthogonalize": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(ifnso_coeffs),
                                       C.POINTER(_P), _P, C.c_size_t, _P]),
+    "ifnso_plan_autotune": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(ifnso_coeffs), C.POINTER(_P), _P,
+                                      C.c_size_t, C.c_int32, C.POINTER(C.c_int32), _P]),
     "ifnso_orthogonalize_host": (C.c_int, [_P, C.POINTER(_P), C.POINTER(ifnso_batch_desc), C.POINTER(ifnso_coeffs),
                                            C.POINTER(_P), C.POINTER(_P), _P, C.c_size_t, C.c_int32, _P]),
     "ns_iterate": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(C.c_double), C.c_int32, C.c_int32,
@@ -268,6 +271,20 @@ class Plan:
                                   ws.nbytes, _stream(stream)), "ifnso_orthogonalize")
         self._last_ws = ws
         return outs
+
+    def autotune(self, batch, coeffs, outs, reps=3, ws=None, stream=None):
+        """Time per-CTA and CTA-pair MMAs on this batch and keep the faster per
+        pass kind; returns the modes (Gram, split squaring, plain squaring, product)."""
+        cf = self._coeffs(batch, coeffs)
+        need = self.workspace_bytes(batch)
+        if ws is None:
+            ws = self.workspace(need)
+        optr = (C.c_void_p * max(len(outs), 1))(*[o.data_ptr() for o in outs])
+        chosen = (C.c_int32 * 4)()
+        check(ifnso_plan_autotune(self.handle, batch.ref(), C.byref(cf), optr, C.c_void_p(ws.ptr), ws.nbytes,
+                                  int(reps), chosen, _stream(stream)), "ifnso_plan_autotune")
+        self._last_ws = ws
+        return list(chosen)
 
     def orthogonalize_host(self, host_in, batch, coeffs, outs, host_out, groups=0, ws=None, stream=None):
         """Algorithm 1 on matrices in host memory: host_in[i] (page-locked CPU

@@ -152,3 +152,22 @@ def test_gram_e4m3_option(F):
     st, p = _plan(F, 256, 512, 4, dtype=0)  # F32 plans have no E4M3 Gram
     assert F.ifnso_plan_set(p, F.IFNSO_OPT_GRAM_E4M3, 1) == F.IFNSO_ERR_UNSUPPORTED
     F.ifnso_plan_destroy(p)
+
+
+def test_autotune_argument_checks(F):
+    st, p = _plan(F, 256, 512, 4)
+    w = (C.c_double * 5)(1.0, 0.1, 0.2, 0.3, 0.4)
+    cf = F.ifnso_coeffs(5, w, None, None)
+    ptrs = (C.c_void_p * 1)(16 * 1024)
+    rows = (C.c_int64 * 1)(256)
+    cols = (C.c_int64 * 1)(512)
+    desc = F.ifnso_batch_desc(1, ptrs, rows, cols, None)
+    outs = (C.c_void_p * 1)(32 * 1024)
+    for reps in (0, 101):
+        assert F.ifnso_plan_autotune(p, C.byref(desc), C.byref(cf), outs, None, 0, reps, None,
+                                     None) == F.IFNSO_ERR_INVALID_ARG
+    F.ifnso_plan_destroy(p)
+    st, p = _plan(F, 256, 512, 4, dtype=0)
+    assert F.ifnso_plan_autotune(p, C.byref(desc), C.byref(cf), outs, None, 0, 2, None,
+                                 None) == F.IFNSO_ERR_UNSUPPORTED
+    F.ifnso_plan_destroy(p)

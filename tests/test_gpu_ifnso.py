@@ -258,3 +258,30 @@ def test_bf16_ifnso_gram_e4m3_end_to_end(shape):
     err = rel(to_np(y), O.ifnso_alg1(to_np(x), w))
     print(f"E4M3 Gram {shape}: relative error {err:.3e}")
     assert err < 0.1
+
+
+def test_autotune_keeps_results():
+    """Autotuning picks a mode per pass kind; results stay those of the oracle
+    and agree with the untuned plan to rounding order."""
+    import torch
+
+    F = lib()
+    shapes = [(512, 1024), (768, 640), (256, 512)]
+    mats = [synth.gaussian(90 + i, *s) for i, s in enumerate(shapes)]
+    xs = [to_dev(m, "bf16") for m in mats]
+    L = 10
+    w = np.r_[1.0, coeffs(L)]
+    plan = F.Plan(768, 1024, "bf16", L=L)
+    b = F.Batch(xs)
+    ref = [torch.empty(x.shape, dtype=x.dtype, device=x.device) for x in xs]
+    plan.orthogonalize(b, w, ref)
+    torch.cuda.synchronize()
+    outs = [torch.empty(x.shape, dtype=x.dtype, device=x.device) for x in xs]
+    chosen = plan.autotune(b, w, outs, reps=2)
+    assert len(chosen) == 4 and all(c in (1, 2) for c in chosen)
+    assert plan.get(F.IFNSO_OPT_CTA_GROUP) == 0
+    plan.orthogonalize(b, w, outs)
+    torch.cuda.synchronize()
+    for x, y, r in zip(xs, outs, ref):
+        assert rel(to_np(y), to_np(r)) < 1e-3
+        assert rel(to_np(y), O.ifnso_alg1(to_np(x), w[1:])) < TOL["bf16"]
