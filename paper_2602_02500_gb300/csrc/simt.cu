@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(256) k_norm2(const MatInfo* mats, int bf16, do
 // ---------------------------------------------------------------- E4M3 Gram input
 // max |M_ij| of every matrix (block (x, m): rows [x chunk, (x + 1) chunk) of
 // matrix m; BF16), as the bit pattern of a non-negative float, into
-// MatScalars::amax of matrix m.
+// MatScalars::amax of matrix m.  Rows whose start is 16-byte aligned are read
+// as 16-byte vectors.
 __global__ void __launch_bounds__(256) k_amax(const MatInfo* mats, MatScalars* scal) {
   __shared__ float red[32];
   const MatInfo& mi = mats[blockIdx.y];
@@ -93,10 +94,22 @@ __global__ void __launch_bounds__(256) k_amax(const MatInfo* mats, MatScalars* s
   const int64_t r0 = blockIdx.x * chunk;
   const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
   const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(mi.in);
+  const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  const int64_t c8 = vec ? cols / 8 * 8 : 0;  // columns read as vectors
   float mx = 0.f;
-  const int64_t n = (r1 > r0 ? r1 - r0 : 0) * cols;
-  for (int64_t e = threadIdx.x; e < n; e += blockDim.x)
-    mx = fmaxf(mx, fabsf(__bfloat162float(A[(r0 + e / cols) * ld + e % cols])));
+  for (int64_t r = r0; r < r1; ++r) {
+    const __nv_bfloat16* row = A + r * ld;
+    for (int64_t c = threadIdx.x * 8; c < c8; c += blockDim.x * 8) {
+      const uint4 u = *reinterpret_cast<const uint4*>(row + c);
+      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float2 f = __bfloat1622float2(h2[t]);
+        mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+      }
+    }
+    for (int64_t c = c8 + threadIdx.x; c < cols; c += blockDim.x) mx = fmaxf(mx, fabsf(__bfloat162float(row[c])));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -109,30 +122,68 @@ __global__ void __launch_bounds__(256) k_amax(const MatInfo* mats, MatScalars* s
   }
 }
 
-// A s in E4M3 (round to nearest even, saturating at +-448), K-major: A = M for
-// a wide matrix, M^T for a tall one (transposed through a 32 x 33 tile).
-// Block (x, y, m) writes output rows [32 y, 32 y + 32), columns [32 x, 32 x + 32).
+// Four values of A s in E4M3 (round to nearest even, saturating at +-448),
+// packed little-endian into 32 bits.
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
+}
+
+// A s in E4M3, K-major: A = M for a wide matrix, M^T for a tall one.  Block
+// (x, y, m) writes output rows [32 y, 32 y + 32) and columns
+// [128 x, 128 x + 128) of matrix m: a wide matrix is converted row by row
+// (each thread 4 consecutive values, one 32-bit store); a tall one goes
+// through a 128 x 33 tile so that both its reads and its writes are along
+// rows of their matrices.
 __global__ void __launch_bounds__(256) k_cast_e4m3(const MatInfo* mats, const MatScalars* scal) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[128][33];
   const MatInfo& mi = mats[blockIdx.z];
   const int h = mi.h, w = mi.w;
-  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 128;
   if (i0 >= h || k0 >= w) return;
   const __nv_bfloat16* M = static_cast<const __nv_bfloat16*>(mi.in);
   const float s = e4m3_scale(scal[blockIdx.z].amax);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  // source block: rows i0.., columns k0.. of M (wide), or rows k0.., columns i0.. (tall)
-  const int64_t sr0 = mi.trans ? k0 : i0, sc0 = mi.trans ? i0 : k0;
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t sr = sr0 + r, sc = sc0 + tx;
-    tile[r][tx] = (sr < mi.rows && sc < mi.cols) ? __bfloat162float(M[sr * mi.ld + sc]) : 0.f;
+  const int t = threadIdx.x;
+  // output row i0 + (t >> 3) (+ 32 / 8 per step), columns k0 + 4 (t & 7) + 32 j
+  if (!mi.trans) {
+    for (int rr = t >> 5; rr < 32; rr += 8) {
+      const int oi = i0 + rr;
+      if (oi >= h) break;
+      const int ok = k0 + 4 * (t & 31);
+      if (ok >= w) continue;
+      const __nv_bfloat16* src = M + static_cast<int64_t>(oi) * mi.ld + ok;
+      float v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = (ok + q < w) ? __bfloat162float(src[q]) * s : 0.f;
+      uint8_t* dst = mi.a8 + static_cast<int64_t>(oi) * mi.a8ld + ok;
+      const uint32_t packed = e4m3x4(v[0], v[1], v[2], v[3]);
+      if (ok + 4 <= w) {
+        *reinterpret_cast<uint32_t*>(dst) = packed;  // a8ld and ok are multiples of 4
+      } else {
+        for (int q = 0; ok + q < w; ++q) dst[q] = static_cast<uint8_t>(packed >> (8 * q));
+      }
+    }
+    return;
+  }
+  // tall: source rows k0..k0+127 of M, columns i0..i0+31
+  for (int r = t >> 5; r < 128; r += 8) {
+    const int64_t sr = k0 + r, sc = i0 + (t & 31);
+    tile[r][t & 31] = (sr < mi.rows && sc < mi.cols) ? __bfloat162float(M[sr * mi.ld + sc]) : 0.f;
   }
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int oi = i0 + r, ok = k0 + tx;
-    if (oi < h && ok < w) {
-      const float v = (mi.trans ? tile[tx][r] : tile[r][tx]) * s;
-      mi.a8[static_cast<int64_t>(oi) * mi.a8ld + ok] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  for (int rr = t >> 5; rr < 32; rr += 8) {
+    const int oi = i0 + rr;
+    const int kk = 4 * (t & 31);
+    const int ok = k0 + kk;
+    if (oi >= h || ok >= w) continue;
+    const uint32_t packed = e4m3x4(tile[kk][rr] * s, tile[kk + 1][rr] * s, tile[kk + 2][rr] * s,
+                                   tile[kk + 3][rr] * s);
+    uint8_t* dst = mi.a8 + static_cast<int64_t>(oi) * mi.a8ld + ok;
+    if (ok + 4 <= w) {
+      *reinterpret_cast<uint32_t*>(dst) = packed;
+    } else {
+      for (int q = 0; ok + q < w; ++q) dst[q] = static_cast<uint8_t>(packed >> (8 * q));
     }
   }
 }
@@ -369,7 +420,7 @@ cudaError_t launch_amax(const MatInfo* d_mats, int count, MatScalars* scal, int 
 cudaError_t launch_cast_e4m3(const MatInfo* d_mats, int count, int max_h, int max_w, MatScalars* scal,
                              cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  k_cast_e4m3<<<dim3((max_w + 31) / 32, (max_h + 31) / 32, count), 256, 0, s>>>(d_mats, scal);
+  k_cast_e4m3<<<dim3((max_w + 127) / 128, (max_h + 31) / 32, count), 256, 0, s>>>(d_mats, scal);
   count_launch();
   return cudaGetLastError();
 }
