@@ -246,18 +246,38 @@ Prec resolve_prec(const ifnso_plan* p) {
   return r;
 }
 
-// Matrices [b[g], b[g + 1]) form group g: contiguous index ranges of about
-// equal work (h_pad^2 w each), at most `groups` of them, none empty.
-std::vector<int> group_bounds(const std::vector<Shape>& shp, int groups) {
+// Matrices [b[g], b[g + 1]) form group g: contiguous index ranges, at most
+// `groups` of them, none empty, cut where the cumulative work (h_pad^2 w per
+// matrix) crosses the targets.  Equal shares, or with `ramp` (6 groups or
+// more) 1/48 and 1/16 of the work in the first two and the last two groups
+// and equal shares in between: the upload before the first group's passes
+// and the download after the last group's are then short, and every middle
+// group's passes still outlast the next group's upload.
+std::vector<int> group_bounds(const std::vector<Shape>& shp, int groups, bool ramp = false) {
   const int n = static_cast<int>(shp.size());
+  std::vector<double> target;  // cumulative work fractions of the cuts
+  if (ramp && groups >= 6) {
+    const double e1 = 1.0 / 48.0, e2 = 1.0 / 16.0;
+    const double mid = (1.0 - 2.0 * (e1 + e2)) / (groups - 4);
+    double t = 0.0;
+    for (int g = 0; g + 1 < groups; ++g) {
+      t += (g == 0) ? e1 : (g == 1) ? e2 : (g == groups - 2) ? e2 : mid;
+      target.push_back(t);
+    }
+  } else {
+    for (int g = 1; g < groups; ++g) target.push_back(static_cast<double>(g) / groups);
+  }
   std::vector<int> b{0};
   double total = 0.0;
   for (const Shape& s : shp) total += static_cast<double>(s.hpad) * s.hpad * s.w;
   double acc = 0.0;
-  for (int i = 0; i + 1 < n; ++i) {
+  size_t next = 0;
+  for (int i = 0; i + 1 < n && next < target.size(); ++i) {
     acc += static_cast<double>(shp[i].hpad) * shp[i].hpad * shp[i].w;
-    const int g = static_cast<int>(b.size());
-    if (g < groups && acc >= total * g / groups) b.push_back(i + 1);
+    if (acc >= total * target[next]) {
+      b.push_back(i + 1);
+      while (next < target.size() && acc >= total * target[next]) ++next;
+    }
   }
   b.push_back(n);
   return b;
@@ -1451,7 +1471,7 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   const int n = ly.count;
   const int want = ly.f32 ? 1 : std::min(groups <= 0 ? 8 : groups, n);
-  const std::vector<int> gb = group_bounds(shp, want);
+  const std::vector<int> gb = group_bounds(shp, want, true);
   const int ng = static_cast<int>(gb.size()) - 1;
   if ((st = upload_ifnso_meta(plan, ly, dev_batch, dev_out, ws, coeffs, gb, stream)) != IFNSO_OK) return st;
   if ((st = ensure_copy_streams(plan, ng)) != IFNSO_OK) return st;
