@@ -1175,6 +1175,9 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
       p.p_mode = j == 1 ? 0 : (j == 2 ? 4 : ((j & 1) == 0 ? 2 : (j == L - 1 ? 3 : 0)));
       p.feat = j == 1 ? 1 : 0;
     }
+    // passes whose P update has no D_l term take 2 D_l - D_l^2 from the MMAs
+    // (the feature pass needs D_l^2 itself)
+    p.fold_d = ((p.p_mode == 0 || p.p_mode == 3) && !p.feat) ? 1 : 0;
     IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, n_sym), stream), "squaring pass");
     if (net && j == 1) {
       IFNSO_CUDA(mlp_infer(net->prm, net->K, net->wfix, net->scale, net->stats, d_mats, scal, count,
@@ -1191,6 +1194,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.coef_l = 0;
   p.final_pass = 0;
   p.read_lo = p.write_lo = 0;
+  p.fold_d = 0;
   p.cta_group = cta_group(kApply);
   IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream), "apply pass");
   IFNSO_CUDA(mark_pass(false), "timing event");

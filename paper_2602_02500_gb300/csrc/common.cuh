@@ -24,6 +24,7 @@ enum EpiKind : int {
   EPI_NS_SQR = 4,    // B = b S + c S^2 (BF16, direct + mirrored)
   EPI_NS_APPLY = 5,  // X <- a X + (B X  or  b S X)
   EPI_GRAM_F8 = 6,   // T_0 from E4M3 copies of A (kind::f8f6f4), rescaled; else as EPI_GRAM
+  EPI_SQR_FOLD = 7,  // EPI_SQR with -2 D_l folded into the MMAs (chosen by TcParams::fold_d)
 };
 
 // Per-matrix scalars kept in the workspace (64 bytes).
@@ -129,6 +130,9 @@ struct TcParams {
   uint32_t wait_ms;    // limit of every pipeline wait (0: the default of ptx.cuh)
   int32_t cta_group;   // 2: MMAs of the CTA pair (M = 256, B halves stay in each CTA);
                        // 1: per-CTA MMAs with the B tile multicast to both CTAs
+  int32_t fold_d;      // EPI_SQR: the MMAs also add -2 D_l (an identity product), so the
+                       // accumulator holds D_l^2 - 2 D_l = -D_{l+1} and the epilogue
+                       // does not read D_l (passes whose P update has no D_l term)
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;

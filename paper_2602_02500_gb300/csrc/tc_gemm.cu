@@ -51,6 +51,7 @@ constexpr uint32_t kTileA = BM * BK * 2;  // 16 KB: 128 rows x 64 K of 16-bit va
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStageLd = 33;                               // padded row of a transpose buffer
 constexpr uint32_t kStageBytes = kEpiWarps * 32 * kStageLd * 4;  // one 32 x 33 float buffer per epilogue warp
+constexpr uint32_t kIdBytes = 512;  // -2 I, the 16 x 16 FP16 B operand of the squarings' identity products
 constexpr int kDevTimeout = 4;  // IFNSO_DEV_TIMEOUT
 
 template <int NA, int NB, int CG>
@@ -61,8 +62,8 @@ struct Cfg {
   static constexpr uint32_t stage_bytes = NA * kTileA + NB * tile_b;
   static constexpr int stages_fit = static_cast<int>((200u * 1024u) / stage_bytes);
   static constexpr int stages = stages_fit > 6 ? 6 : stages_fit;
-  // tiles + 1 KB alignment slack + barriers / flags + epilogue transpose buffers
-  static constexpr uint32_t smem = stages * stage_bytes + 1024 + 256 + kStageBytes;
+  // tiles + 1 KB alignment slack + barriers / flags + identity tile + epilogue transpose buffers
+  static constexpr uint32_t smem = stages * stage_bytes + 1024 + 256 + kIdBytes + kStageBytes;
 };
 
 // Number of products per K step: every (A source, B source) pair except
@@ -322,10 +323,12 @@ struct EpiIn {
 
 template <int EPI>
 __device__ __forceinline__ void epilogue_load(const TcParams& p, const TcProblem& pr, int r0, int c0, EpiIn& in) {
-  if constexpr (EPI == EPI_SQR) {
+  if constexpr (EPI == EPI_SQR || EPI == EPI_SQR_FOLD) {
     const int64_t off = static_cast<int64_t>(r0) * pr.ld_aux + c0;
-    blk_load<__half>(in.a, static_cast<const __half*>(pr.aux0) + off, pr.ld_aux);
-    if (p.read_lo) blk_load<__half>(in.b, static_cast<const __half*>(pr.aux1) + off, pr.ld_aux);
+    if constexpr (EPI == EPI_SQR) {
+      blk_load<__half>(in.a, static_cast<const __half*>(pr.aux0) + off, pr.ld_aux);
+      if (p.read_lo) blk_load<__half>(in.b, static_cast<const __half*>(pr.aux1) + off, pr.ld_aux);
+    }
     if (p.p_mode >= 2) blk_load<float>(in.c, pr.pacc + off, pr.ld_aux);
   } else if constexpr (EPI == EPI_NS_SQR) {
     blk_load<__nv_bfloat16>(in.a, static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r0) * pr.ld_aux + c0,
@@ -357,7 +360,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = u2f(u[j]);
   };
-  if constexpr (EPI != EPI_SQR) take();
+  if constexpr (EPI != EPI_SQR && EPI != EPI_SQR_FOLD) take();
   if constexpr (EPI == EPI_GRAM_F8) {
     // the E4M3 products are of A s: T_0 = (A s)(A s)^T / s^2 (s a power of two)
     const float sc = e4m3_scale(p.scal[pr.mat].amax);
@@ -372,13 +375,15 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       if (c0 + j == r) ea.tr += v[j];
     }
     store_blk<float>(pr.pacc, pr.ld_aux, r0, c0, v, st);
-  } else if constexpr (EPI == EPI_SQR) {
+  } else if constexpr (EPI == EPI_SQR || EPI == EPI_SQR_FOLD) {
     float d[32], lo[32];
-    blk_unpack<__half>(in.a, st, d);
-    if (p.read_lo) {
-      blk_unpack<__half>(in.b, st, lo);
+    if constexpr (EPI == EPI_SQR) {
+      blk_unpack<__half>(in.a, st, d);
+      if (p.read_lo) {
+        blk_unpack<__half>(in.b, st, lo);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) d[j] += lo[j];
+        for (int j = 0; j < 32; ++j) d[j] += lo[j];
+      }
     }
     take();
     // P = (1 + sum w) I - sum_l w_l D_l is accumulated two terms at a time:
@@ -410,11 +415,20 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
 #pragma unroll
       for (int j = 0; j < 32; ++j) pv[j] = (c0 + j == r) ? c0f : 0.f;
     }
+    if constexpr (EPI == EPI_SQR_FOLD) {
+      // the accumulator holds D_l^2 - 2 D_l = -D_{l+1}; no P term of this pass uses D_l
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float dn = 2.0f * d[j] - v[j];  // D_{l+1} = 2 D_l - D_l^2
-      v[j] = dn;
-      pv[j] = fmaf(-w, dn, fmaf(-wp, d[j], pv[j]));
+      for (int j = 0; j < 32; ++j) {
+        v[j] = -v[j];
+        pv[j] = fmaf(-w, v[j], pv[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float dn = 2.0f * d[j] - v[j];  // D_{l+1} = 2 D_l - D_l^2
+        v[j] = dn;
+        pv[j] = fmaf(-w, dn, fmaf(-wp, d[j], pv[j]));
+      }
     }
     if (!p.final_pass) {
       if (p.p_mode != 0) {
@@ -484,7 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   using PR = Products<NA, NB>;
   constexpr int S = C::stages;
   // D_l are FP16, the E4M3 Gram's operands E4M3 (format code 0 of its kind), all else BF16
-  constexpr uint32_t kIsBf16 = (EPI == EPI_SQR || EPI == EPI_GRAM_F8) ? 0u : 1u;
+  constexpr bool kSqr = (EPI == EPI_SQR || EPI == EPI_SQR_FOLD);
+  constexpr uint32_t kIsBf16 = (kSqr || EPI == EPI_GRAM_F8) ? 0u : 1u;
   constexpr bool kF8 = (EPI == EPI_GRAM_F8);
   constexpr int kBKe = kF8 ? 2 * BK : BK;  // elements per 128-byte K block
   constexpr uint16_t kPair = 0x3;                           // both CTAs of the cluster
@@ -536,6 +551,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   if (warp == 1) {
     tmem_alloc<CG>(smem_u32(tmem_slot), kTmemCols);
     tmem_relinquish<CG>();
+  }
+  // -2 I for the squarings that fold -2 D_l into the accumulator: a 16 x 16
+  // FP16 B operand, K-major without swizzle, core matrix (n block, k block)
+  // at byte 256 n + 128 k (8 rows of 16 bytes), -2 I_8 on the diagonal
+  // blocks.  With MMAs of the CTA pair each CTA holds 8 of the 16 rows: the
+  // even CTA rows 0..7 (core matrix (0, 0)), the odd CTA rows 8..15 (core
+  // matrix (0, 1) of its half).  Either way the tile is symmetric, as is
+  // each of its core matrices.
+  const uint32_t id_tile = base + S * C::stage_bytes + 256;
+  if constexpr (EPI == EPI_SQR_FOLD) {
+    if (warp == 2) {
+      const int cm = lane >> 3, i = lane & 7;  // core matrix, row within it
+      const bool diag = (CG == 1) ? (cm == 0 || cm == 3) : (cm == crank);
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (diag && (i >> 1) == t) w[t] = (i & 1) ? 0xC0000000u : 0x0000C000u;  // -2.0 at column i
+      *reinterpret_cast<uint4*>(base_ptr + S * C::stage_bytes + 256 + 16 * lane) = make_uint4(w[0], w[1], w[2], w[3]);
+      fence_proxy_async_smem();
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -593,9 +628,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint32_t st = base + stage * C::stage_bytes;
           const int k0 = kb * kBKe;
           // K blocks left of the diagonal block of a symmetric operand come
-          // from the stored block across the diagonal, read MN-major
+          // from the stored block across the diagonal, read MN-major.  B is
+          // read MN-major in the diagonal block too, so that the product is
+          // D D (not D D^T) there: a rounding asymmetry of a diagonal block
+          // then decays under D -> 2 D - D^2 instead of doubling every pass.
           const bool at = (pr.sym & kSymA) && (kb >> 2) < (wi.tm >> 1);
-          const bool bt = (pr.sym & kSymB) && (kb >> 2) < wi.tn;
+          const bool bt = (pr.sym & kSymB) && (kb >> 2) <= wi.tn;
           const int a_mn = pr.a_mn | at, b_mn = pr.b_mn | bt;
 #pragma unroll
           for (int a = 0; a < NA; ++a) {
@@ -677,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           const uint32_t st = base + stage * C::stage_bytes;
           // the layout the producer chose for this K block
           const uint32_t a_mn = static_cast<uint32_t>(pr.a_mn | ((pr.sym & kSymA) && (kb >> 2) < (wi.tm >> 1)));
-          const uint32_t b_mn = static_cast<uint32_t>(pr.b_mn | ((pr.sym & kSymB) && (kb >> 2) < wi.tn));
+          const uint32_t b_mn = static_cast<uint32_t>(pr.b_mn | ((pr.sym & kSymB) && (kb >> 2) <= wi.tn));
           const uint32_t idesc = idesc_f16(kIsBf16, CG * BM, BN, a_mn, b_mn);
 #pragma unroll
           for (int k = 0; k < BK / 16; ++k) {
@@ -693,6 +731,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 umma_e4m3<CG>(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
               else
                 umma_f16<CG>(d_tmem, ad, bd, idesc, (kb | k | q) != 0 ? 1u : 0u);
+            }
+          }
+          if constexpr (EPI == EPI_SQR_FOLD) {
+            // -2 D_l into the accumulator: in the K blocks of the tile's own
+            // columns the A tile is D_l there, so one N = 16 MMA per 16-wide
+            // K step and A source against -2 I adds -2 D_l to the 16 columns
+            // that K step covers
+            if ((kb >> 2) == wi.tn) {
+              const uint32_t id16 = idesc_f16(0u, CG * BM, 16, a_mn, 0u);
+              const uint64_t bd = sdesc_plain(id_tile, 128, CG == 1 ? 256 : 128);
+              const uint32_t d_col = d_tmem + static_cast<uint32_t>(64 * (kb & 3));
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                  const uint32_t sa = st + a * kTileA;
+                  const uint64_t ad = a_mn ? sdesc_sw128(sa + k * 2048, 8192, 1024)
+                                           : sdesc_sw128(sa + k * 32, 16, 1024);
+                  umma_f16<CG>(d_col + static_cast<uint32_t>(16 * k), ad, bd, id16, 1u);
+                }
+              }
             }
           }
           // frees the stage in both CTAs once these MMAs have read it
@@ -716,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
-    float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256) + (warp - 2) * 32 * kStageLd;
+    float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256 + kIdBytes) + (warp - 2) * 32 * kStageLd;
     const int q = warp & 3;            // TMEM lane quadrant this warp may access
     const int half = (warp - 2) >> 2;  // which 128 of the tile's 256 columns
     int local = 0;
@@ -772,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           if (tr != 0.f) atomicAdd(&p.scal[pr.mat].trace, static_cast<double>(tr));
         }
       }
-      if constexpr (EPI == EPI_SQR) {
+      if constexpr (kSqr) {
         if (p.feat) {
           const float ss = warp_reduce_sum(ea.ss);
           if (lane == 0)
@@ -846,6 +905,10 @@ cudaError_t dispatch(int epi, int na, const TcParams& p, int max_clusters, cudaS
     case EPI_GRAM_F8:
       return launch_one<1, 1, EPI_GRAM_F8, CG>(p, max_clusters, s);
     case EPI_SQR:
+      if (p.fold_d) {
+        if (na == 2) return launch_one<2, 2, EPI_SQR_FOLD, CG>(p, max_clusters, s);
+        return launch_one<1, 1, EPI_SQR_FOLD, CG>(p, max_clusters, s);
+      }
       if (na == 2) return launch_one<2, 2, EPI_SQR, CG>(p, max_clusters, s);
       return launch_one<1, 1, EPI_SQR, CG>(p, max_clusters, s);
     case EPI_APPLY:
