@@ -184,6 +184,13 @@ __device__ __forceinline__ int blk_col() {
   return ((threadIdx.x & 31) % Blk<T>::kLanesPerRow) * Blk<T>::kPer;
 }
 
+// The staging buffer is also the source of this lane's bulk stores (below):
+// before the warp writes it again, every lane's copies must have read it.
+__device__ __forceinline__ void st_acquire() {
+  bulk_wait_read();
+  __syncwarp();
+}
+
 // Issue the loads of the 32 x 32 block at src (row-major, leading dimension
 // ld, 16-byte aligned rows); the values are used after blk_unpack.
 template <typename T>
@@ -222,7 +229,7 @@ template <typename T, bool TRANS = false>
 __device__ __forceinline__ void blk_unpack(const RawBlk& raw, float* st, float* d) {
   const int lane = threadIdx.x & 31;
   const int cc = blk_col<T>();
-  __syncwarp();
+  st_acquire();
 #pragma unroll
   for (int s = 0; s < Blk<T>::kPasses; ++s) {
     float x[Blk<T>::kPer];
@@ -239,7 +246,7 @@ __device__ __forceinline__ void blk_unpack(const RawBlk& raw, float* st, float* 
 // Lane t's 32 values become row t of the staged block.
 __device__ __forceinline__ void blk_put(float* st, const float* v) {
   const int lane = threadIdx.x & 31;
-  __syncwarp();
+  st_acquire();
 #pragma unroll
   for (int j = 0; j < 32; ++j) st[lane * kStageLd + j] = v[j];
   __syncwarp();
@@ -288,10 +295,36 @@ __device__ __forceinline__ void blk_store_bounded(T* dst, int64_t ld, const floa
 // Store the 32 x 32 block whose rows are lanes' v (rows r0.., columns c0..)
 // into an h_pad x h_pad buffer.  Symmetric results are computed and stored on
 // the upper 256 x 256 blocks only; their readers take the rest from there.
-template <typename T>
+// kBulk: each lane writes its row, 64 bytes at a time, into the staging
+// buffer (rows 80 bytes apart, so that eight lanes' 16-byte stores cover all
+// banks) and hands it to the bulk-copy engine.  The block then leaves without
+// global store instructions, whose traffic through the load/store path slows
+// the TMA operand loads of the main loop.  FP32 rows go as two pieces, the
+// second after the engine has read the first; that wait costs more than it
+// saves where the epilogue also loads (P in the squarings), so only the Gram
+// stores FP32 this way.  Otherwise the block goes through blk_store.
+template <typename T, bool kBulk = (sizeof(T) == 2)>
 __device__ __forceinline__ void store_blk(T* buf, int64_t ld, int r0, int c0, const float* v, float* st) {
-  blk_put(st, v);
-  blk_store<T, false>(buf + static_cast<int64_t>(r0) * ld + c0, ld, st);
+  if constexpr (kBulk) {
+    constexpr int kPieces = sizeof(T) == 4 ? 2 : 1;
+    constexpr int kCols = 32 / kPieces;  // columns per 64-byte piece
+    const int lane = threadIdx.x & 31;
+    uint8_t* row = reinterpret_cast<uint8_t*>(st) + lane * 80;
+    T* dst = buf + static_cast<int64_t>(r0 + lane) * ld + c0;
+#pragma unroll
+    for (int pc = 0; pc < kPieces; ++pc) {
+      st_acquire();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(row + 16 * q) = pack16<T>(v + pc * kCols + q * (16 / sizeof(T)));
+      fence_proxy_async_smem();
+      bulk_store_s2g(dst + pc * kCols, smem_u32(row), 64);
+      bulk_commit();
+    }
+  } else {
+    blk_put(st, v);
+    blk_store<T, false>(buf + static_cast<int64_t>(r0) * ld + c0, ld, st);
+  }
 }
 
 // BF16 output block of the tile (rows r0.., columns c0..), clipped to the
@@ -374,7 +407,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       ea.ss = fmaf(v[j], v[j], ea.ss);
       if (c0 + j == r) ea.tr += v[j];
     }
-    store_blk<float>(pr.pacc, pr.ld_aux, r0, c0, v, st);
+    store_blk<float, true>(pr.pacc, pr.ld_aux, r0, c0, v, st);
   } else if constexpr (EPI == EPI_SQR || EPI == EPI_SQR_FOLD) {
     float d[32], lo[32];
     if constexpr (EPI == EPI_SQR) {
@@ -839,6 +872,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
       }
     }
+    bulk_wait_all();  // the epilogue's bulk stores are complete before the CTA exits
   }
 
   __syncthreads();
