@@ -414,37 +414,52 @@ def main():
     fl = sum(flops_ifnso(h, w, L) for h, w in hw)
     tflops = world * fl * args.steps / (ms_total / 1000.0) / 1e12
 
-    # the dominant kernel: the squaring pass with split operands (the first k of
-    # the L - 1 squarings; the others run with plain FP16 operands)
+    # The dominant kernel: the squaring instantiation with the most time per
+    # step.  Squarings j = 1..L-1 take split operands for j <= k (the rest
+    # plain FP16), and every squaring whose P update has no D_l term folds
+    # -2 D_l into its MMAs (a separate kernel instantiation): with fixed
+    # coefficients the even ones, with proposed coefficients the odd ones
+    # from 3 on.
     peaks, peak_src = load_peaks()
     mode = plan.get(F.IFNSO_OPT_PRECISION)
     k_split = {F.IFNSO_PREC_SPLIT: L - 1, F.IFNSO_PREC_MIXED: max(0, L - 8)}.get(mode, 0)
     per_step = [float(x) / max(1, calls) for x in pass_ms]
     sq = per_step[2:2 + (L - 1)] if L > 1 else []
-    sq_split, sq_plain = sq[:k_split], sq[k_split:]
+
+    def folded(j):
+        return (j % 2 == 0) if args.coeffs == "fixed" else (j % 2 == 1 and j >= 3)
+
+    variants = {}
+    for j, t in enumerate(sq, start=1):
+        key = ("split" if j <= k_split else "plain") + ("_fold" if folded(j) else "_p")
+        variants.setdefault(key, []).append(t)
     sq_alg = sum(2 * h ** 3 for h, _ in hw)  # algorithmic FLOPs per squaring launch
     hp = [((h + 255) // 256) * 256 for h, _ in hw]
     exec_one = sum(((p // 256) * (p // 256 + 1) // 2) * 2 * (2 * 128 * 256 * p) for p in hp)
-    dominant = "split" if sum(sq_split) >= sum(sq_plain) else "plain"
-    dom = sq_split if dominant == "split" else sq_plain
-    sq_launch_ms = float(np.mean(dom)) if dom else None
-    sq_exec = exec_one * (3 if dominant == "split" else 1)
-    traffic = load_traffic().get(f"{args.workload}:squaring_{dominant}")
+    dominant = max(variants, key=lambda k: sum(variants[k])) if variants else None
     roof = None
-    if sq_launch_ms:
+    if dominant:
+        dom = variants[dominant]
+        sq_launch_ms = float(np.mean(dom))
+        split = dominant.startswith("split")
+        sq_exec = exec_one * (3 if split else 1)
+        if dominant.endswith("_fold"):
+            # the identity products: one N = 16 MMA per K step and A source in
+            # the four K blocks of each 128 x 256 tile's own columns
+            sq_exec += sum(((p // 256) * (p // 256 + 1) // 2) * 2 * (2 * 128 * 16 * 256) for p in hp) * (2 if split else 1)
+        traffic = load_traffic().get(f"{args.workload}:squaring_{dominant}")
         ach = sq_alg / (sq_launch_ms / 1000.0) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        what = ("D_{l+1} = 2 D_l - D_l^2, -2 D_l folded into the MMAs" if dominant.endswith("_fold")
+                else "D_{l+1} = 2 D_l - D_l^2 with the P update fused")
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic,
-                "kernel": f"tc_gemm_kernel squaring pass, {dominant} operands "
-                          "(D_{l+1} = 2 D_l - D_l^2 with the P update fused)",
+                "kernel": f"tc_gemm_kernel squaring pass, {dominant.split('_')[0]} operands ({what})",
                 "launch_ms": sq_launch_ms, "launches_per_step": len(dom),
                 "algorithmic_flop_per_launch": sq_alg, "executed_flop_per_launch": sq_exec,
                 "executed_tflops": sq_exec / (sq_launch_ms / 1000.0) / 1e12,
                 "peak_source": f"bf16_tflops_sustained ({peak_src})",
-                "squarings": {"split": len(sq_split), "plain": len(sq_plain),
-                              "split_ms": float(np.mean(sq_split)) if sq_split else None,
-                              "plain_ms": float(np.mean(sq_plain)) if sq_plain else None},
+                "squarings": {k: {"launches": len(v), "ms": float(np.mean(v))} for k, v in sorted(variants.items())},
                 "pass_ms_per_step": per_step}
 
     # 5-step quintic Newton-Schulz on the same list
