@@ -142,6 +142,21 @@ def test_bf16_cta_groups(shape, L, precision):
     assert rel(out[1], out[2]) < 1e-3
 
 
+@pytest.mark.parametrize("L,precision", [(14, "mixed"), (14, "plain"), (16, "mixed")])
+def test_bf16_folded_squarings_stay_accurate(L, precision):
+    """Every other squaring folds -2 D_l into its MMAs, which rounds the two
+    entries (r, c) and (c, r) of a diagonal block at different points of the K
+    sum.  The next squaring forms D D there (B read MN-major), under which that
+    asymmetry decays; under D D^T it would double every pass.  On a
+    well-conditioned input D_l converges early, and the late squarings must
+    keep it exact: with the asymmetry doubling, this case reached 4.2e-2 (256 x
+    512, L = 14, mixed); the unfolded squarings give 1.7e-3."""
+    M = synth.gaussian(4, 256, 512)
+    F, plan, b, xs, ys, w = run_ifnso([M], L, "bf16", precision=precision)
+    err = rel(to_np(ys[0]), O.ifnso_alg1(to_np(xs[0]), w))
+    assert err < 1e-2, err
+
+
 @pytest.mark.parametrize("cg", [1, 2])
 def test_bf16_ns_cta_groups(cg):
     import torch
