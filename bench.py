@@ -75,6 +75,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="time eager calls instead of a captured CUDA graph of one step")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: one list shared out over the ranks (LPT on FLOPs), results exchanged")
+    ap.add_argument("--ablation", action="store_true",
+                    help="the L ablation on the Table 1 shapes (one JSON line of per-L rows) instead of the bench")
+    ap.add_argument("--ablation-L", default="2-16", help="range of L for --ablation, e.g. 2-16")
+    ap.add_argument("--ablation-seeds", type=int, default=10)
     return ap.parse_args()
 
 
@@ -240,6 +246,172 @@ def cpu_oracle_sample(shapes, L, budget_s=20.0):
     return len(shapes) / total, sample, os.cpu_count()
 
 
+def run_ablation(args):
+    """L ablation on the Table 1 shapes (Sec. 3.4, Table 1): N(0,1) matrices
+    128 x {128, 512, 1024}, seeds 0..S-1.  For each L, the library's GPU
+    learner fits w_1..w_L (Sec. 3.1.1 schedule) and the library orthogonalizes
+    the batch in an FP32 and a BF16 plan; the error is ||Y Y^T - I||_F (the
+    Table 1 metric), evaluated on the host in FP64 from the returned Y.  The
+    cubic NS with 8 steps (the Table 1 "Original NS") and Muon's quintic NS
+    with 5 steps run on the same inputs.  FLOPs follow Table 1's counting."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2602_02500_gb300 import ifnso as F
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    lo, hi = (int(v) for v in args.ablation_L.split("-"))
+    shapes = [(128, 128), (128, 512), (128, 1024)]
+    S = args.ablation_seeds
+    mats = [(h, w, synth.gaussian(seed, h, w)) for h, w in shapes for seed in range(S)]
+
+    def inputs(dtype):
+        out = []
+        for h, w, M in mats:
+            t = torch.tensor(M, dtype=torch.float32, device=dev)
+            out.append(t.to(torch.bfloat16) if dtype == "bf16" else t)
+        return out
+
+    def orth_err(ys):
+        per = {}
+        for (h, w, _), y in zip(mats, ys):
+            Y = y.double().cpu().numpy()
+            per.setdefault((h, w), []).append(float(np.linalg.norm(Y @ Y.T - np.eye(h))))
+        return {f"{h}x{w}": float(np.mean(v)) for (h, w), v in per.items()}
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    xin = {d: inputs(d) for d in ("f32", "bf16")}
+    rows = []
+    for L in range(lo, hi + 1):
+        w = F.learn_coefficients(L)
+        row = {"L": L, "flops": {f"{h}x{wd}": 4 * h * h * wd + 2 * (L - 1) * h ** 3 + L * h * h for h, wd in shapes}}
+        for d in ("f32", "bf16"):
+            xs = xin[d]
+            ys = [torch.empty_like(x) for x in xs]
+            plan = F.Plan(128, 1024, d, L=L)
+            b = F.Batch(xs)
+            ws = F.Workspace(plan.workspace_bytes(b), device=dev)
+            ms = timed(lambda: plan.orthogonalize(b, np.r_[1.0, w], ys, ws=ws))
+            row[f"err_{d}"] = orth_err(ys)
+            row[f"ms_{d}"] = ms
+        rows.append(row)
+    ns = {}
+    for name, poly, steps, fl in (("original_ns_8", (1.5, -0.5), 8, lambda h, w: 8 * (4 * h * h * w + 2 * h * w + h * h)),
+                                  ("muon_ns_5", MUON_ABC, 5, lambda h, w: 5 * (6 * h * h * w + 5 * h * w))):
+        ent = {"flops": {f"{h}x{wd}": fl(h, wd) for h, wd in shapes}}
+        for d in ("f32", "bf16"):
+            xs = xin[d]
+            zs = [torch.empty_like(x) for x in xs]
+            plan = F.Plan(128, 1024, d, L=1)
+            b = F.Batch(xs)
+            ws = F.Workspace(plan.ns_workspace_bytes(b), device=dev)
+            ms = timed(lambda: plan.ns_iterate(b, poly, steps, zs, ws=ws))
+            ent[f"err_{d}"] = orth_err(zs)
+            ent[f"ms_{d}"] = ms
+        ns[name] = ent
+    print(json.dumps({"metric": "L ablation: ||Y Y^T - I||_F and FLOPs on the Table 1 shapes", "impl": "ours",
+                      "data": f"synthetic: N(0,1), seeds 0..{S - 1} per shape",
+                      "shapes": [f"{h}x{w}" for h, w in shapes], "rows": rows, "ns": ns,
+                      "ms": "one call over all shapes and seeds (FP32 or BF16 plan), CUDA events, mean of 5"}),
+          flush=True)
+    return 0
+
+
+def run_shard(args):
+    """Strong scaling over N ranks: every rank holds the same list (seeds
+    0..n-1), orthogonalizes the share that greedy LPT on Algorithm 1's
+    nominal FLOPs gives it, and the results are then broadcast from their
+    owners, so that every rank ends with all of them (a replicated Muon
+    update).  The timed step is the library call plus the exchange."""
+    import numpy as np
+    import torch
+
+    from paper_2602_02500_gb300 import ifnso as F
+    from paper_2602_02500_gb300 import shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+    wl = WORKLOADS[args.workload]
+    shapes = workload_list(wl)
+    L = args.L or wl["L"]
+    n = len(shapes)
+    parts = shard.lpt_partition([shard.ifnso_cost(r, c, L) for _, r, c in shapes], world)
+    mine = parts[rank]
+    xs = make_inputs(F, torch, shapes, 0, device)
+    ys = [torch.empty_like(x) for x in xs]
+    hw = [oriented(r, c) for _, r, c in shapes]
+    sub = F.Batch([xs[i] for i in mine])
+    sub_out = [ys[i] for i in mine]
+    w_full = F.learn_coefficients(L)
+    coef = np.r_[1.0, w_full]
+    plan = F.Plan(max(hw[i][0] for i in mine), max(hw[i][1] for i in mine), "bf16", L=L,
+                  precision=args.precision)
+    plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
+    ws = F.Workspace(plan.workspace_bytes(sub), device=device)
+    if args.autotune and args.cta_group == 0:
+        plan.autotune(sub, coef, sub_out, reps=2, ws=ws)
+
+    def run_local(_idx):
+        plan.orthogonalize(sub, coef, sub_out, ws=ws)
+
+    def step():
+        shard.sharded_orthogonalize(run_local, ys, parts, rank, dist)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = max_over_ranks_of(dist, e0.elapsed_time(e1), device)
+    loads = [sum(shard.ifnso_cost(shapes[i][1], shapes[i][2], L) for i in p) for p in parts]
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": n * args.steps / (ms / 1000.0), "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + wl["desc"], "L": L,
+                       "parallelism": f"list sharded over {world} ranks (greedy LPT on FLOPs), results broadcast "
+                                      "from their owners",
+                       "matrices_per_rank": [len(p) for p in parts],
+                       "flop_share_max_over_mean": max(loads) / (sum(loads) / len(loads))},
+        }), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -291,6 +463,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        return run_ablation(args)
+    if args.shard:
+        return run_shard(args)
 
     import numpy as np
     import torch
