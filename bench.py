@@ -77,6 +77,8 @@ def parse():
                     help="time eager calls instead of a captured CUDA graph of one step")
     ap.add_argument("--shard", action="store_true",
                     help="strong scaling: one list shared out over the ranks (LPT on FLOPs), results exchanged")
+    ap.add_argument("--muon", action="store_true",
+                    help="time a whole Muon step (momentum, orthogonalization, fused weight update) on the list")
     ap.add_argument("--ablation", action="store_true",
                     help="the L ablation on the Table 1 shapes (one JSON line of per-L rows) instead of the bench")
     ap.add_argument("--ablation-L", default="2-16", help="range of L for --ablation, e.g. 2-16")
@@ -332,6 +334,72 @@ def run_ablation(args):
     return 0
 
 
+def run_muon(args):
+    """A whole Muon step on the list (ifnso_muon_step): the momentum update
+    and Nesterov input (one elementwise kernel per matrix), Algorithm 1 on
+    that input, and the weight update fused into the final product, captured
+    in one CUDA graph; beside it the orthogonalization alone on the same
+    list.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2602_02500_gb300 import ifnso as F
+
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    wl = WORKLOADS[args.workload]
+    shapes = workload_list(wl)
+    L = args.L or wl["L"]
+    n = len(shapes)
+    hw = [oriented(r, c) for _, r, c in shapes]
+    xs = make_inputs(F, torch, shapes, 0, device)
+    mom = [torch.zeros(x.shape, dtype=torch.float32, device=device) for x in xs]
+    stg = [torch.empty_like(x) for x in xs]
+    wts = [torch.zeros_like(x) for x in xs]
+    ys = [torch.empty_like(x) for x in xs]
+    batch = F.Batch(xs)
+    coef = np.r_[1.0, F.learn_coefficients(L)]
+    plan = F.Plan(max(h for h, _ in hw), max(w for _, w in hw), "bf16", L=L, precision=args.precision)
+    plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
+    ws = F.Workspace(plan.workspace_bytes(batch), device=device)
+    if args.autotune and args.cta_group == 0:
+        plan.autotune(batch, coef, ys, reps=2, ws=ws)
+
+    def graph(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        return g
+
+    def timed(g):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    g_muon = graph(lambda: plan.muon_step(batch, mom, stg, wts, coef, beta=0.95, nesterov=True, lr=0.02, ws=ws))
+    g_orth = graph(lambda: plan.orthogonalize(batch, coef, ys, ws=ws))
+    ms_muon, ms_orth = timed(g_muon), timed(g_orth)
+    print(json.dumps({
+        "metric": "Muon steps/s over the list (momentum, IFNSO, fused weight update)", "value": 1000.0 / ms_muon,
+        "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_muon,
+        "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + wl["desc"], "L": L, "matrices": n, "beta": 0.95,
+                   "nesterov": True, "momentum": "FP32", "weights": "BF16"},
+        "orthogonalize_only_ms": ms_orth, "overhead_ms": ms_muon - ms_orth,
+    }), flush=True)
+    return 0
+
+
 def run_shard(args):
     """Strong scaling over N ranks: every rank holds the same list (seeds
     0..n-1), orthogonalizes the share that greedy LPT on Algorithm 1's
@@ -467,6 +535,8 @@ def main():
         return run_ablation(args)
     if args.shard:
         return run_shard(args)
+    if args.muon:
+        return run_muon(args)
 
     import numpy as np
     import torch

@@ -238,6 +238,26 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
                                       void* const* dev_out, void* const* host_out, void* workspace,
                                       size_t workspace_bytes, int32_t groups, ifnso_stream_t stream);
 
+/* One Muon step around the orthogonalization (the optimizer of Sec. 3.3;
+ * the paper does not spell out its momentum, and this follows Muon's
+ * published form).  For every matrix i of `grads` (BF16 gradients G, the
+ * batch layout above):
+ *   M <- beta M + G                          momentum[i]: FP32, rows x cols contiguous
+ *   U <- G + beta M (nesterov = 1) or M      staging[i]: BF16, rows x cols, leading dimension ld[i]
+ *   W <- W - lr sqrt(max(1, rows/cols)) Y    weights[i]: BF16, rows x cols contiguous
+ * with Y the result of ifnso_orthogonalize on U (Algorithm 1, Sec. 2.4).
+ * The update is fused into the final product's epilogue: Y is never
+ * stored.  All four buffers are device memory owned by the caller, 16-byte
+ * aligned and pairwise distinct; the workspace is ifnso_workspace_bytes of
+ * `grads`.  beta in [0, 1), lr finite and >= 0, nesterov 0 or 1.  BF16
+ * plans only (IFNSO_ERR_UNSUPPORTED otherwise).  Asynchronous on `stream`,
+ * like ifnso_orthogonalize; capturable once it has run outside capture with
+ * the same buffers. */
+ifnso_status ifnso_muon_step(ifnso_plan* plan, const ifnso_batch_desc* grads, void* const* momentum,
+                             void* const* staging, void* const* weights, const ifnso_coeffs* coeffs, double beta,
+                             int32_t nesterov, double lr, void* workspace, size_t workspace_bytes,
+                             ifnso_stream_t stream);
+
 /* The comparison baseline, Newton-Schulz: X_0 = A/||A||_F (Eq. constraint),
  * then `steps` times X <- sum_n poly[n] (X X^T)^n X (Eq. general_eq_matrix):
  * degree 3 takes poly = (a, b) (the classical iteration is (1.5, -0.5),

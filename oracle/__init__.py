@@ -16,6 +16,7 @@ coeffs  the scalar polynomial f, the peak constraint on w_L (exact and the
         printed approximation), the Adam coefficient learner of Sec. 2.3/3.1.1.
 flops   the FLOP counts behind Table 1.
 mlp     FP64 forward/backward of the coefficient-proposal MLP.
+muon    one Muon step (momentum, Nesterov input, scaled update) around Algorithm 1.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, invariants, brute force or printed values, except the learned

@@ -683,6 +683,9 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     a.cols_out = static_cast<int32_t>(s.cols);
     a.ld_out = s.cols;
     a.out0 = mi.out;
+    // a Muon step reads the weights where the update goes (M's shape, contiguous)
+    a.aux0 = mi.out;
+    a.ld_aux = s.cols;
   }
   std::vector<WorkItem> sy, ap;
   sym_items(ly.shp, gb, sy);
@@ -1031,6 +1034,8 @@ struct Run {
   int hpad_max;
   cudaStream_t stream;
   bool whole;  // the whole batch in one go: per-pass timing events and IFNSO_OPT_STOP_AFTER apply
+  bool update = false;  // the product updates weights in place: W <- W - lr s Y (ifnso_muon_step)
+  float lr = 0.f;
 };
 
 // Coefficient rows of matrix `first` onwards (the SIMT kernels index a group from 0).
@@ -1195,6 +1200,8 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.final_pass = 0;
   p.read_lo = p.write_lo = 0;
   p.fold_d = 0;
+  p.update = r.update ? 1 : 0;
+  p.lr = r.lr;
   p.cta_group = cta_group(kApply);
   IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream), "apply pass");
   IFNSO_CUDA(mark_pass(false), "timing event");
@@ -1232,7 +1239,8 @@ ifnso_status pass_times_locked(ifnso_plan* plan, double* ms_out, int32_t max_pas
 
 // ifnso_orthogonalize with the plan's mutex held.
 ifnso_status orthogonalize_locked(ifnso_plan* plan, const ifnso_batch_desc* batch, const ifnso_coeffs* coeffs,
-                                  void* const* out, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+                                  void* const* out, void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                                  bool update = false, float lr = 0.f) {
   std::vector<Shape> shp;
   ifnso_status st = check_call(plan, batch, coeffs, out, shp);
   if (st != IFNSO_OK || batch->count == 0) return st;
@@ -1243,7 +1251,9 @@ ifnso_status orthogonalize_locked(ifnso_plan* plan, const ifnso_batch_desc* batc
   if ((st = upload_ifnso_meta(plan, ly, batch, out, ws, coeffs, {0, ly.count}, stream)) != IFNSO_OK) return st;
   int hpad_max = 0;
   for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
-  const Run r{plan, &ly, ws, coeffs, hpad_max, stream, true};
+  Run r{plan, &ly, ws, coeffs, hpad_max, stream, true};
+  r.update = update;
+  r.lr = lr;
   if (ly.f32) return run_f32(r);
   return run_tc(r, 0, ly.count, 0, ly.n_sym, 0, ly.n_app);
 }
@@ -1400,6 +1410,49 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
   std::lock_guard<std::mutex> lk(plan->mu);
   return orthogonalize_locked(plan, batch, coeffs, out, workspace, workspace_bytes,
                               reinterpret_cast<cudaStream_t>(stream_));
+}
+
+ifnso_status ifnso_muon_step(ifnso_plan* plan, const ifnso_batch_desc* grads, void* const* momentum,
+                             void* const* staging, void* const* weights, const ifnso_coeffs* coeffs, double beta,
+                             int32_t nesterov, double lr, void* workspace, size_t workspace_bytes,
+                             ifnso_stream_t stream_) {
+  if (!plan) return fail(IFNSO_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->dtype != IFNSO_BF16) return fail(IFNSO_ERR_UNSUPPORTED, "the Muon step needs a BF16 plan");
+  if (!grads || !momentum || !staging || !weights)
+    return fail(IFNSO_ERR_INVALID_ARG, "grads / momentum / staging / weights is NULL");
+  if (!(beta >= 0.0 && beta < 1.0)) return fail(IFNSO_ERR_INVALID_ARG, "beta = %g must be in [0, 1)", beta);
+  if (!(lr >= 0.0 && lr < 1e30)) return fail(IFNSO_ERR_INVALID_ARG, "lr = %g must be finite and >= 0", lr);
+  if (nesterov != 0 && nesterov != 1) return fail(IFNSO_ERR_INVALID_ARG, "nesterov must be 0 or 1");
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(plan->mu);
+  std::vector<Shape> shp;
+  ifnso_status st = read_batch(plan, grads, shp);
+  if (st != IFNSO_OK) return st;
+  std::vector<const void*> u_in(static_cast<size_t>(grads->count));
+  for (int i = 0; i < grads->count; ++i) {
+    const void* g = grads->in[i];
+    if (!momentum[i] || !staging[i] || !weights[i])
+      return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: NULL momentum, staging or weights", i);
+    for (const void* q : {static_cast<const void*>(momentum[i]), static_cast<const void*>(staging[i]),
+                          static_cast<const void*>(weights[i])})
+      if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
+        return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: momentum, staging and weights must be 16-byte aligned", i);
+    if (staging[i] == g || weights[i] == g || weights[i] == staging[i] || momentum[i] == g ||
+        momentum[i] == staging[i] || momentum[i] == weights[i])
+      return fail(IFNSO_ERR_INVALID_ARG, "matrix %d: grads, momentum, staging and weights must be distinct", i);
+    u_in[static_cast<size_t>(i)] = staging[i];
+  }
+  for (int i = 0; i < grads->count; ++i) {
+    const Shape& sh = shp[static_cast<size_t>(i)];
+    IFNSO_CUDA(launch_muon_momentum(grads->in[i], sh.ld, static_cast<float*>(momentum[i]), staging[i], sh.rows,
+                                    sh.cols, static_cast<float>(beta), nesterov, stream),
+               "momentum");
+  }
+  // the orthogonalization of U, whose product writes W - lr s Y into the weights
+  ifnso_batch_desc ub = *grads;
+  ub.in = u_in.data();
+  return orthogonalize_locked(plan, &ub, coeffs, weights, workspace, workspace_bytes, stream, true,
+                              static_cast<float>(lr));
 }
 
 ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch, const ifnso_coeffs* coeffs,

@@ -25,6 +25,7 @@ enum EpiKind : int {
   EPI_NS_APPLY = 5,  // X <- a X + (B X  or  b S X)
   EPI_GRAM_F8 = 6,   // T_0 from E4M3 copies of A (kind::f8f6f4), rescaled; else as EPI_GRAM
   EPI_SQR_FOLD = 7,  // EPI_SQR with -2 D_l folded into the MMAs (chosen by TcParams::fold_d)
+  EPI_APPLY_UPDATE = 8,  // EPI_APPLY whose result updates the weights: W -= lr s Y (TcParams::update)
 };
 
 // Per-matrix scalars kept in the workspace (64 bytes).
@@ -133,6 +134,9 @@ struct TcParams {
   int32_t fold_d;      // EPI_SQR: the MMAs also add -2 D_l (an identity product), so the
                        // accumulator holds D_l^2 - 2 D_l = -D_{l+1} and the epilogue
                        // does not read D_l (passes whose P update has no D_l term)
+  int32_t update;      // EPI_APPLY: out0 holds the weights W (M's shape, also read through
+                       // aux0): W <- W - lr sqrt(max(1, rows / cols)) Y instead of Y
+  float lr;            // the step size of that update
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;
@@ -202,6 +206,11 @@ struct SgParams {
 };
 
 cudaError_t sg_launch(int epi, const SgParams& p, int count, int max_m, int max_n, cudaStream_t s);
+
+// Muon momentum of one matrix (rows x cols): M <- beta M + G (FP32, contiguous),
+// U <- G + beta M (nesterov) or M, rounded to BF16 (leading dimension ldg, as G).
+cudaError_t launch_muon_momentum(const void* g, int64_t ldg, float* m, void* u, int64_t rows, int64_t cols,
+                                 float beta, int nesterov, cudaStream_t s);
 
 cudaError_t launch_learn(int L, int iters, int samples, double lr, int step_size, double gamma,
                          uint32_t seed, double cL, double* d_w, cudaStream_t s);

@@ -1,7 +1,10 @@
 // SIMT kernels of the IFNSO library: the split-K Frobenius norm, the
 // per-matrix scalars (o, 1/sqrt(o), the D-basis identity weight in FP64),
 // the elementwise initialisation D_1 = T_0/o, P = (1 + sum w) I - w_1 D_1,
-// and the FP32 GEMM that carries every product of FP32 plans.
+// the FP32 GEMM that carries every product of FP32 plans, and the momentum
+// step of a Muon update around the orthogonalization.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -379,7 +382,60 @@ __global__ void __launch_bounds__(256) k_sgemm(const SgParams p) {
   }
 }
 
+// Muon's momentum step for one matrix, 8 consecutive elements of a row per
+// thread (cols and ldg multiples of 8 are not required: the row tail goes
+// element by element).  M <- beta M + G; U <- G + beta M (nesterov) or M.
+__global__ void __launch_bounds__(256) k_muon_momentum(const __nv_bfloat16* __restrict__ g, int64_t ldg,
+                                                      float* __restrict__ m, __nv_bfloat16* __restrict__ u,
+                                                      int64_t rows, int64_t cols, float beta, int nesterov) {
+  const int64_t row8 = (cols + 7) / 8;
+  for (int64_t e8 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e8 < rows * row8;
+       e8 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e8 / row8, j0 = (e8 - i * row8) * 8;
+    const __nv_bfloat16* gr = g + i * ldg + j0;
+    float* mr = m + i * cols + j0;
+    __nv_bfloat16* ur = u + i * ldg + j0;
+    if (j0 + 8 <= cols && (ldg & 7) == 0 && (cols & 3) == 0) {
+      const uint4 gv = *reinterpret_cast<const uint4*>(gr);
+      const __nv_bfloat162* g2 = reinterpret_cast<const __nv_bfloat162*>(&gv);
+      float4 m0 = reinterpret_cast<const float4*>(mr)[0], m1 = reinterpret_cast<const float4*>(mr)[1];
+      float mv[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+      uint4 uv;
+      __nv_bfloat162* u2 = reinterpret_cast<__nv_bfloat162*>(&uv);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float2 gf = __bfloat1622float2(g2[t]);
+        mv[2 * t] = fmaf(beta, mv[2 * t], gf.x);
+        mv[2 * t + 1] = fmaf(beta, mv[2 * t + 1], gf.y);
+        const float a = nesterov ? fmaf(beta, mv[2 * t], gf.x) : mv[2 * t];
+        const float b = nesterov ? fmaf(beta, mv[2 * t + 1], gf.y) : mv[2 * t + 1];
+        u2[t] = __floats2bfloat162_rn(a, b);
+      }
+      reinterpret_cast<float4*>(mr)[0] = make_float4(mv[0], mv[1], mv[2], mv[3]);
+      reinterpret_cast<float4*>(mr)[1] = make_float4(mv[4], mv[5], mv[6], mv[7]);
+      *reinterpret_cast<uint4*>(ur) = uv;
+    } else {
+      for (int64_t j = 0; j < 8 && j0 + j < cols; ++j) {
+        const float gf = __bfloat162float(gr[j]);
+        const float mv = fmaf(beta, mr[j], gf);
+        mr[j] = mv;
+        ur[j] = __float2bfloat16_rn(nesterov ? fmaf(beta, mv, gf) : mv);
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_muon_momentum(const void* g, int64_t ldg, float* m, void* u, int64_t rows, int64_t cols,
+                                 float beta, int nesterov, cudaStream_t s) {
+  const int64_t n8 = rows * ((cols + 7) / 8);
+  const int grid = static_cast<int>(std::min<int64_t>((n8 + 255) / 256, 4096));
+  k_muon_momentum<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(g), ldg, m, static_cast<__nv_bfloat16*>(u),
+                                       rows, cols, beta, nesterov);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,
                          int64_t out_stride, int grid_x, cudaStream_t s) {

@@ -366,7 +366,8 @@ __device__ __forceinline__ void epilogue_load(const TcParams& p, const TcProblem
   } else if constexpr (EPI == EPI_NS_SQR) {
     blk_load<__nv_bfloat16>(in.a, static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r0) * pr.ld_aux + c0,
                             pr.ld_aux);
-  } else if constexpr (EPI == EPI_NS_APPLY) {
+  } else if constexpr (EPI == EPI_NS_APPLY || EPI == EPI_APPLY_UPDATE) {
+    // X (NS) or the weights W (update): M's layout, read where the result goes
     const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(pr.aux0);
     const bool vec = (pr.ld_aux & 7) == 0;
     if (!pr.out_trans)
@@ -519,6 +520,19 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     const float ka = p.ns_a * sc, kb = p.ns_bcoef * sc;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(ka, x[j], kb * v[j]);
+    store_out_bf16(pr, r0, c0, v, st);
+  } else if constexpr (EPI == EPI_APPLY_UPDATE) {
+    // W <- W - lr s Y with Y = Y' A / sqrt(o) and Muon's shape factor
+    // s = sqrt(max(1, rows / cols)) of the weight matrix (M's shape)
+    float x[32];
+    if (!pr.out_trans)
+      blk_unpack<__nv_bfloat16, false>(in.a, st, x);
+    else
+      blk_unpack<__nv_bfloat16, true>(in.a, st, x);
+    const float shape = sqrtf(fmaxf(1.f, static_cast<float>(pr.rows_out) / static_cast<float>(pr.cols_out)));
+    const float kb = -p.lr * shape * p.scal[pr.mat].inv_s;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = fmaf(kb, v[j], x[j]);
     store_out_bf16(pr, r0, c0, v, st);
   }
 }
@@ -946,6 +960,10 @@ cudaError_t dispatch(int epi, int na, const TcParams& p, int max_clusters, cudaS
       if (na == 2) return launch_one<2, 2, EPI_SQR, CG>(p, max_clusters, s);
       return launch_one<1, 1, EPI_SQR, CG>(p, max_clusters, s);
     case EPI_APPLY:
+      if (p.update) {
+        if (na == 2) return launch_one<2, 1, EPI_APPLY_UPDATE, CG>(p, max_clusters, s);
+        return launch_one<1, 1, EPI_APPLY_UPDATE, CG>(p, max_clusters, s);
+      }
       if (na == 2) return launch_one<2, 1, EPI_APPLY, CG>(p, max_clusters, s);
       return launch_one<1, 1, EPI_APPLY, CG>(p, max_clusters, s);
     case EPI_NS_GRAM:

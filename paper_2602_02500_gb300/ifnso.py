@@ -46,7 +46,8 @@ IFNSO_STATIC_NORM_MAX_MATRICES = 1024
 
 EXPORTED = [
     "ifnso_plan_create", "ifnso_plan_set", "ifnso_plan_get", "ifnso_plan_destroy",
-    "ifnso_workspace_bytes", "ifnso_orthogonalize", "ifnso_orthogonalize_host", "ifnso_plan_autotune", "ns_iterate",
+    "ifnso_workspace_bytes", "ifnso_orthogonalize", "ifnso_orthogonalize_host", "ifnso_plan_autotune",
+    "ifnso_muon_step", "ns_iterate",
     "ns_workspace_bytes",
     "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
     "ifnso_frobenius_norm2_static", "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
@@ -79,6 +80,8 @@ _sig = {
                                       C.c_size_t, C.c_int32, C.POINTER(C.c_int32), _P]),
     "ifnso_orthogonalize_host": (C.c_int, [_P, C.POINTER(_P), C.POINTER(ifnso_batch_desc), C.POINTER(ifnso_coeffs),
                                            C.POINTER(_P), C.POINTER(_P), _P, C.c_size_t, C.c_int32, _P]),
+    "ifnso_muon_step": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
+                                  C.POINTER(ifnso_coeffs), C.c_double, C.c_int32, C.c_double, _P, C.c_size_t, _P]),
     "ns_iterate": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), C.POINTER(C.c_double), C.c_int32, C.c_int32,
                              C.POINTER(_P), _P, C.c_size_t, _P]),
     "ifnso_device_status": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
@@ -271,6 +274,25 @@ class Plan:
                                   ws.nbytes, _stream(stream)), "ifnso_orthogonalize")
         self._last_ws = ws
         return outs
+
+    def muon_step(self, grads, momentum, staging, weights, coeffs, beta=0.95, nesterov=True, lr=0.02, ws=None,
+                  stream=None):
+        """One Muon step (ifnso_muon_step): momentum (FP32), staging (BF16,
+        the orthogonalized input U) and weights (BF16) are lists of tensors
+        matching `grads` (Batch of BF16 gradients); W <- W - lr s orth(U)."""
+        cf = self._coeffs(grads, coeffs)
+        need = self.workspace_bytes(grads)
+        if ws is None:
+            ws = self.workspace(need)
+
+        def ptrs(ts):
+            return (C.c_void_p * max(len(ts), 1))(*[t.data_ptr() for t in ts])
+
+        check(ifnso_muon_step(self.handle, grads.ref(), ptrs(momentum), ptrs(staging), ptrs(weights), C.byref(cf),
+                              float(beta), 1 if nesterov else 0, float(lr), C.c_void_p(ws.ptr), ws.nbytes,
+                              _stream(stream)), "ifnso_muon_step")
+        self._last_ws = ws
+        return weights
 
     def autotune(self, batch, coeffs, outs, reps=3, ws=None, stream=None):
         """Time per-CTA and CTA-pair MMAs on this batch and keep the faster per

@@ -142,6 +142,38 @@ def test_host_entry_argument_checks(F):
     F.ifnso_plan_destroy(p)
 
 
+def test_muon_step_argument_checks(F):
+    # every argument error is reported before any device work
+    st, p = _plan(F, 256, 512, 4)
+    w = (C.c_double * 5)(1.0, 0.1, 0.2, 0.3, 0.4)
+    cf = F.ifnso_coeffs(5, w, None, None)
+    g = (C.c_void_p * 1)(16 * 1024)
+    rows = (C.c_int64 * 1)(256)
+    cols = (C.c_int64 * 1)(512)
+    desc = F.ifnso_batch_desc(1, g, rows, cols, None)
+    m = (C.c_void_p * 1)(32 * 1024)
+    u = (C.c_void_p * 1)(48 * 1024)
+    wt = (C.c_void_p * 1)(64 * 1024)
+    bad = F.IFNSO_ERR_INVALID_ARG
+
+    def call(plan=p, mom=m, stg=u, wts=wt, beta=0.95, nesterov=1, lr=0.02):
+        return F.ifnso_muon_step(plan, C.byref(desc), mom, stg, wts, C.byref(cf), beta, nesterov, lr, None, 0, None)
+
+    assert call(plan=None) == bad
+    assert call(mom=None) == bad and call(stg=None) == bad and call(wts=None) == bad
+    assert call(beta=1.0) == bad and call(beta=-0.1) == bad and call(beta=float("nan")) == bad
+    assert call(lr=-1.0) == bad and call(lr=float("inf")) == bad
+    assert call(nesterov=2) == bad
+    assert call(wts=(C.c_void_p * 1)(48 * 1024)) == bad        # weights alias the staging buffer
+    assert call(stg=(C.c_void_p * 1)(16 * 1024)) == bad        # staging aliases the gradient
+    assert call(mom=(C.c_void_p * 1)(64 * 1024 + 8)) == bad    # misaligned momentum
+    assert call(mom=(C.c_void_p * 1)(None)) == bad
+    F.ifnso_plan_destroy(p)
+    st, p = _plan(F, 256, 512, 4, dtype=0)  # F32 plans have no Muon step
+    assert call(plan=p) == F.IFNSO_ERR_UNSUPPORTED
+    F.ifnso_plan_destroy(p)
+
+
 def test_gram_e4m3_option(F):
     st, p = _plan(F, 256, 512, 4)
     v = C.c_int64()
