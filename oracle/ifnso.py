@@ -33,11 +33,16 @@ def scale_of(A, scale: str = "gram"):
     "gram": ||A A^T||_F^(1/2), Gelfand's bound with q = 1 (Eq. new_scale_formula,
             Sec. 2), which Algorithm 1 uses through o = ||T_0||_F.
     "frob": ||A||_F, the classical Newton-Schulz scaling (Eq. constraint, Sec. 1).
+    "gelfand2": ||(A A^T)^2||_F^(1/4), the bound of Eq. gelfand_formula with q = 2
+            (the scaling of Eq. scale_formula_function before the paper sets q = 1).
     """
     if scale == "gram":
         return np.sqrt(np.linalg.norm(A @ A.T, "fro"))
     if scale == "frob":
         return np.linalg.norm(A, "fro")
+    if scale == "gelfand2":
+        G = A @ A.T
+        return np.linalg.norm(G @ G, "fro") ** 0.25
     raise ValueError(scale)
 
 
@@ -47,7 +52,8 @@ def ifnso_alg1(M, w, scale: str = "gram"):
     T_0 = A A^T, o = ||T_0||_F, T_1 = I - T_0/o, T_l = T_{l-1} T_{l-1} (l = 2..L),
     Y' = I + sum_l w_l T_l, Y = Y' A / sqrt(o)  (Sec. 2.4, T_l definition,
     aggregation and Algorithm 1).  ``w`` holds w_1..w_L.  With scale="frob" the
-    divisor sqrt(o) is replaced by ||A||_F (so T_1 = I - A A^T/||A||_F^2).
+    divisor sqrt(o) is replaced by ||A||_F (so T_1 = I - A A^T/||A||_F^2); with
+    scale="gelfand2" by ||T_0^2||_F^(1/4) (o = ||T_0^2||_F^(1/2)).
     The output has the shape of M.  A zero input returns zeros.
     """
     A, tr = orient(M)
@@ -55,11 +61,7 @@ def ifnso_alg1(M, w, scale: str = "gram"):
     L = len(w)
     h = A.shape[0]
     T0 = A @ A.T
-    if scale == "gram":
-        o = np.linalg.norm(T0, "fro")
-        s2 = o
-    else:
-        s2 = np.linalg.norm(A, "fro") ** 2
+    s2 = scale_of(A, scale) ** 2
     if s2 == 0.0:
         return np.zeros_like(np.asarray(M, dtype=np.float64))
     I = np.eye(h)
@@ -84,7 +86,7 @@ def ifnso_dbasis(M, w, scale: str = "gram"):
     L = len(w)
     h = A.shape[0]
     G = A @ A.T
-    s2 = np.linalg.norm(G, "fro") if scale == "gram" else np.linalg.norm(A, "fro") ** 2
+    s2 = scale_of(A, scale) ** 2
     if s2 == 0.0:
         return np.zeros_like(np.asarray(M, dtype=np.float64))
     D = G / s2
@@ -162,6 +164,9 @@ def brute_force(M, w, exps=None, scale: str = "gram", dps: int = 50):
         G = Am * Am.T
         if scale == "gram":
             s2 = mp.sqrt(sum(G[i, j] ** 2 for i in range(h) for j in range(h)))
+        elif scale == "gelfand2":
+            G2 = G * G
+            s2 = mp.sqrt(mp.sqrt(sum(G2[i, j] ** 2 for i in range(h) for j in range(h))))
         else:
             s2 = sum(Am[i, j] ** 2 for i in range(h) for j in range(wd))
         X = Am / mp.sqrt(s2)

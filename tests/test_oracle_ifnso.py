@@ -19,7 +19,7 @@ def _paths(M, w, scale="gram"):
 
 
 @pytest.mark.parametrize("shape", [(12, 30), (30, 12), (17, 17), (1, 9), (9, 1)])
-@pytest.mark.parametrize("scale", ["gram", "frob"])
+@pytest.mark.parametrize("scale", ["gram", "frob", "gelfand2"])
 def test_three_paths_agree(shape, scale):
     # P1: Algorithm 1 (T basis), the D basis and the SVD evaluation of f agree (Sec. 2.1, 2.4)
     M = gaussian(3, *shape)
@@ -45,7 +45,7 @@ def test_rank_one_returns_uv():
     v = rng.standard_normal(19)
     v /= np.linalg.norm(v)
     M = 3.7 * np.outer(u, v)
-    for scale in ("gram", "frob"):
+    for scale in ("gram", "frob", "gelfand2"):
         Y = I.ifnso_alg1(M, W6, scale)
         assert np.allclose(Y, np.outer(u, v), atol=1e-12)
 
@@ -63,6 +63,9 @@ def test_orthonormal_rows_closed_form(h, w):
     xf = hh ** -0.5
     assert np.allclose(Yg, C.f_full(xg, W4) * M, atol=1e-12)
     assert np.allclose(Yf, C.f_full(xf, W4) * M, atol=1e-12)
+    # Gelfand q = 2: (Q Q^T)^2 = I, ||I||_F^(1/4) = h^(1/8), x = h^(-1/8)
+    Y2 = I.ifnso_alg1(M, W4, "gelfand2")
+    assert np.allclose(Y2, C.f_full(hh ** -0.125, W4) * M, atol=1e-12)
 
 
 def test_single_row_is_normalised():
@@ -81,12 +84,26 @@ def test_brute_force_mpmath(M):
     pytest.importorskip("mpmath")
     if M is None:
         M = gaussian(11, 4, 8)
-    for scale in ("gram", "frob"):
+    for scale in ("gram", "frob", "gelfand2"):
         ref = I.brute_force(M, W4, scale=scale)
         assert I.rel_fro(I.ifnso_alg1(M, W4, scale), ref) < 1e-12
         assert I.rel_fro(I.ifnso_dbasis(M, W4, scale), ref) < 1e-12
         ref_t = I.brute_force(M.T, W4, scale=scale)
         assert I.rel_fro(I.ifnso_alg1(M.T, W4, scale), ref_t) < 1e-12
+
+
+def test_gelfand_bounds():
+    # Eq. gelfand_formula: sigma_1 <= ||(A A^T)^q||_F^(1/(2q)), and the bound
+    # tightens from q = 1 to q = 2; h equal singular values s give s h^(1/(4q))
+    for seed, shape in [(1, (8, 20)), (2, (15, 15)), (3, (30, 6))]:
+        A = I.orient(gaussian(seed, *shape))[0]
+        s1 = np.linalg.svd(A, compute_uv=False)[0]
+        g1, g2 = I.scale_of(A, "gram"), I.scale_of(A, "gelfand2")
+        assert s1 <= g2 * (1 + 1e-14) and g2 <= g1 * (1 + 1e-14)
+    rng = np.random.default_rng(4)
+    Q = haar_stiefel(rng, 12, 5).T
+    for q, name in [(1, "gram"), (2, "gelfand2")]:
+        assert np.isclose(I.scale_of(2.5 * Q, name), 2.5 * 5 ** (1 / (4 * q)), rtol=1e-14)
 
 
 def test_orientation_and_transpose():
