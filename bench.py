@@ -34,12 +34,12 @@ WORKLOADS = {
     "muon_1b": {
         "desc": "synthetic 1B transformer weight-gradient list: 24 layers x {Q,K,V,O 2048x2048; gate, up "
                 "2048x5632; down 5632x2048}, 168 BF16 rank-32 + noise (10:1) matrices, seeds 0..167",
-        "list": "list_1b", "L": 14,
+        "list": "list_1b", "L": 14, "L_gelfand2": 13,
     },
     "muon_1b_4l": {
         "desc": "first 4 layers of the synthetic 1B list (28 BF16 matrices, 412 MB of input > L2): the "
                 "small case used for ncu captures",
-        "list": "list_1b_4l", "L": 14,
+        "list": "list_1b_4l", "L": 14, "L_gelfand2": 13,
     },
     "muon_7b": {
         "desc": "synthetic 7B transformer weight-gradient list: 32 layers x {4 x 4096x4096; gate, up "
@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="muon_1b", choices=sorted(WORKLOADS))
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
+    ap.add_argument("--scale", default="gram", choices=["gram", "frob", "gelfand2"],
+                    help="input scaling: Gram (q = 1, the paper's), Frobenius, or Gelfand's bound with q = 2")
     ap.add_argument("--cta-group", type=int, default=0, choices=[0, 1, 2],
                     help="tensor-core passes: MMAs of the CTA pair (2), per-CTA MMAs with B multicast (1), "
                          "or the library's choice per pass (0)")
@@ -564,7 +566,8 @@ def main():
 
     wl = WORKLOADS[args.workload]
     shapes = workload_list(wl)
-    L = args.L or wl["L"]
+    # the equal-polar-error depth of the scaling (tests/golden/equal_polar.json)
+    L = args.L or (wl.get("L_gelfand2", wl["L"]) if args.scale == "gelfand2" else wl["L"])
     n = len(shapes)
     hw = [oriented(r, c) for _, r, c in shapes]
     hmax = max(h for h, _ in hw)
@@ -602,7 +605,7 @@ def main():
         mlp_info = {"train_spectra": n_train, "steps": args.mlp_steps, "batch": 512,
                     "loss_first_50": float(np.mean(curve[:50])), "loss_last_50": float(np.mean(curve[-50:]))}
 
-    plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision)
+    plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision, scale=args.scale)
     plan.set(F.IFNSO_OPT_TIMING, 1)
     plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
     plan.set(F.IFNSO_OPT_GRAM_E4M3, 1 if args.gram_e4m3 else 0)
@@ -792,7 +795,10 @@ def main():
                                         "fixed, learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 "
                                         "schedule)"),
                        "coefficient_network": mlp_info,
-                       "gram": "E4M3 copy of A s, FP32 accumulation (experiment)" if args.gram_e4m3 else "BF16"},
+                       "gram": "E4M3 copy of A s, FP32 accumulation (experiment)" if args.gram_e4m3 else "BF16",
+                       "scale": {"gram": "X = A / ||A A^T||_F^(1/2) (q = 1, the paper's)",
+                                 "frob": "X = A / ||A||_F",
+                                 "gelfand2": "X = A / ||(A A^T)^2||_F^(1/4) (Gelfand, q = 2)"}[args.scale]},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
                     "ifnso_over_ns5": value / ns_value},

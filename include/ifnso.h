@@ -57,7 +57,12 @@ typedef enum {
   IFNSO_OPT_PRECISION = 1,
   /* Input scaling.  IFNSO_SCALE_GRAM (default): X = A / ||A A^T||_F^(1/2)
    * (Eq. new_scale_formula, Sec. 2; o = ||T_0||_F in Algorithm 1).
-   * IFNSO_SCALE_FROB: X = A / ||A||_F (Eq. constraint, Sec. 1). */
+   * IFNSO_SCALE_FROB: X = A / ||A||_F (Eq. constraint, Sec. 1).
+   * IFNSO_SCALE_GELFAND2: X = A / ||(A A^T)^2||_F^(1/4), Gelfand's bound with
+   * q = 2 (Eq. gelfand_formula, Eq. scale_formula_function), closer to the
+   * largest singular value than q = 1; costs one extra product of D_1 with
+   * itself (nothing stored) and a second prep.  Not with proposed
+   * coefficients (IFNSO_ERR_UNSUPPORTED). */
   IFNSO_OPT_SCALE = 2,
   /* Upper bound on the CTAs of each persistent launch (0 = one per SM). */
   IFNSO_OPT_MAX_CTAS = 3,
@@ -104,7 +109,7 @@ typedef enum {
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };
-enum { IFNSO_SCALE_GRAM = 0, IFNSO_SCALE_FROB = 1 };
+enum { IFNSO_SCALE_GRAM = 0, IFNSO_SCALE_FROB = 1, IFNSO_SCALE_GELFAND2 = 2 };
 
 /* Per-matrix device status bits (ifnso_device_status). */
 enum {

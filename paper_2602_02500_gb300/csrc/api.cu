@@ -974,6 +974,8 @@ ifnso_status check_call(const ifnso_plan* plan, const ifnso_batch_desc* batch, c
     if (coeffs->mlp->K != coeffs->K) return fail(IFNSO_ERR_INVALID_ARG, "coefficient network has K = %d", coeffs->mlp->K);
     if (plan->L < 3) return fail(IFNSO_ERR_INVALID_ARG, "proposed coefficients need L >= 3");
     if (plan->dtype != IFNSO_BF16) return fail(IFNSO_ERR_UNSUPPORTED, "proposed coefficients need a BF16 plan");
+    if (plan->scale == IFNSO_SCALE_GELFAND2)
+      return fail(IFNSO_ERR_UNSUPPORTED, "proposed coefficients are trained on features under Gram scaling");
   }
   if (!out) return fail(IFNSO_ERR_INVALID_ARG, "out is NULL");
   for (int i = 0; i < batch->count; ++i) {
@@ -1069,6 +1071,14 @@ ifnso_status run_f32(const Run& r) {
   IFNSO_CUDA(launch_scalars(d_mats, n, p.scal, p.coef, L, frob, 0, stream), "scalars");
   IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 0) return IFNSO_OK;
+  if (plan->scale == IFNSO_SCALE_GELFAND2) {
+    // Gelfand's bound with q = 2: D_1 under o = ||T_0||_F (T_0 kept), the
+    // FP64 sum of (D_1^2)_ij^2, and o rescaled to ||T_0^2||_F^(1/2)
+    IFNSO_CUDA(launch_prep(d_mats, n, r.hpad_max, p.scal, p.coef, L, 0, 1, stream, 1), "Gelfand prep");
+    p.probs = probs + ly.pi_sqr;
+    IFNSO_CUDA(sg_launch(EPI_SQR_NORM, p, n, r.hpad_max, r.hpad_max, stream), "Gelfand norm pass");
+    IFNSO_CUDA(launch_gelfand(n, p.scal, stream), "Gelfand scale");
+  }
   IFNSO_CUDA(launch_prep(d_mats, n, r.hpad_max, p.scal, p.coef, L, 0, 1, stream), "prep");
   IFNSO_CUDA(mark(plan, stream, false), "timing event");
   if (plan->stop_after == 1) return IFNSO_OK;
@@ -1152,6 +1162,16 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   }
   IFNSO_CUDA(mark_pass(false), "timing event");
   if (stop(0)) return IFNSO_OK;
+  if (plan->scale == IFNSO_SCALE_GELFAND2) {
+    // Gelfand's bound with q = 2: D_1 under o = ||T_0||_F (FP16 hi), then
+    // ||D_1^2||_F^2 from one product of it with itself (nothing stored), and
+    // o rescaled to ||T_0^2||_F^(1/2); the prep below then divides T_0 by that
+    IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, 0, 0, stream, 1), "Gelfand prep");
+    p.probs = probs + ly.pi_sqr;  // squaring 1 reads D buffer 0
+    p.cta_group = cta_group(kPlain);
+    IFNSO_CUDA(tc_launch(EPI_SQR_NORM, 1, 1, p, grid_for(plan, n_sym), stream), "Gelfand norm pass");
+    IFNSO_CUDA(launch_gelfand(count, scal, stream), "Gelfand scale");
+  }
   // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo)
   const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
   IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream), "prep");
@@ -1304,7 +1324,7 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       plan->precision = static_cast<int>(value);
       break;
     case IFNSO_OPT_SCALE:
-      if (value < 0 || value > 1) return fail(IFNSO_ERR_INVALID_ARG, "scale %lld", (long long)value);
+      if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "scale %lld", (long long)value);
       plan->scale = static_cast<int>(value);
       break;
     case IFNSO_OPT_MAX_CTAS:

@@ -26,6 +26,7 @@ enum EpiKind : int {
   EPI_GRAM_F8 = 6,   // T_0 from E4M3 copies of A (kind::f8f6f4), rescaled; else as EPI_GRAM
   EPI_SQR_FOLD = 7,  // EPI_SQR with -2 D_l folded into the MMAs (chosen by TcParams::fold_d)
   EPI_APPLY_UPDATE = 8,  // EPI_APPLY whose result updates the weights: W -= lr s Y (TcParams::update)
+  EPI_SQR_NORM = 9,      // ||D_1^2||_F^2 into MatScalars::spare[0], nothing stored (Gelfand q = 2)
 };
 
 // Per-matrix scalars kept in the workspace (64 bytes).
@@ -170,8 +171,12 @@ cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out
                          int64_t out_stride, int grid_x, cudaStream_t s);
 cudaError_t launch_scalars(const MatInfo* d_mats, int count, MatScalars* scal, CoefTable coef,
                            int L, int scale_frob, int from_norm2, cudaStream_t s);
+// d_only: write D_1 only (no P, T_0 kept), for the norm pass of Gelfand scaling.
 cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
-                        CoefTable coef, int L, int split, int f32, cudaStream_t s);
+                        CoefTable coef, int L, int split, int f32, cudaStream_t s, int d_only = 0);
+// Gelfand scaling with q = 2: from o = ||T_0||_F and spare[0] = ||(T_0/o)^2||_F^2,
+// o <- ||T_0^2||_F^(1/2) = o spare[0]^(1/4), with 1/o and 1/sqrt(o) to match.
+cudaError_t launch_gelfand(int count, MatScalars* scal, cudaStream_t s);
 // E4M3 Gram: max |A_ij| into MatScalars::amax, then the scaled E4M3 copy of
 // A (M or M^T, K-major) into MatInfo::a8.
 cudaError_t launch_amax(const MatInfo* d_mats, int count, MatScalars* scal, int grid_x, cudaStream_t s);

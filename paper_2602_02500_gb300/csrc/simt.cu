@@ -215,6 +215,23 @@ __global__ void k_scalars(int count, MatScalars* scal, CoefTable coef, int L, in
   s.status = st;
 }
 
+// Gelfand's bound with q = 2 (Eq. gelfand_formula): the scalars of Gram
+// scaling hold o = ||T_0||_F, and the norm pass summed ||(T_0/o)^2||_F^2 into
+// spare[0]; o <- ||T_0^2||_F^(1/2) = o spare[0]^(1/4), in FP64.  Zero,
+// non-finite and flagged matrices keep their scalars.
+__global__ void k_gelfand(int count, MatScalars* scal) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  MatScalars& s = scal[m];
+  const double q = s.spare[0];
+  s.spare[0] = 0.0;
+  if (s.status != 0 || !(s.s2 > 0.0) || !(q > 0.0) || !isfinite(q)) return;
+  const double s2 = s.s2 * sqrt(sqrt(q));
+  s.s2 = s2;
+  s.inv_s2 = static_cast<float>(1.0 / s2);
+  s.inv_s = static_cast<float>(1.0 / sqrt(s2));
+}
+
 // ---------------------------------------------------------------- prep
 // Elementwise over the h_pad x h_pad buffers of every matrix:
 //   d = T_0 * (1/s2)                       (D_1 = T_0 / o, the scaled Gram)
@@ -224,7 +241,7 @@ __global__ void k_scalars(int count, MatScalars* scal, CoefTable coef, int L, in
 // is no squaring: P itself is written as BF16 (hi, lo) into D buffer 0.
 // FP32 plans store D_1 in FP32 in D buffer 0 and P in place of T_0.
 __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* scal, CoefTable coef,
-                                              int L, int split, int f32) {
+                                              int L, int split, int f32, int d_only) {
   const int m = blockIdx.y;
   const MatInfo& mi = mats[m];
   const int64_t hp = mi.hpad;
@@ -256,9 +273,11 @@ __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* s
       float4* dd = reinterpret_cast<float4*>(static_cast<float*>(mi.d[0]) + e);
       dd[0] = make_float4(d[0], d[1], d[2], d[3]);
       dd[1] = make_float4(d[4], d[5], d[6], d[7]);
-      reinterpret_cast<float4*>(gp + e)[0] = make_float4(p[0], p[1], p[2], p[3]);
-      reinterpret_cast<float4*>(gp + e)[1] = make_float4(p[4], p[5], p[6], p[7]);
-    } else if (L == 1) {
+      if (!d_only) {
+        reinterpret_cast<float4*>(gp + e)[0] = make_float4(p[0], p[1], p[2], p[3]);
+        reinterpret_cast<float4*>(gp + e)[1] = make_float4(p[4], p[5], p[6], p[7]);
+      }
+    } else if (L == 1 && !d_only) {
       uint4 uh, ul;
       __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&uh);
       __nv_bfloat162* l2 = reinterpret_cast<__nv_bfloat162*>(&ul);
@@ -333,6 +352,7 @@ __global__ void __launch_bounds__(256) k_sgemm(const SgParams p) {
     __syncthreads();
   }
   float ss = 0.f, tr = 0.f;
+  double nn = 0.0;
   const int m = pr.mat;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -345,6 +365,9 @@ __global__ void __launch_bounds__(256) k_sgemm(const SgParams p) {
         pr.pacc[i * pr.ld_aux + j] = v;
         ss = fmaf(v, v, ss);
         if (i == j) tr += v;
+      } else if constexpr (EPI == EPI_SQR_NORM) {
+        // (D_1^2)_ij with D_1 = T_0 / o; the squares are summed in FP64 below
+        nn = fma(static_cast<double>(v), static_cast<double>(v), nn);
       } else if constexpr (EPI == EPI_SQR) {
         const int64_t o = i * pr.ld_aux + j;
         const float dn = 2.0f * pr.aux0[o] - v;
@@ -371,6 +394,11 @@ __global__ void __launch_bounds__(256) k_sgemm(const SgParams p) {
         pr.out0[i * pr.ld_out + j] = fmaf(p.ns_c, v, p.ns_b * sv);
       }
     }
+  }
+  if constexpr (EPI == EPI_SQR_NORM) {
+    // per-block FP64 sum of the squares (FP32 partials would lose digits here)
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&p.scal[m].spare[0], nn);
   }
   if constexpr (EPI == EPI_GRAM) {
     const float s = block_sum(ss, red);
@@ -455,13 +483,20 @@ cudaError_t launch_scalars(const MatInfo*, int count, MatScalars* scal, CoefTabl
 }
 
 cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
-                        CoefTable coef, int L, int split, int f32, cudaStream_t s) {
+                        CoefTable coef, int L, int split, int f32, cudaStream_t s, int d_only) {
   if (count == 0) return cudaSuccess;
   const int64_t n = static_cast<int64_t>(hpad_max) * hpad_max;
   int gx = static_cast<int>((n + 256 * 8 - 1) / (256 * 8));
   if (gx > 4096) gx = 4096;
   dim3 grid(gx, count);
-  k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32);
+  k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32, d_only);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gelfand(int count, MatScalars* scal, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_gelfand<<<(count + 127) / 128, 128, 0, s>>>(count, scal);
   count_launch();
   return cudaGetLastError();
 }
@@ -488,6 +523,7 @@ cudaError_t sg_launch(int epi, const SgParams& p, int count, int max_m, int max_
     case EPI_GRAM: k_sgemm<EPI_GRAM><<<grid, 256, 0, s>>>(p); break;
     case EPI_SQR: k_sgemm<EPI_SQR><<<grid, 256, 0, s>>>(p); break;
     case EPI_APPLY: k_sgemm<EPI_APPLY><<<grid, 256, 0, s>>>(p); break;
+    case EPI_SQR_NORM: k_sgemm<EPI_SQR_NORM><<<grid, 256, 0, s>>>(p); break;
     case EPI_NS_GRAM: k_sgemm<EPI_NS_GRAM><<<grid, 256, 0, s>>>(p); break;
     case EPI_NS_SQR: k_sgemm<EPI_NS_SQR><<<grid, 256, 0, s>>>(p); break;
     case EPI_NS_APPLY: k_sgemm<EPI_NS_APPLY><<<grid, 256, 0, s>>>(p); break;

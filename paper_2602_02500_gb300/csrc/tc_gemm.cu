@@ -409,6 +409,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       if (c0 + j == r) ea.tr += v[j];
     }
     store_blk<float, true>(pr.pacc, pr.ld_aux, r0, c0, v, st);
+  } else if constexpr (EPI == EPI_SQR_NORM) {
+    // ||D_1^2||_F^2 only: the tile's squares are summed, nothing is stored
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ea.ss = fmaf(v[j], v[j], ea.ss);
   } else if constexpr (EPI == EPI_SQR || EPI == EPI_SQR_FOLD) {
     float d[32], lo[32];
     if constexpr (EPI == EPI_SQR) {
@@ -545,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   using PR = Products<NA, NB>;
   constexpr int S = C::stages;
   // D_l are FP16, the E4M3 Gram's operands E4M3 (format code 0 of its kind), all else BF16
-  constexpr bool kSqr = (EPI == EPI_SQR || EPI == EPI_SQR_FOLD);
+  constexpr bool kSqr = (EPI == EPI_SQR || EPI == EPI_SQR_FOLD || EPI == EPI_SQR_NORM);
   constexpr uint32_t kIsBf16 = (kSqr || EPI == EPI_GRAM_F8) ? 0u : 1u;
   constexpr bool kF8 = (EPI == EPI_GRAM_F8);
   constexpr int kBKe = kF8 ? 2 * BK : BK;  // elements per 128-byte K block
@@ -879,7 +883,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
       }
       if constexpr (kSqr) {
-        if (p.feat) {
+        if (p.feat || EPI == EPI_SQR_NORM) {
           const float ss = warp_reduce_sum(ea.ss);
           if (lane == 0)
             atomicAdd(&p.scal[pr.mat].spare[0], ((wi.flags & 1) ? 1.0 : 2.0) * static_cast<double>(ss));
@@ -959,6 +963,8 @@ cudaError_t dispatch(int epi, int na, const TcParams& p, int max_clusters, cudaS
       }
       if (na == 2) return launch_one<2, 2, EPI_SQR, CG>(p, max_clusters, s);
       return launch_one<1, 1, EPI_SQR, CG>(p, max_clusters, s);
+    case EPI_SQR_NORM:
+      return launch_one<1, 1, EPI_SQR_NORM, CG>(p, max_clusters, s);
     case EPI_APPLY:
       if (p.update) {
         if (na == 2) return launch_one<2, 1, EPI_APPLY_UPDATE, CG>(p, max_clusters, s);

@@ -40,7 +40,7 @@ IFNSO_OPT_INJECT_STALL = 7
 IFNSO_OPT_CTA_GROUP = 8
 IFNSO_OPT_GRAM_E4M3 = 9
 IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT, IFNSO_PREC_MIXED = 0, 1, 2, 3
-IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB = 0, 1
+IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB, IFNSO_SCALE_GELFAND2 = 0, 1, 2
 IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4
 IFNSO_STATIC_NORM_MAX_MATRICES = 1024
 
@@ -199,7 +199,7 @@ class Plan:
         if precision is not None:
             self.set(IFNSO_OPT_PRECISION, {"auto": 0, "plain": 1, "split": 2, "mixed": 3}.get(precision, precision))
         if scale is not None:
-            self.set(IFNSO_OPT_SCALE, {"gram": 0, "frob": 1}.get(scale, scale))
+            self.set(IFNSO_OPT_SCALE, {"gram": 0, "frob": 1, "gelfand2": 2}.get(scale, scale))
         if max_ctas is not None:
             self.set(IFNSO_OPT_MAX_CTAS, max_ctas)
         self._ws = None

@@ -1,6 +1,7 @@
 """Write tests/golden/equal_polar.json: distance to the polar factor U V^T (per sqrt(h)) of
 the 5-step quintic NS and of IFNSO at depths L = 4..20 on one low-rank-plus-noise matrix of each
-shape of the synthetic 1B list, by spectral evaluation in FP64 (oracle + synth only).
+shape of the synthetic 1B list, by spectral evaluation in FP64 (oracle + synth only), under the
+paper's scaling (q = 1) and under Gelfand's bound with q = 2.
 The smallest L whose distance is at or below NS5 is the depth the benchmark uses.
 
 Run:  python tests/golden/make_equal_polar.py
@@ -32,10 +33,14 @@ for name, r, c, seed in [("sq2048", 2048, 2048, 0), ("wide2048x5632", 2048, 5632
     o = np.sqrt(np.sum(s**4))
     x = s / np.sqrt(o)
     out["x_signal_min"] = float(x[31]); out["x_noise_max"] = float(x[32]); out["x_min"] = float(x[-1])
+    # Gelfand's bound with q = 2: x = s / ||T_0^2||_F^(1/4)
+    x2 = s / np.sum(s**8) ** 0.125
     for L in range(4, 21):
         w = np.array(art["L"][str(L)]["w"])
         y = O.f_scalar(x, w)
         out[f"ifnso_L{L}"] = float(np.sqrt(np.sum((y - 1)**2) / h))
+        y2 = O.f_scalar(x2, w)
+        out[f"ifnso_gelfand2_L{L}"] = float(np.sqrt(np.sum((y2 - 1)**2) / h))
     # NS5 spectral (Frobenius scaling)
     xf = s / np.sqrt(np.sum(s**2))
     out["ns5_spectral"] = float(np.sqrt(np.sum((ONS.ns_scalar(xf, ONS.MUON_ABC, 5) - 1)**2) / h))

@@ -142,6 +142,17 @@ def test_host_entry_argument_checks(F):
     F.ifnso_plan_destroy(p)
 
 
+def test_scale_option(F):
+    st, p = _plan(F, 256, 512, 4)
+    v = C.c_int64()
+    for val in (F.IFNSO_SCALE_GRAM, F.IFNSO_SCALE_FROB, F.IFNSO_SCALE_GELFAND2):
+        assert F.ifnso_plan_set(p, F.IFNSO_OPT_SCALE, val) == 0
+        assert F.ifnso_plan_get(p, F.IFNSO_OPT_SCALE, C.byref(v)) == 0 and v.value == val
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_SCALE, 3) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_SCALE, -1) == F.IFNSO_ERR_INVALID_ARG
+    F.ifnso_plan_destroy(p)
+
+
 def test_muon_step_argument_checks(F):
     # every argument error is reported before any device work
     st, p = _plan(F, 256, 512, 4)

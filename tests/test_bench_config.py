@@ -18,6 +18,20 @@ def test_bench_depth_matches_equal_polar_analysis():
     assert chosen == {bench.WORKLOADS["muon_1b"]["L"]}
 
 
+def test_gelfand2_depth_matches_equal_polar_analysis():
+    # Gelfand's bound with q = 2 moves x toward 1, and one squaring fewer
+    # reaches NS5's distance to U V^T on every shape of the list
+    with open(os.path.join(ROOT, "tests", "golden", "equal_polar.json")) as f:
+        eq = json.load(f)
+    chosen = {min(L for L in range(4, 21) if v[f"ifnso_gelfand2_L{L}"] <= v["ns5"]) for v in eq.values()}
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    assert chosen == {bench.WORKLOADS["muon_1b"]["L_gelfand2"]}
+    for v in eq.values():
+        assert all(v[f"ifnso_gelfand2_L{L}"] <= v[f"ifnso_L{L}"] for L in range(8, 17))
+
+
 def test_flop_counts_match_oracle():
     from oracle import flops
 

@@ -49,7 +49,7 @@ def test_f32_ifnso(shape):
     assert abs(tr[0] - np.sum(A * A)) / np.sum(A * A) < 1e-6
 
 
-@pytest.mark.parametrize("scale", ["gram", "frob"])
+@pytest.mark.parametrize("scale", ["gram", "frob", "gelfand2"])
 def test_f32_scale_modes(scale):
     M = synth.gaussian(5, 96, 200)
     F, plan, b, xs, ys, w = run_ifnso([M], 6, "f32", scale=scale)
@@ -155,6 +155,34 @@ def test_bf16_folded_squarings_stay_accurate(L, precision):
     F, plan, b, xs, ys, w = run_ifnso([M], L, "bf16", precision=precision)
     err = rel(to_np(ys[0]), O.ifnso_alg1(to_np(xs[0]), w))
     assert err < 1e-2, err
+
+
+@pytest.mark.parametrize("L,shape", [(1, (256, 512)), (4, (200, 328)), (10, (512, 256)), (14, (256, 512)),
+                                     (14, (640, 1000))])
+def test_bf16_gelfand2(L, shape):
+    """Gelfand scaling with q = 2 (Eq. gelfand_formula): o = ||T_0^2||_F^(1/2)
+    from a product of D_1 with itself, then Algorithm 1 as usual."""
+    M = synth.gaussian(50 + L, *shape)
+    F, plan, b, xs, ys, w = run_ifnso([M], L, "bf16", scale="gelfand2")
+    assert plan.get(F.IFNSO_OPT_SCALE) == F.IFNSO_SCALE_GELFAND2
+    A = to_np(xs[0])
+    assert rel(to_np(ys[0]), O.ifnso_alg1(A, w, "gelfand2")) < TOL["bf16"]
+    st, s2, _ = plan.device_status(1)
+    assert st[0] == 0
+    At = O.orient(A)[0]
+    assert abs(s2[0] - O.scale_of(At, "gelfand2") ** 2) < 1e-3 * O.scale_of(At, "gelfand2") ** 2
+
+
+def test_bf16_gelfand2_zero_and_batch():
+    import torch
+
+    Z = np.zeros((256, 512))
+    M = synth.gaussian(7, 200, 328)
+    F, plan, b, xs, ys, w = run_ifnso([Z, M], 6, "bf16", scale="gelfand2")
+    st, _, _ = plan.device_status(2)
+    assert st[0] & F.IFNSO_DEV_ZERO_INPUT and st[1] == 0
+    assert torch.all(ys[0] == 0)
+    assert rel(to_np(ys[1]), O.ifnso_alg1(to_np(xs[1]), w, "gelfand2")) < TOL["bf16"]
 
 
 @pytest.mark.parametrize("cg", [1, 2])
