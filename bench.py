@@ -582,7 +582,7 @@ def main():
     coef = np.r_[1.0, w_full]
     mlp_info = None
     if args.coeffs == "mlp":
-        # per-matrix proposals (config 4 network, K = L + 1 outputs), trained on
+        # per-matrix proposals (the coefficient network, K = L + 1 outputs), trained on
         # synthetic spectra; the timed step includes the features, the network
         # and the coefficient rows inside ifnso_orthogonalize
         import synth
