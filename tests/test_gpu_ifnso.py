@@ -173,6 +173,13 @@ def test_bf16_gelfand2(L, shape):
     assert abs(s2[0] - O.scale_of(At, "gelfand2") ** 2) < 1e-3 * O.scale_of(At, "gelfand2") ** 2
 
 
+@pytest.mark.parametrize("cg", [1, 2])
+def test_bf16_gelfand2_cta_groups(cg):
+    M = synth.gaussian(61, 512, 768)
+    F, plan, b, xs, ys, w = run_ifnso([M], 10, "bf16", scale="gelfand2", cta_group=cg)
+    assert rel(to_np(ys[0]), O.ifnso_alg1(to_np(xs[0]), w, "gelfand2")) < TOL["bf16"]
+
+
 def test_bf16_gelfand2_zero_and_batch():
     import torch
 

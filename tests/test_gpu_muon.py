@@ -19,8 +19,8 @@ def bf16(a, dev):
     return torch.tensor(np.asarray(a, dtype=np.float32), device=dev).to(torch.bfloat16).contiguous()
 
 
-@pytest.mark.parametrize("nesterov", [True, False])
-def test_muon_step_matches_oracle(nesterov):
+@pytest.mark.parametrize("nesterov,cg", [(True, 0), (False, 0), (True, 2)])
+def test_muon_step_matches_oracle(nesterov, cg):
     import torch
 
     F = lib()
@@ -36,6 +36,7 @@ def test_muon_step_matches_oracle(nesterov):
     hmax = max(min(s) for s in SHAPES)
     wmax = max(max(s) for s in SHAPES)
     plan = F.Plan(hmax, wmax, "bf16", L=L)
+    plan.set(F.IFNSO_OPT_CTA_GROUP, cg)  # 2: the fused update also on MMAs of the CTA pair
     batch = F.Batch(G)
     for step in range(2):
         M0 = [to_np(m) for m in M]
