@@ -251,14 +251,34 @@ __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* s
   const float w1 = static_cast<float>(coef_at(coef, m, 1));
   float* gp = mi.gp;
   // 8 consecutive elements of one row per step (h_pad is a multiple of 256):
-  // two 16-byte loads of T_0, 16-byte stores of every output
+  // two 16-byte loads of T_0, 16-byte stores of every output.  FP32 plans
+  // cover the whole h_pad x h_pad buffer with a grid-stride loop; the
+  // tensor-core path stores symmetric intermediates on the 256 x 256 blocks on
+  // and above the diagonal only, and there each CTA takes one such block.
   const int64_t row8 = hp / 8;
-  for (int64_t e8 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e8 < n / 8;
-       e8 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = e8 / row8, j0 = (e8 - i * row8) * 8;
-    // the tensor-core path stores symmetric intermediates on the 256 x 256
-    // blocks on and above the diagonal only (T_0 in, D_1 / P out)
-    if (!f32 && (i >> 8) > (j0 >> 8)) continue;
+  const int nb = static_cast<int>(hp / 256);
+  int bi = 0, bj = 0;
+  if (!f32) {
+    int t = blockIdx.x;
+    if (t >= nb * (nb + 1) / 2) return;
+    while (t >= nb - bi) {  // block row bi holds blocks bi..nb-1
+      t -= nb - bi;
+      ++bi;
+    }
+    bj = bi + t;
+  }
+  const int64_t steps = f32 ? n / 8 : 256 * 32;
+  const int64_t first = f32 ? blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x : threadIdx.x;
+  const int64_t stride = f32 ? static_cast<int64_t>(gridDim.x) * blockDim.x : blockDim.x;
+  for (int64_t e8 = first; e8 < steps; e8 += stride) {
+    int64_t i, j0;
+    if (f32) {
+      i = e8 / row8;
+      j0 = (e8 - i * row8) * 8;
+    } else {
+      i = 256 * static_cast<int64_t>(bi) + (e8 >> 5);
+      j0 = 256 * static_cast<int64_t>(bj) + (e8 & 31) * 8;
+    }
     const int64_t e = i * hp + j0;
     const float4 g0 = reinterpret_cast<const float4*>(gp + e)[0];
     const float4 g1 = reinterpret_cast<const float4*>(gp + e)[1];
@@ -488,6 +508,10 @@ cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScala
   const int64_t n = static_cast<int64_t>(hpad_max) * hpad_max;
   int gx = static_cast<int>((n + 256 * 8 - 1) / (256 * 8));
   if (gx > 4096) gx = 4096;
+  if (!f32) {
+    const int nb = hpad_max / 256;  // one CTA per upper 256 x 256 block
+    gx = nb * (nb + 1) / 2;
+  }
   dim3 grid(gx, count);
   k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32, d_only);
   count_launch();
