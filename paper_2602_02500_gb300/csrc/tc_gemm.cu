@@ -25,12 +25,19 @@
 //               CTA only), N=256, K=16.
 //   warps 2..9  epilogue (two warps per TMEM lane quadrant, 128 columns each):
 //               tcgen05.ld of the accumulator, fused elementwise math of the
-//               pass, stores to global memory.
+//               pass, stores to global memory (16-bit results and T_0 through
+//               the bulk-copy engine).
 // The two accumulators let the epilogue of tile t overlap the main loop of
 // tile t + 1.  Symmetric results (T_0, D_l, P) are computed and stored on
 // the upper 256 x 256 blocks only; where a pass reads one as an operand, the
 // K blocks left of the tile's diagonal block are loaded from the stored block
 // across the diagonal (MN-major boxes; the MMA layout bits follow per K block).
+//
+// Epilogue kinds (EpiKind): the Gram (BF16 or E4M3 operands), the squaring
+// with its P update, the squaring that folds -2 D_l into its MMAs through an
+// identity product (no D_l read), the norm-only squaring of Gelfand scaling,
+// the final product (or the Muon weight update fused into it), and the three
+// products of the Newton-Schulz baseline.
 //
 // Every wait is bounded (ptx.cuh): on a timeout the CTA raises a shared
 // abort flag, records IFNSO_DEV_TIMEOUT in the matrix status word, lets its
