@@ -44,7 +44,7 @@ WORKLOADS = {
     "muon_7b": {
         "desc": "synthetic 7B transformer weight-gradient list: 32 layers x {4 x 4096x4096; gate, up "
                 "4096x14336; down 14336x4096}, 224 BF16 rank-32 + noise (10:1) matrices, seeds 0..223",
-        "list": "list_7b", "L": 14,
+        "list": "list_7b", "L": 14, "L_gelfand2": 13,
     },
 }
 
