@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="muon_1b", choices=sorted(WORKLOADS))
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--precision", default="auto", choices=["auto", "plain", "split"])
+    ap.add_argument("--split-squarings", type=int, default=-1,
+                    help="leading squarings with split FP16 operands in the mixed precision (-1: L - 8)")
     ap.add_argument("--scale", default="gram", choices=["gram", "frob", "gelfand2"],
                     help="input scaling: Gram (q = 1, the paper's), Frobenius, or Gelfand's bound with q = 2")
     ap.add_argument("--cta-group", type=int, default=0, choices=[0, 1, 2],
@@ -606,6 +608,7 @@ def main():
                     "loss_first_50": float(np.mean(curve[:50])), "loss_last_50": float(np.mean(curve[-50:]))}
 
     plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision, scale=args.scale)
+    plan.set(F.IFNSO_OPT_SPLIT_SQUARINGS, args.split_squarings)
     plan.set(F.IFNSO_OPT_TIMING, 1)
     plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
     plan.set(F.IFNSO_OPT_GRAM_E4M3, 1 if args.gram_e4m3 else 0)
@@ -671,7 +674,7 @@ def main():
     # from 3 on.
     peaks, peak_src = load_peaks()
     mode = plan.get(F.IFNSO_OPT_PRECISION)
-    k_split = {F.IFNSO_PREC_SPLIT: L - 1, F.IFNSO_PREC_MIXED: max(0, L - 8)}.get(mode, 0)
+    k_split = plan.get(F.IFNSO_OPT_SPLIT_SQUARINGS)
     per_step = [float(x) / max(1, calls) for x in pass_ms]
     sq = per_step[2:2 + (L - 1)] if L > 1 else []
 

@@ -105,7 +105,15 @@ typedef enum {
    * a relative rounding error of about 2^-5 per input element.  The
    * workspace grows by h x round_up(w, 16) bytes per matrix.  0 (default):
    * the BF16 Gram. */
-  IFNSO_OPT_GRAM_E4M3 = 9
+  IFNSO_OPT_GRAM_E4M3 = 9,
+  /* Number of leading squarings that take split FP16 hi + lo operands in
+   * IFNSO_PREC_MIXED (AUTO resolves to MIXED for 5 <= L <= 14): -1 (default)
+   * means max(0, L - 8); n >= 0 means min(n, L - 1).  Fewer split squarings
+   * are faster (a split squaring costs three products, a plain one one) and
+   * less accurate: the rounding of D_l in a plain squaring l grows by up to
+   * 2^(L - l) on small singular values.  Reading it back gives the number
+   * the plan uses (L - 1 for SPLIT, 0 for PLAIN). */
+  IFNSO_OPT_SPLIT_SQUARINGS = 10
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };

@@ -30,6 +30,7 @@ struct ifnso_plan {
   int dtype = IFNSO_BF16;
   int L = 0;
   int precision = IFNSO_PREC_AUTO;
+  int split_squarings = -1;  // IFNSO_OPT_SPLIT_SQUARINGS (-1: max(0, L - 8))
   int scale = IFNSO_SCALE_GRAM;
   int max_ctas = 0;
   int stop_after = -1;
@@ -239,7 +240,7 @@ Prec resolve_prec(const ifnso_plan* p) {
     r.k_split = L - 1;
     r.p_split = 1;
   } else if (mode == IFNSO_PREC_MIXED) {
-    r.k_split = std::max(0, L - 8);
+    r.k_split = p->split_squarings >= 0 ? std::min(p->split_squarings, L - 1) : std::max(0, L - 8);
     r.p_split = 1;
   }
   r.ws_lo = r.p_split || r.k_split > 0;
@@ -1353,6 +1354,10 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
         return fail(IFNSO_ERR_UNSUPPORTED, "the E4M3 Gram needs a BF16 plan");
       plan->gram_e4m3 = value != 0;
       break;
+    case IFNSO_OPT_SPLIT_SQUARINGS:
+      if (value < -1 || value > 30) return fail(IFNSO_ERR_INVALID_ARG, "split squarings %lld", (long long)value);
+      plan->split_squarings = static_cast<int>(value);
+      break;
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -1374,6 +1379,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_INJECT_STALL: *value = plan->inject_stall; return IFNSO_OK;
     case IFNSO_OPT_CTA_GROUP: *value = plan->cta_group; return IFNSO_OK;
     case IFNSO_OPT_GRAM_E4M3: *value = plan->gram_e4m3; return IFNSO_OK;
+    case IFNSO_OPT_SPLIT_SQUARINGS: *value = resolve_prec(plan).k_split; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }

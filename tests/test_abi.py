@@ -153,6 +153,23 @@ def test_scale_option(F):
     F.ifnso_plan_destroy(p)
 
 
+def test_split_squarings_option(F):
+    st, p = _plan(F, 256, 512, 14)
+    v = C.c_int64()
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_SPLIT_SQUARINGS, C.byref(v)) == 0 and v.value == 6  # AUTO -> MIXED: L - 8
+    for n, eff in [(0, 0), (3, 3), (13, 13), (30, 13), (-1, 6)]:
+        assert F.ifnso_plan_set(p, F.IFNSO_OPT_SPLIT_SQUARINGS, n) == 0
+        assert F.ifnso_plan_get(p, F.IFNSO_OPT_SPLIT_SQUARINGS, C.byref(v)) == 0 and v.value == eff
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_SPLIT_SQUARINGS, -2) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_SPLIT_SQUARINGS, 31) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_SPLIT_SQUARINGS, 4) == 0
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_PRECISION, F.IFNSO_PREC_SPLIT) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_SPLIT_SQUARINGS, C.byref(v)) == 0 and v.value == 13
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_PRECISION, F.IFNSO_PREC_PLAIN) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_SPLIT_SQUARINGS, C.byref(v)) == 0 and v.value == 0
+    F.ifnso_plan_destroy(p)
+
+
 def test_muon_step_argument_checks(F):
     # every argument error is reported before any device work
     st, p = _plan(F, 256, 512, 4)

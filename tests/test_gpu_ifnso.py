@@ -173,6 +173,31 @@ def test_bf16_gelfand2(L, shape):
     assert abs(s2[0] - O.scale_of(At, "gelfand2") ** 2) < 1e-3 * O.scale_of(At, "gelfand2") ** 2
 
 
+def test_bf16_split_squarings_option():
+    """IFNSO_OPT_SPLIT_SQUARINGS moves the split/plain boundary of the mixed
+    precision: 5 split squarings or all 13, on a well-conditioned input where
+    both stay within the tolerance (the precision margin itself is measured
+    on hard inputs separately); the two results differ, so the option acts."""
+    import torch
+
+    M = synth.gaussian(3, 512, 768)
+    F = lib()
+    x = to_dev(M, "bf16")
+    w = coeffs(14)
+    ref = O.ifnso_alg1(to_np(x), w)
+    out = {}
+    for k in (5, 13):
+        y = torch.empty(x.shape, dtype=x.dtype, device=x.device)
+        plan = F.Plan(512, 768, "bf16", L=14)
+        plan.set(F.IFNSO_OPT_SPLIT_SQUARINGS, k)
+        assert plan.get(F.IFNSO_OPT_SPLIT_SQUARINGS) == k
+        plan.orthogonalize(F.Batch([x]), np.r_[1.0, w], [y])
+        torch.cuda.synchronize()
+        out[k] = to_np(y)
+        assert rel(out[k], ref) < TOL["bf16"]
+    assert not np.array_equal(out[5], out[13])
+
+
 @pytest.mark.parametrize("cg", [1, 2])
 def test_bf16_gelfand2_cta_groups(cg):
     M = synth.gaussian(61, 512, 768)
