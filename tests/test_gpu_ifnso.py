@@ -253,6 +253,33 @@ def test_bf16_zero_and_scale_invariance():
     assert rel(to_np(ys[2]), O.ifnso_alg1(to_np(xs[2]), w)) < TOL["bf16"]
 
 
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_nonfinite_input_is_flagged_and_isolated(dtype):
+    """A matrix holding a NaN (or an Inf) gets IFNSO_DEV_NONFINITE; the other
+    matrices of the same call are unaffected (their scalars, tiles and
+    results are their own)."""
+    M = synth.gaussian(8, 128, 256)
+    bad_nan = M.copy()
+    bad_nan[5, 7] = np.nan
+    bad_inf = M.copy()
+    bad_inf[100, 200] = np.inf
+    F, plan, b, xs, ys, w = run_ifnso([bad_nan, M, bad_inf], 6, dtype)
+    st, _, _ = plan.device_status(3)
+    assert st[0] & F.IFNSO_DEV_NONFINITE and st[2] & F.IFNSO_DEV_NONFINITE and st[1] == 0
+    assert rel(to_np(ys[1]), O.ifnso_alg1(to_np(xs[1]), w)) < TOL[dtype]
+
+
+def test_empty_batch_is_a_no_op():
+    import torch
+
+    F = lib()
+    plan = F.Plan(128, 256, "bf16", L=4)
+    before = F.launch_count()
+    plan.orthogonalize(F.Batch([]), np.r_[1.0, coeffs(4)], [], ws=F.Workspace(1024, device=torch.device("cuda")))
+    torch.cuda.synchronize()
+    assert F.launch_count() == before
+
+
 @pytest.mark.parametrize("shape", [(256, 512), (392, 136)])
 def test_bf16_ns(shape):
     import torch
