@@ -113,7 +113,14 @@ typedef enum {
    * less accurate: the rounding of D_l in a plain squaring l grows by up to
    * 2^(L - l) on small singular values.  Reading it back gives the number
    * the plan uses (L - 1 for SPLIT, 0 for PLAIN). */
-  IFNSO_OPT_SPLIT_SQUARINGS = 10
+  IFNSO_OPT_SPLIT_SQUARINGS = 10,
+  /* Compute streams of ifnso_orthogonalize_host: 1 runs every group's
+   * passes on the caller's stream; 2 (default) alternates the groups between
+   * the caller's stream and a second stream of the plan, so that one
+   * group's passes can start on the SMs another group's pass is leaving
+   * (the groups share no buffers).  Either way the call is ordered after
+   * earlier work on the caller's stream and later work waits for it. */
+  IFNSO_OPT_HOST_STREAMS = 11
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };

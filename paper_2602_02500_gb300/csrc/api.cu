@@ -53,6 +53,8 @@ struct ifnso_plan {
   std::vector<std::vector<cudaEvent_t>> ev_graph;  // recorded by captured calls (kept for replays)
   // ifnso_orthogonalize_host: copy streams and the events that order them
   cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaStream_t s_comp = nullptr;  // the second compute stream (IFNSO_OPT_HOST_STREAMS = 2)
+  int host_streams = 2;
   cudaEvent_t ev_start = nullptr, ev_last = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_done;
   int groups = 1;  // groups the item lists of the cached metadata are built for
@@ -993,6 +995,7 @@ ifnso_status ensure_copy_streams(ifnso_plan* plan, int groups) {
   if (!plan->s_in) {
     IFNSO_CUDA(cudaStreamCreateWithFlags(&plan->s_in, cudaStreamNonBlocking), "cudaStreamCreate");
     IFNSO_CUDA(cudaStreamCreateWithFlags(&plan->s_out, cudaStreamNonBlocking), "cudaStreamCreate");
+    IFNSO_CUDA(cudaStreamCreateWithFlags(&plan->s_comp, cudaStreamNonBlocking), "cudaStreamCreate");
     IFNSO_CUDA(cudaEventCreateWithFlags(&plan->ev_start, cudaEventDisableTiming), "cudaEventCreate");
     IFNSO_CUDA(cudaEventCreateWithFlags(&plan->ev_last, cudaEventDisableTiming), "cudaEventCreate");
   }
@@ -1358,6 +1361,10 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       if (value < -1 || value > 30) return fail(IFNSO_ERR_INVALID_ARG, "split squarings %lld", (long long)value);
       plan->split_squarings = static_cast<int>(value);
       break;
+    case IFNSO_OPT_HOST_STREAMS:
+      if (value != 1 && value != 2) return fail(IFNSO_ERR_INVALID_ARG, "host streams %lld (1 or 2)", (long long)value);
+      plan->host_streams = static_cast<int>(value);
+      return IFNSO_OK;  // the metadata does not depend on it
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -1380,6 +1387,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_CTA_GROUP: *value = plan->cta_group; return IFNSO_OK;
     case IFNSO_OPT_GRAM_E4M3: *value = plan->gram_e4m3; return IFNSO_OK;
     case IFNSO_OPT_SPLIT_SQUARINGS: *value = resolve_prec(plan).k_split; return IFNSO_OK;
+    case IFNSO_OPT_HOST_STREAMS: *value = plan->host_streams; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }
@@ -1393,8 +1401,10 @@ ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
   if (plan->s_in) {
     cudaStreamSynchronize(plan->s_in);
     cudaStreamSynchronize(plan->s_out);
+    cudaStreamSynchronize(plan->s_comp);
     cudaStreamDestroy(plan->s_in);
     cudaStreamDestroy(plan->s_out);
+    cudaStreamDestroy(plan->s_comp);
     cudaEventDestroy(plan->ev_start);
     cudaEventDestroy(plan->ev_last);
   }
@@ -1563,6 +1573,10 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
   IFNSO_CUDA(cudaEventRecord(plan->ev_start, stream), "cudaEventRecord");
   IFNSO_CUDA(cudaStreamWaitEvent(plan->s_in, plan->ev_start, 0), "cudaStreamWaitEvent");
   IFNSO_CUDA(cudaStreamWaitEvent(plan->s_out, plan->ev_start, 0), "cudaStreamWaitEvent");
+  // odd groups on the second compute stream (which also waits for the
+  // caller's earlier work, the metadata upload included)
+  const bool two = plan->host_streams == 2 && ng > 1;
+  if (two) IFNSO_CUDA(cudaStreamWaitEvent(plan->s_comp, plan->ev_start, 0), "cudaStreamWaitEvent");
   for (int g = 0; g < ng; ++g) {
     for (int i = gb[g]; i < gb[g + 1]; ++i) {
       const Shape& s = shp[i];
@@ -1579,16 +1593,17 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
   }
   int hpad_max = 0;
   for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
-  const Run r{plan, &ly, ws, coeffs, hpad_max, stream, ly.f32 != 0};
   for (int g = 0; g < ng; ++g) {
-    IFNSO_CUDA(cudaStreamWaitEvent(stream, plan->ev_in[g], 0), "cudaStreamWaitEvent");
+    cudaStream_t cs = (two && (g & 1)) ? plan->s_comp : stream;
+    const Run r{plan, &ly, ws, coeffs, hpad_max, cs, ly.f32 != 0};
+    IFNSO_CUDA(cudaStreamWaitEvent(cs, plan->ev_in[g], 0), "cudaStreamWaitEvent");
     if (ly.f32)
       st = run_f32(r);
     else
       st = run_tc(r, gb[g], gb[g + 1] - gb[g], plan->sym_off[g], plan->sym_off[g + 1], plan->app_off[g],
                   plan->app_off[g + 1]);
     if (st != IFNSO_OK) return st;
-    IFNSO_CUDA(cudaEventRecord(plan->ev_done[g], stream), "cudaEventRecord");
+    IFNSO_CUDA(cudaEventRecord(plan->ev_done[g], cs), "cudaEventRecord");
     IFNSO_CUDA(cudaStreamWaitEvent(plan->s_out, plan->ev_done[g], 0), "cudaStreamWaitEvent");
     for (int i = gb[g]; i < gb[g + 1]; ++i) {
       const Shape& s = shp[i];

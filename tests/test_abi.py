@@ -170,6 +170,17 @@ def test_split_squarings_option(F):
     F.ifnso_plan_destroy(p)
 
 
+def test_host_streams_option(F):
+    st, p = _plan(F, 256, 512, 6)
+    v = C.c_int64()
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_HOST_STREAMS, C.byref(v)) == 0 and v.value == 2
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_HOST_STREAMS, 1) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_HOST_STREAMS, C.byref(v)) == 0 and v.value == 1
+    for bad in (0, 3, -1):
+        assert F.ifnso_plan_set(p, F.IFNSO_OPT_HOST_STREAMS, bad) == F.IFNSO_ERR_INVALID_ARG
+    F.ifnso_plan_destroy(p)
+
+
 def test_muon_step_argument_checks(F):
     # every argument error is reported before any device work
     st, p = _plan(F, 256, 512, 4)

@@ -19,8 +19,8 @@ def _host_copy(x):
     return full.cpu().pin_memory()
 
 
-@pytest.mark.parametrize("groups", [1, 2, 3, 0])
-def test_host_matches_device_bf16(groups):
+@pytest.mark.parametrize("groups,streams", [(1, 2), (2, 2), (3, 2), (0, 2), (3, 1), (0, 1)])
+def test_host_matches_device_bf16(groups, streams):
     import torch
 
     F = lib()
@@ -32,6 +32,7 @@ def test_host_matches_device_bf16(groups):
     hmax = max(min(s) for s in shapes)
     wmax = max(max(s) for s in shapes)
     plan = F.Plan(hmax, wmax, "bf16", L=L)
+    plan.set(F.IFNSO_OPT_HOST_STREAMS, streams)  # 2: odd groups on the plan's second compute stream
     batch = F.Batch(xs)
     ref = [torch.empty(x.shape, dtype=x.dtype, device=x.device) for x in xs]
     plan.orthogonalize(batch, w, ref)
@@ -53,7 +54,7 @@ def test_host_matches_device_bf16(groups):
         for i, (h, m) in enumerate(zip(hout, mats)):
             got = h.double().numpy()
             # same kernels; only the order of the FP64 atomics of o = ||T_0||_F may differ
-            assert rel(got, ref_h[i]) < 1e-5, (groups, i)
+            assert rel(got, ref_h[i]) < 1e-5, (groups, streams, i)
             A = to_np(xs[i])
             assert rel(got, O.ifnso_alg1(A, w[1:])) < 2e-2
 
