@@ -274,6 +274,19 @@ __device__ __forceinline__ void blk_store(T* dst, int64_t ld, const float* st) {
   }
 }
 
+// Add the staged block into the FP32 block at dst (block row i at
+// dst + i * ld) with vector reductions performed in L2: the destination is
+// not read into the SM.  Rows 16-byte aligned.
+__device__ __forceinline__ void blk_red_add(float* dst, int64_t ld, const float* st) {
+  const int cc = blk_col<float>();
+#pragma unroll
+  for (int s = 0; s < Blk<float>::kPasses; ++s) {
+    const int i = blk_row<float>(s);
+    const float* x = st + i * kStageLd + cc;
+    red_add_v4(dst + static_cast<int64_t>(i) * ld + cc, x[0], x[1], x[2], x[3]);
+  }
+}
+
 // Same, clipped to `rows` x `cols` of the destination; vec: 16-byte aligned rows.
 template <typename T, bool TRANS>
 __device__ __forceinline__ void blk_store_bounded(T* dst, int64_t ld, const float* st, int rows, int cols,
@@ -369,7 +382,9 @@ __device__ __forceinline__ void epilogue_load(const TcParams& p, const TcProblem
       blk_load<__half>(in.a, static_cast<const __half*>(pr.aux0) + off, pr.ld_aux);
       if (p.read_lo) blk_load<__half>(in.b, static_cast<const __half*>(pr.aux1) + off, pr.ld_aux);
     }
-    if (p.p_mode >= 2) blk_load<float>(in.c, pr.pacc + off, pr.ld_aux);
+    // P itself only where the pass needs its value: the final pass (P goes
+    // out as BF16 hi + lo) and p_mode 4 (T_0); other passes add into it in L2
+    if (p.p_mode == 4 || (p.p_mode >= 2 && p.final_pass)) blk_load<float>(in.c, pr.pacc + off, pr.ld_aux);
   } else if constexpr (EPI == EPI_NS_SQR) {
     blk_load<__nv_bfloat16>(in.a, static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r0) * pr.ld_aux + c0,
                             pr.ld_aux);
@@ -453,9 +468,11 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       blk_unpack<float>(in.c, st, pv);
 #pragma unroll
       for (int j = 0; j < 32; ++j) pv[j] = fmaf(-w1, pv[j] * inv, (c0 + j == r) ? c0f : 0.f);
-    } else if (p.p_mode >= 2) {
+    } else if (p.p_mode >= 2 && p.final_pass) {
       blk_unpack<float>(in.c, st, pv);
     } else {
+      // p_mode 1: P starts as c0 I; p_mode 2 and 3 before the final pass: pv
+      // is the sum of this pass's terms, which is added to P in L2
       const float c0f = p.p_mode == 1 ? static_cast<float>(p.scal[pr.mat].c0) : 0.f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) pv[j] = (c0 + j == r) ? c0f : 0.f;
@@ -476,7 +493,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
       }
     }
     if (!p.final_pass) {
-      if (p.p_mode != 0) {
+      if (p.p_mode == 2 || p.p_mode == 3) {
+        blk_put(st, pv);
+        blk_red_add(pr.pacc + static_cast<int64_t>(r0) * pr.ld_aux + c0, pr.ld_aux, st);
+      } else if (p.p_mode != 0) {
         store_blk<float>(pr.pacc, pr.ld_aux, r0, c0, pv, st);
       }
       if (p.write_lo) {
