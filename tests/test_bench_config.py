@@ -41,3 +41,21 @@ def test_flop_counts_match_oracle():
     for h, w in [(2048, 2048), (2048, 5632), (128, 1024)]:
         assert bench.flops_ifnso(h, w, 14) == flops.ifnso_nominal(h, w, 14)
         assert bench.flops_ns5(h, w) == flops.ns5_nominal(h, w)
+
+
+def test_committed_traffic_counters_belong_to_the_kernel_source():
+    """profiles/traffic.json holds ncu DRAM counters of the tensor-core kernel as
+    it is committed (the bench reports them only then): every pass kind of the
+    1B list is there, and each is within 15% of its algorithmic bytes."""
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    t = bench.load_traffic()
+    assert t, "traffic.json was captured from another version of tc_gemm.cu"
+    # algorithmic bytes per launch on the 1B list: 168 matrices with h = 2048, upper
+    # 256-blocks (36 of 64) of 2048 x 2048, bytes per element as in the pass profiles
+    upper = 36 * 256 * 256
+    per = {"squaring_split_p": 16, "squaring_split_fold": 8, "squaring_plain_p": 12, "squaring_plain_fold": 4}
+    for k, b in per.items():
+        alg = 168 * upper * b
+        assert 0.85 * alg <= t["muon_1b:" + k] <= 1.15 * alg, (k, t["muon_1b:" + k], alg)
