@@ -125,7 +125,8 @@ struct TcParams {
   int32_t write_lo;    // EPI_SQR: store D_{l+1} as hi + lo (the next pass is split)
   int32_t p_split;     // EPI_SQR final pass / prep: store P as BF16 hi + lo
   int32_t p_mode;      // EPI_SQR: 0 P untouched, 1 P written from c0 I and two terms,
-                       // 2 P read and two terms subtracted, 3 P read and one term subtracted,
+                       // 2 two terms subtracted from P, 3 one term subtracted from P (in L2,
+                       // without reading P; the final pass reads it and writes hi + lo),
                        // 4 P written from c0 I, w_1 T_0 / o (read) and two terms
   int32_t feat;        // EPI_SQR: accumulate sum (D_l^2)_ij^2 into MatScalars::spare[0]
   int32_t inject;      // testing aid: CTA 0's producer loads nothing, so its waits run out
