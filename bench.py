@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--scale", default="gram", choices=["gram", "frob", "gelfand2"],
                     help="input scaling: Gram (q = 1, the paper's), Frobenius, or Gelfand's bound with q = 2")
     ap.add_argument("--cta-group", type=int, default=0, choices=[0, 1, 2],
-                    help="tensor-core passes: MMAs of the CTA pair (2), per-CTA MMAs with B multicast (1), "
+                    help="tensor-core passes: MMAs of the CTA pair (2), per-CTA MMAs, each CTA loading its whole B tile (1), "
                          "or the library's choice per pass (0)")
     ap.add_argument("--coeffs", default="fixed", choices=["fixed", "mlp"],
                     help="fixed: the learner's w_1..w_L for every matrix; mlp: per-matrix coefficients "
@@ -786,11 +786,11 @@ def main():
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
                        "l2": "inputs larger than L2 (no flush)",
                        "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
-                       "mma": ({k: ("CTA pair (M = 256)" if v == 2 else "per CTA, B multicast")
+                       "mma": ({k: ("CTA pair (M = 256)" if v == 2 else "per CTA (M = 128), whole B tile per CTA")
                                 for k, v in tuned.items()} if tuned else
                                {0: "tcgen05 MMAs of the CTA pair (M = 256) for the split squarings, per-CTA "
-                                   "MMAs with the B tile multicast in 2-CTA clusters for the other passes",
-                                1: "per-CTA tcgen05 MMAs, B tile multicast in 2-CTA clusters",
+                                   "MMAs (each CTA loading its whole B tile) for the other passes",
+                                1: "per-CTA tcgen05 MMAs, each CTA loading its whole B tile",
                                 2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group]),
                        "autotuned": tuned is not None,
                        "coefficients": ("per-matrix proposals of the coefficient network, computed inside each "

@@ -87,8 +87,8 @@ typedef enum {
   /* How the two CTAs of a cluster share the B operand of a pair of output
    * tiles in the tensor-core passes (the results agree bit for bit on every
    * case tested):
-   * 1: each CTA issues its own M = 128 MMAs and multicasts its half of B to
-   *    both CTAs.
+   * 1: each CTA issues its own M = 128 MMAs and loads the whole B tile into
+   *    its own shared memory (the CTAs exchange nothing).
    * 2: MMAs of the CTA pair, M = 256 (tcgen05 cta_group::2); each CTA keeps
    *    its own half of B (a third fewer operand bytes per SM and product)
    *    and the odd CTA's copies complete on the even CTA's stage barrier.
@@ -319,7 +319,12 @@ ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_pass
  * ifnso_orthogonalize.  which: 0 = T_0 then P (FP32), 1/2 = D buffer 0 hi/lo
  * (FP16, or FP32 for F32 plans), 3/4 = D buffer 1 hi/lo, 5 = the FP32
  * coefficient row (c_0, w_1..w_L) the proposal network chose for the matrix
- * (ld = 32).  BF16 plans keep these symmetric matrices on their 256 x 256
+ * (ld = 32), 6 = the matrix's 64-byte record of FP64 scalars (ld = 8): [0]
+ * ||T_0||_F^2, [1] tr(T_0), [2] the squared input scale, [3] the D-basis
+ * identity weight 1 + sum w_l, [4] two FP32 reciprocals and two 32-bit words
+ * (status bits, max |A_ij|), [6] ||D_1^2||_F^2 = tr(D_1^4) when the proposal
+ * network ran (its third feature), [7] 1.0 where that network's fallback head
+ * chose the fixed coefficients, else 0.0.  BF16 plans keep these symmetric matrices on their 256 x 256
  * blocks on and above the diagonal only: element (i, j) with
  * i / 256 > j / 256 is the one at (j, i); the memory below is unspecified. */
 ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch,
@@ -332,7 +337,11 @@ ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc
 
 /* norm2_out[i] (device, FP64, count entries) = ||M_i||_F^2, reduced as FP32
  * partial sums of squares per CTA and an FP64 final accumulation (the scaling
- * of Eq. constraint, Sec. 1).  dtype is that of the matrices.  Asynchronous. */
+ * of Eq. constraint, Sec. 1).  dtype is that of the matrices.  The matrices'
+ * descriptions go through a device buffer that the library allocates per
+ * device on first use and grows; before overwriting it a call waits (on the
+ * host) until the previous call's kernel on that device has read it, so
+ * calls from several streams or threads are safe.  Otherwise asynchronous. */
 ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dtype,
                                    double* norm2_out, ifnso_stream_t stream);
 
@@ -351,7 +360,8 @@ ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dt
  * caller passes the inputs and norm2_out (device, FP64, count entries), which
  * the call zeroes before accumulating.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares
+ * current; make that first call before any stream capture.  Every call
+ * uploads its descriptors from pageable host memory.  Every call shares
  * the array and it keeps the last call's descriptors: calls whose work
  * overlaps on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Asynchronous on `stream`. */

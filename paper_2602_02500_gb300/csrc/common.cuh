@@ -132,7 +132,7 @@ struct TcParams {
   int32_t inject;      // testing aid: CTA 0's producer loads nothing, so its waits run out
   uint32_t wait_ms;    // limit of every pipeline wait (0: the default of ptx.cuh)
   int32_t cta_group;   // 2: MMAs of the CTA pair (M = 256, B halves stay in each CTA);
-                       // 1: per-CTA MMAs with the B tile multicast to both CTAs
+                       // 1: per-CTA MMAs, each CTA loading the whole B tile
   int32_t fold_d;      // EPI_SQR: the MMAs also add -2 D_l (an identity product), so the
                        // accumulator holds D_l^2 - 2 D_l = -D_{l+1} and the epilogue
                        // does not read D_l (passes whose P update has no D_l term)

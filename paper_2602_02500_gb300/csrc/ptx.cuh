@@ -141,18 +141,6 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap,
       : "memory");
 }
 
-// The same box delivered to the same shared-memory offset of every CTA in
-// `mask` (this GPU's own memory only), completing bytes on each destination
-// CTA's mbarrier at `bar`'s offset.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const void* tmap, uint32_t bar, int32_t x,
-                                               int32_t y, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-      "l"(tmap), "r"(bar), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-
 // ---------------------------------------------------------------- clusters
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
@@ -282,19 +270,19 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
         : "memory");
 }
 
-// Same, arriving on the mbarrier at `bar`'s offset in every CTA of `mask`.
+// CG 1: umma_commit on this CTA's barrier.  CG 2 (issued by the even CTA):
+// one arrive on the barrier at `bar`'s offset in both CTAs of the pair (a
+// completion signal of the pair's MMAs, delivered to the two CTAs' barriers;
+// no data moves).
 template <int CG = 1>
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask) {
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
   if constexpr (CG == 2)
     asm volatile(
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-        "h"(mask)
+        "h"(static_cast<uint16_t>(0x3))
         : "memory");
   else
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
+    umma_commit<CG>(bar);
 }
 
 // 32 lanes x 32 consecutive 32-bit columns: thread t of the warp receives

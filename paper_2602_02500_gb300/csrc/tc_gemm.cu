@@ -6,10 +6,11 @@
 // D basis, D_{l+1} = 2 D_l - D_l^2), or the final product Y = Y' A / sqrt(o).
 // Clusters of two CTAs (one CTA per SM) walk a static list of pairs of
 // 128 x 256 output tiles that share their B operand; each CTA owns one tile
-// of the pair (its 128 rows of A, its accumulator) and loads half of the
-// shared B tile.  Two ways to use that half (template parameter CG):
-//   CG = 1  each CTA issues its own M = 128 MMAs and TMA-multicasts its half
-//           of B to both CTAs, so each shared memory holds the whole B tile;
+// of the pair (its 128 rows of A, its accumulator).  Two MMA modes (template
+// parameter CG):
+//   CG = 1  each CTA issues its own M = 128 MMAs and TMA-loads the whole
+//           256-row B tile into its own shared memory (the pair reads the
+//           shared B tile twice from L2; the CTAs exchange nothing);
 //   CG = 2  the even CTA issues M = 256 MMAs of the CTA pair
 //           (tcgen05 cta_group::2) that read A and B from both shared
 //           memories: each CTA stores only its own half of B, so an SM takes
@@ -63,8 +64,7 @@ constexpr int kDevTimeout = 4;  // IFNSO_DEV_TIMEOUT
 
 template <int NA, int NB, int CG>
 struct Cfg {
-  // B tile held by one CTA: all 256 rows (CG 1, half of them multicast by the
-  // peer) or its own 128-row half (CG 2)
+  // B tile held by one CTA: all 256 rows (CG 1) or its own 128-row half (CG 2)
   static constexpr uint32_t tile_b = (CG == 2 ? BN / 2 : BN) * BK * 2;
   static constexpr uint32_t stage_bytes = NA * kTileA + NB * tile_b;
   static constexpr int stages_fit = static_cast<int>((200u * 1024u) / stage_bytes);
@@ -580,7 +580,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   constexpr uint32_t kIsBf16 = (kSqr || EPI == EPI_GRAM_F8) ? 0u : 1u;
   constexpr bool kF8 = (EPI == EPI_GRAM_F8);
   constexpr int kBKe = kF8 ? 2 * BK : BK;  // elements per 128-byte K block
-  constexpr uint16_t kPair = 0x3;                           // both CTAs of the cluster
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -599,8 +598,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   // A cluster of two CTAs computes the two 128-row halves of one 256 x 256
-  // pair of tiles: both need the same B tile, which each CTA loads half of
-  // (and, CG 1, multicasts to both).
+  // pair of tiles: both need the same B tile (CG 1: each CTA loads all of it;
+  // CG 2: each loads the half its MMAs contribute).
   const int crank = static_cast<int>(cluster_ctarank());
   const int cid = static_cast<int>(cluster_id_x());
   const int ncl = static_cast<int>(cluster_count_x());
@@ -611,10 +610,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // even CTA: armed with the bytes of both CTAs' copies (the odd CTA's
         // stage barriers are not used)
         mbar_init(full_bar(s), 1);
-        mbar_init(empty_bar(s), 1);  // freed by the pair's MMAs (one commit, multicast)
+        mbar_init(empty_bar(s), 1);  // freed by the pair's MMAs (the even CTA commits to both CTAs)
       } else {
         mbar_init(full_bar(s), 1);
-        mbar_init(empty_bar(s), 2);  // freed by the MMAs of both CTAs (their B halves live here)
+        mbar_init(empty_bar(s), 1);  // freed by this CTA's own MMAs
       }
     }
     for (int a = 0; a < 2; ++a) {
@@ -653,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
+  cluster_sync();  // CG 2: the peer's barriers are initialised before any copy or commit reaches them
   const uint32_t tmem_base = *tmem_slot;
   const unsigned long long tmo = p.wait_ms ? p.wait_ms * 1000000ull : kWaitTimeoutNs;
 
@@ -692,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
           const uint32_t fb = full_bar(stage);
           if constexpr (CG == 1)
-            mbar_arrive_expect_tx(fb, C::stage_bytes);  // own A + both halves of B
+            mbar_arrive_expect_tx(fb, C::stage_bytes);  // own A + the whole B tile
           else if (crank == 0)
             mbar_arrive_expect_tx(fb, 2 * C::stage_bytes);  // A and the B half of both CTAs
           // CG 2, odd CTA: the copies complete on the even CTA's barrier
@@ -737,13 +736,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
                 load(dst + 8192, m, wi.tn * BN + 128 * crank + 64, k0);
               }
             } else if (!b_mn) {
-              // this CTA's half: rows [128 crank, 128 crank + 128) of the B tile
-              tma_load_2d_mc(dst + 16384 * crank, m, fb, k0, wi.tn * BN + 128 * crank, kPair);
+              // the whole B tile: two 128-row boxes
+              load(dst, m, k0, wi.tn * BN);
+              load(dst + 16384, m, k0, wi.tn * BN + 128);
             } else {
-              // this CTA's half: MN chunks 2 crank and 2 crank + 1 of the B tile
+              // the whole B tile: four 64-wide MN chunks
 #pragma unroll
-              for (int j = 2 * crank; j < 2 * crank + 2; ++j)
-                tma_load_2d_mc(dst + 8192 * j, m, fb, wi.tn * BN + 64 * j, k0, kPair);
+              for (int j = 0; j < 4; ++j) load(dst + 8192 * j, m, wi.tn * BN + 64 * j, k0);
             }
           }
           ++filled[stage];
@@ -832,8 +831,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
               }
             }
           }
-          // frees the stage in both CTAs once these MMAs have read it
-          umma_commit_mc<CG>(empty_bar(stage), kPair);
+          // frees the stage once these MMAs have read it (CG 2: in both CTAs)
+          umma_commit_pair<CG>(empty_bar(stage));
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -841,10 +840,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         }
         if (!ok) break;
         // accumulator ready for the epilogue (of both CTAs when the MMAs are the pair's)
-        if constexpr (CG == 2)
-          umma_commit_mc<CG>(tfull_bar(acc), kPair);
-        else
-          umma_commit<CG>(tfull_bar(acc));
+        umma_commit_pair<CG>(tfull_bar(acc));
       }
       if (!ok) set_timeout(p.scal, cur_mat);
       // make sure no MMA is still writing TMEM or reading shared memory
@@ -928,7 +924,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     tc_fence_after();
     tmem_dealloc<CG>(tmem_base, kTmemCols);
   }
-  // neither CTA leaves while the other may still multicast into it or arrive on its barriers
+  // neither CTA leaves while the other may still arrive on its barriers or read its shared memory
   cluster_sync();
 }
 

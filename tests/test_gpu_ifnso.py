@@ -128,7 +128,7 @@ def test_bf16_ifnso(shape, L, precision):
 @pytest.mark.parametrize("L,precision", [(4, "plain"), (14, "mixed"), (3, "split")])
 @pytest.mark.parametrize("shape", [(256, 512), (392, 136), (640, 1000), (1000, 640)])
 def test_bf16_cta_groups(shape, L, precision):
-    """Per-CTA MMAs (B multicast) and MMAs of the CTA pair give the same
+    """Per-CTA MMAs (whole B tile per CTA) and MMAs of the CTA pair give the same
     products up to the rounding order of the accumulation."""
     M = synth.gaussian(40, *shape)
     out = {}
