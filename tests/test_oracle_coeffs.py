@@ -144,3 +144,26 @@ def test_table1_flops():
         assert sf4(flops.original_ns(h, w, t["original_ns_steps"])) == on
         assert sf4(flops.muon_ns(h, w)) == mu
         assert sf4(flops.ifnso(h, w, t["ifnso_L"])) == ours
+
+
+def test_nominal_flop_helpers():
+    """The product-only counts used for TFLOP/s, tied to Table 1 and to hand counts."""
+    with open(os.path.join(GOLDEN, "table1_flops.json")) as f:
+        t = json.load(f)
+    L = t["ifnso_L"]
+    for (h, w), ifn, mu in zip(t["sizes"], t["ifnso"], t["muon_ns"]):
+        # IFNSO: Table 1's count less its L h^2 elementwise aggregation
+        assert flops.ifnso_nominal(h, w, L) + L * h * h == flops.ifnso(h, w, L)
+        assert float(f"{flops.ifnso_nominal(h, w, L) + L * h * h:.3e}") == ifn
+    # NS5 with (X X^T)^2 X formed as S (S X): on a square input 4h^2 w + 2h^3 =
+    # 6h^2 w, the product part of the printed Muon count; only its 5 x 5hw
+    # elementwise terms differ (Table 1, 128 x 128: 6.332e7)
+    h = 128
+    assert flops.ns5_nominal(h, h) + 25 * h * h == flops.muon_ns(h, h)
+    assert float(f"{flops.ns5_nominal(h, h) + 25 * h * h:.3e}") == t["muon_ns"][0]
+    # hand counts: one step on a 2 x 3 input is X X^T (2*2*3*2 = 24), S S (2*2*2*2 = 16),
+    # B X (24) = 64; an L = 1 IFNSO on 1 x 1 is the Gram and the apply, 2 + 2
+    assert flops.ns5_nominal(2, 3, steps=1) == 64
+    assert flops.ns5_nominal(2, 3) == 5 * 64
+    assert flops.ifnso_nominal(1, 1, 1) == 4
+    assert flops.ifnso_nominal(2, 3, 3) == 4 * 4 * 3 + 2 * 2 * 8

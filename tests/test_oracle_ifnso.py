@@ -145,3 +145,18 @@ def test_polar_factor_and_errors():
 def test_exponents():
     assert I.exponents(4) == [0, 1, 2, 4, 8]
     assert I.exponents(1) == [0, 1]
+
+
+def test_rel_fro_hand_computed():
+    # the metric every parity assertion goes through, on values worked by hand
+    assert I.rel_fro(np.array([3.0, 4.0]), np.array([0.0, 5.0])) == pytest.approx(np.sqrt(10.0) / 5.0, rel=1e-15)
+    R = np.array([[1.0, -2.0], [2.0, 4.0]])            # ||R||_F = 5
+    assert I.rel_fro(R, R) == 0.0
+    assert I.rel_fro(2.0 * R, R) == pytest.approx(1.0, rel=1e-15)
+    assert I.rel_fro(R + np.array([[0.0, 0.0], [0.0, 1.0]]), R) == pytest.approx(0.2, rel=1e-15)
+    assert I.rel_fro(R.T, R) == pytest.approx(np.sqrt(32.0) / 5.0, rel=1e-15)   # not symmetric: a transposed operand shows
+    # a zero reference gives the absolute error
+    assert I.rel_fro(np.array([3.0, 4.0]), np.zeros(2)) == pytest.approx(5.0, rel=1e-15)
+    # invariant under a common scale, and not symmetric in its arguments
+    assert I.rel_fro(7.0 * np.array([1.0, 2.0]), 7.0 * np.array([1.0, 3.0])) == pytest.approx(1.0 / np.sqrt(10.0))
+    assert I.rel_fro(np.array([1.0, 3.0]), np.array([1.0, 2.0])) == pytest.approx(1.0 / np.sqrt(5.0))
