@@ -10,10 +10,13 @@ distinct shapes of different cost (on the synthetic 1B list a 2048 x 5632
 matrix costs 1.23 times a 2048 x 2048 one), so equal counts per rank would
 not balance.
 
-The exchange is one broadcast per matrix from the rank that owns it, on the
-process group's device (NCCL for CUDA tensors, gloo on CPU); nothing else
-crosses ranks.  Only host-side logic lives here: the compute is the caller's
-call into the library.
+The exchange is one all-gather over the process group (NCCL for CUDA
+tensors, gloo on CPU): each rank packs its share's results into one flat
+buffer, every rank receives every rank's buffer, and unpacks the matrices it
+did not compute.  The layout of the buffers follows from the list's shapes
+and the partition, which every rank knows, so nothing else crosses ranks.
+Only host-side logic lives here: the compute is the caller's call into the
+library.
 """
 
 
@@ -51,17 +54,48 @@ def owner_table(parts):
     return owner
 
 
+def pack_layout(parts, numels):
+    """Flat exchange layout: rank r's buffer holds the matrices of parts[r]
+    back to back in ascending index order, and every buffer is padded to the
+    largest share's length.  Returns (that length in elements,
+    {matrix: (rank, element offset)})."""
+    offs = {}
+    seg = 0
+    for r, p in enumerate(parts):
+        o = 0
+        for i in p:
+            offs[i] = (r, o)
+            o += numels[i]
+        seg = max(seg, o)
+    if len(offs) != len(numels):
+        raise ValueError("the shares do not cover the list")
+    return seg, offs
+
+
 def sharded_orthogonalize(run_local, outs, parts, rank, dist=None, group=None):
     """Run this rank's share, then exchange the results.
 
     run_local(indices) writes outs[i] for every i of this rank's share (one
     library call over those matrices).  Afterwards every rank holds all of
-    outs: each matrix is broadcast from its owner.  dist is
-    torch.distributed (None or a world of one: no exchange)."""
+    outs (tensors of one dtype on one device): one all-gather of the ranks'
+    packed results.  dist is torch.distributed (None or a world of one: no
+    exchange)."""
     run_local(parts[rank])
     if dist is None or len(parts) == 1:
         return outs
-    owner = owner_table(parts)
-    for i, r in enumerate(owner):
-        dist.broadcast(outs[i], src=r, group=group)
+    import torch
+
+    world = len(parts)
+    seg, offs = pack_layout(parts, [o.numel() for o in outs])
+    ref = outs[0]
+    send = torch.zeros(seg, dtype=ref.dtype, device=ref.device)
+    for i in parts[rank]:
+        _, o = offs[i]
+        send[o:o + outs[i].numel()].copy_(outs[i].reshape(-1))
+    recv = torch.empty(world * seg, dtype=ref.dtype, device=ref.device)
+    dist.all_gather_into_tensor(recv, send, group=group)
+    for i, (r, o) in offs.items():
+        if r != rank:
+            base = r * seg + o
+            outs[i].copy_(recv[base:base + outs[i].numel()].view(outs[i].shape))
     return outs

@@ -66,6 +66,16 @@ def test_lpt_partition_small():
         S.lpt_partition([1], 0)
 
 
+def test_pack_layout():
+    S = _shard()
+    # shares [0, 3] and [1, 2, 4] of matrices with 6, 4, 10, 2, 3 elements
+    seg, offs = S.pack_layout([[0, 3], [1, 2, 4]], [6, 4, 10, 2, 3])
+    assert seg == 17   # rank 1 packs 4 + 10 + 3
+    assert offs == {0: (0, 0), 3: (0, 6), 1: (1, 0), 2: (1, 4), 4: (1, 14)}
+    with pytest.raises(ValueError):
+        S.pack_layout([[0], [2]], [1, 1, 1])
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))
@@ -75,9 +85,12 @@ def _free_port():
 
 
 def _mats():
+    """Mixed shapes, wide and tall, of different element counts (the shares'
+    packed buffers differ in length)."""
     import synth
 
-    return [synth.gaussian(40 + i, r, c) for i, (r, c) in enumerate([(16, 32), (32, 16), (24, 24), (8, 40), (20, 30)])]
+    return [synth.gaussian(40 + i, r, c)
+            for i, (r, c) in enumerate([(16, 32), (32, 16), (24, 24), (8, 40), (20, 30), (36, 12), (9, 9)])]
 
 
 def _worker(rank, world, port, q):
@@ -129,4 +142,4 @@ def test_sharded_exchange_two_gloo_ranks():
     for rank, ok, done, mine in out:
         assert ok                      # every rank ends with every result
         assert done == sorted(mine)    # and computed only its own share
-    assert sorted(out[0][2] + out[1][2]) == list(range(5))
+    assert sorted(out[0][2] + out[1][2]) == list(range(7))
