@@ -1782,11 +1782,26 @@ ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc
   else if (which == 5) {
     *ptr = static_cast<uint8_t*>(workspace) + ly.off_rows + static_cast<size_t>(index) * kRowSlots * sizeof(float);
     *ld = kRowSlots;
+  } else if (which == 6) {
+    *ptr = static_cast<uint8_t*>(workspace) + ly.off_scal + static_cast<size_t>(index) * sizeof(MatScalars);
+    *ld = sizeof(MatScalars) / sizeof(double);
   }
   else return fail(IFNSO_ERR_INVALID_ARG, "which = %d", which);
   if (!*ptr) return fail(IFNSO_ERR_INVALID_ARG, "buffer %d is not used by this plan", which);
   return IFNSO_OK;
 }
+
+namespace {
+// Descriptor buffers of ifnso_frobenius_norm2, one per device.
+struct NormDesc {
+  MatInfo* d = nullptr;
+  int cap = 0;
+  cudaEvent_t done = nullptr;  // recorded after the last launch that read d
+};
+constexpr int kNormDevices = 64;
+std::mutex g_norm_mu;
+NormDesc g_norm_desc[kNormDevices];
+}  // namespace
 
 ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dtype, double* norm2_out,
                                    ifnso_stream_t stream_) {
@@ -1803,21 +1818,23 @@ ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dt
   int dev = 0, sms = 0;
   IFNSO_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   IFNSO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  if (dev < 0 || dev >= kNormDevices) return fail(IFNSO_ERR_UNSUPPORTED, "device %d", dev);
   IFNSO_CUDA(cudaMemsetAsync(norm2_out, 0, batch->count * sizeof(double), stream), "reset");
-  // one launch per matrix with its description passed through a small device copy
-  // kept in static storage of this entry point (grown on demand)
-  static MatInfo* d_mi = nullptr;
-  static int d_cap = 0;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lk(mu);
-  if (d_cap < batch->count) {
-    if (d_mi) {
-      cudaStreamSynchronize(stream);
-      cudaFree(d_mi);
-    }
-    IFNSO_CUDA(cudaMalloc(&d_mi, batch->count * sizeof(MatInfo)), "cudaMalloc");
-    d_cap = batch->count;
+  // The matrices' descriptions go to a device buffer of this entry point, one
+  // per device (grown on demand).  A call waits until the previous call's
+  // kernel on that device has read the buffer before overwriting it, so
+  // calls on different streams or host threads do not race on it.
+  std::lock_guard<std::mutex> lk(g_norm_mu);
+  NormDesc& nd = g_norm_desc[dev];
+  if (nd.done) IFNSO_CUDA(cudaEventSynchronize(nd.done), "cudaEventSynchronize");
+  if (nd.cap < batch->count) {
+    if (nd.d) cudaFree(nd.d);
+    nd.d = nullptr;
+    nd.cap = 0;
+    IFNSO_CUDA(cudaMalloc(&nd.d, batch->count * sizeof(MatInfo)), "cudaMalloc");
+    nd.cap = batch->count;
   }
+  if (!nd.done) IFNSO_CUDA(cudaEventCreateWithFlags(&nd.done, cudaEventDisableTiming), "cudaEventCreate");
   std::vector<MatInfo> h(batch->count);
   for (int i = 0; i < batch->count; ++i) {
     memset(&h[i], 0, sizeof(MatInfo));
@@ -1826,10 +1843,11 @@ ifnso_status ifnso_frobenius_norm2(const ifnso_batch_desc* batch, ifnso_dtype dt
     h[i].cols = shp[i].cols;
     h[i].ld = shp[i].ld;
   }
-  IFNSO_CUDA(cudaMemcpyAsync(d_mi, h.data(), h.size() * sizeof(MatInfo), cudaMemcpyHostToDevice, stream), "upload");
-  IFNSO_CUDA(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
+  // (a pageable source: the copy has taken the bytes when the call returns)
+  IFNSO_CUDA(cudaMemcpyAsync(nd.d, h.data(), h.size() * sizeof(MatInfo), cudaMemcpyHostToDevice, stream), "upload");
   int gx = std::max(1, std::min(1024, 16 * sms / std::max(1, batch->count)));
-  IFNSO_CUDA(launch_norm2(d_mi, batch->count, dtype == IFNSO_BF16, norm2_out, 1, gx, stream), "norm");
+  IFNSO_CUDA(launch_norm2(nd.d, batch->count, dtype == IFNSO_BF16, norm2_out, 1, gx, stream), "norm");
+  IFNSO_CUDA(cudaEventRecord(nd.done, stream), "cudaEventRecord");
   return IFNSO_OK;
 }
 

@@ -63,3 +63,22 @@ def sym_upper(G, block=256):
     low = bi > bj
     G[low] = G.T[low]
     return G
+
+
+def block_max_rel(a, b, block=256):
+    """Largest per-block relative Frobenius error over the block x block tiles
+    of the output: ||a_t - b_t||_F / max(||b_t||_F, ||b||_F sqrt(|t| / |b|)).
+    A tile whose reference is smaller than the average tile is measured
+    against the average tile's norm, so that a wrong output tile (1/352 of a
+    2048 x 5632 matrix) shows its own error instead of being averaged away."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    tot = np.linalg.norm(b)
+    worst = 0.0
+    for i in range(0, b.shape[0], block):
+        for j in range(0, b.shape[1], block):
+            bt = b[i:i + block, j:j + block]
+            at = a[i:i + block, j:j + block]
+            den = max(np.linalg.norm(bt), tot * np.sqrt(bt.size / b.size), 1e-300)
+            worst = max(worst, float(np.linalg.norm(at - bt) / den))
+    return worst

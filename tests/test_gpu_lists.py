@@ -3,27 +3,39 @@ times: every matrix of the synthetic 1B (168) or 7B (224) list goes through one
 ifnso_orthogonalize call with the bench's defaults (L = 14, AUTO precision,
 autotuned MMA modes, the GPU learner's coefficients).  A deterministic sample
 (first, middle and last layer; every oriented shape) is compared with Algorithm 1
-evaluated in FP64 on the same BF16 input, regenerated bit for bit on the CPU."""
+evaluated in FP64 on the same BF16 input, regenerated bit for bit on the CPU,
+over the whole matrix and per 256 x 256 output tile.
+
+The 5-step quintic Newton-Schulz baseline is checked the same way on one
+matrix of each 1B shape, and the claim the benchmark rests on -- IFNSO at
+L = 14 is at least as close to U V^T as NS5 -- is checked on the GPU outputs
+themselves."""
 import numpy as np
 import pytest
 
 import synth
 from oracle import ifnso as O
-from tests.gpu_util import lib, rel, to_np
+from oracle import ns as ON
+from tests.gpu_util import block_max_rel, lib, rel, to_np
 
 pytestmark = pytest.mark.gpu
 
+# BF16 tolerance of IFNSO (whole matrix), and per 256 x 256 tile
+TOL = 2e-2
+TOL_TILE = 5e-2
+# NS5 in BF16 stores X, S = X X^T and B = b S + c S^2 in BF16 at each of its 5
+# steps; the quintic's slope a = 3.4445 at small singular values amplifies the
+# rounding of the early steps.  Those roundings alone, emulated in FP64 on the
+# 1B shapes (2048^2 and 2048 x 5632 low-rank + noise), put the result 2.56e-2
+# and 2.57e-2 (relative Frobenius) from the FP64 iteration, 2.62e-2 and 2.65e-2
+# on the worst 256 x 256 tile.  The baseline's tolerance is twice that.
+TOL_NS5 = 5e-2
+TOL_NS5_TILE = 6e-2
 
-@pytest.mark.parametrize("workload,samples", [
-    ("muon_1b", [0, 4, 6, 84, 88, 90, 161, 165, 167]),   # q, gate, down of layers 0, 12, 23
-    ("muon_7b", [0, 6]),                                   # q and down of layer 0
-])
-def test_list_in_bench_configuration(workload, samples):
-    import torch
 
+def run_list(F, torch, workload):
     import bench
 
-    F = lib()
     wl = bench.WORKLOADS[workload]
     shapes = bench.workload_list(wl)
     L = wl["L"]
@@ -35,6 +47,18 @@ def test_list_in_bench_configuration(workload, samples):
     batch = F.Batch(xs)
     w = F.learn_coefficients(L)
     coef = np.r_[1.0, w]
+    return shapes, L, xs, ys, plan, batch, w, coef
+
+
+@pytest.mark.parametrize("workload,samples", [
+    ("muon_1b", [0, 4, 6, 84, 88, 90, 161, 165, 167]),   # q, gate, down of layers 0, 12, 23
+    ("muon_7b", [0, 6]),                                   # q and down of layer 0
+])
+def test_list_in_bench_configuration(workload, samples):
+    import torch
+
+    F = lib()
+    shapes, L, xs, ys, plan, batch, w, coef = run_list(F, torch, workload)
     plan.autotune(batch, coef, ys, reps=1)
     for y in ys:
         y.fill_(float("nan"))
@@ -42,11 +66,56 @@ def test_list_in_bench_configuration(workload, samples):
     torch.cuda.synchronize()
     st, _, _ = plan.device_status(len(xs))
     assert np.all(st == 0)
-    alpha, beta = synth.lowrank_constants()
     for i in samples:
         _, r, c = shapes[i]
         M = synth.bf16_bits_to_f64(synth.lowrank_noise_bf16(i, r, c))
         assert np.array_equal(to_np(xs[i]), M)  # the GPU generator matches synth/
-        err = rel(to_np(ys[i]), O.ifnso_alg1(M, w))
-        print(f"{workload} matrix {i} ({r}x{c}): relative error {err:.2e}")
-        assert err < 2e-2
+        ref = O.ifnso_alg1(M, w)
+        Y = to_np(ys[i])
+        err = rel(Y, ref)
+        tile = block_max_rel(Y, ref)
+        print(f"{workload} matrix {i} ({r}x{c}): relative error {err:.2e}, worst 256x256 tile {tile:.2e}")
+        assert err < TOL
+        assert tile < TOL_TILE
+
+
+def test_ns5_and_equal_polar_error_on_1b_shapes():
+    """One matrix of each 1B shape (q 2048^2, gate 2048 x 5632, down 5632 x 2048
+    of layer 0) in one ns_iterate call of the whole list and one IFNSO call:
+    NS5 against the FP64 quintic iteration; the GPU outputs' distances to
+    U V^T against the oracle's, and IFNSO's against NS5's."""
+    import torch
+
+    import bench
+
+    F = lib()
+    shapes, L, xs, ys, plan, batch, w, coef = run_list(F, torch, "muon_1b")
+    zs = [torch.empty_like(x) for x in xs]
+    plan.orthogonalize(batch, coef, ys)
+    plan.ns_iterate(batch, bench.MUON_ABC, 5, zs)
+    torch.cuda.synchronize()
+    st, _, _ = plan.device_status(len(xs))
+    assert np.all(st == 0)
+    for i in (0, 4, 6):
+        _, r, c = shapes[i]
+        M = to_np(xs[i])
+        h = min(r, c)
+        ref_ns = ON.ns_quintic(M, 5)
+        Z = to_np(zs[i])
+        Y = to_np(ys[i])
+        err = rel(Z, ref_ns)
+        tile = block_max_rel(Z, ref_ns)
+        P = O.polar_factor(M)
+        d_ns_gpu = np.linalg.norm(Z - P) / np.sqrt(h)
+        d_ns_ref = np.linalg.norm(ref_ns - P) / np.sqrt(h)
+        d_if_gpu = np.linalg.norm(Y - P) / np.sqrt(h)
+        d_if_ref = np.linalg.norm(O.ifnso_alg1(M, w) - P) / np.sqrt(h)
+        print(f"matrix {i} ({r}x{c}): NS5 rel err {err:.2e}, worst tile {tile:.2e}; ||Y - UV^T||_F/sqrt(h): "
+              f"NS5 GPU {d_ns_gpu:.4f} oracle {d_ns_ref:.4f}, IFNSO L={L} GPU {d_if_gpu:.4f} oracle {d_if_ref:.4f}")
+        assert err < TOL_NS5
+        assert tile < TOL_NS5_TILE
+        # the rounding of either GPU path moves its distance to U V^T by under 1%
+        assert abs(d_ns_gpu - d_ns_ref) <= 0.01 * d_ns_ref
+        assert abs(d_if_gpu - d_if_ref) <= 0.01 * d_if_ref
+        # equal or lower polar error than the baseline, on the GPU outputs themselves
+        assert d_if_gpu <= d_ns_gpu
