@@ -14,7 +14,12 @@ from tests.gpu_util import coeffs, lib, rel, to_dev, to_np
 pytestmark = pytest.mark.gpu
 
 
-def test_stalled_pipeline_times_out_and_context_survives():
+@pytest.mark.parametrize("cta_group", [1, 2])
+def test_stalled_pipeline_times_out_and_context_survives(cta_group):
+    """cta_group 1: each CTA's own waits run out.  cta_group 2: the even CTA
+    never arms its stage barriers, so the odd CTA's copies (which complete on
+    the even CTA's barrier) never complete a phase; both CTAs' waits run out
+    and the pair meets at its final cluster barriers."""
     import torch
 
     F = lib()
@@ -22,6 +27,7 @@ def test_stalled_pipeline_times_out_and_context_survives():
     y = torch.empty(x.shape, dtype=x.dtype, device="cuda")
     w = coeffs(4)
     plan = F.Plan(256, 512, "bf16", L=4)
+    plan.set(F.IFNSO_OPT_CTA_GROUP, cta_group)
     plan.set(F.IFNSO_OPT_WAIT_LIMIT_MS, 100)
     plan.set(F.IFNSO_OPT_INJECT_STALL, 1)
     b = F.Batch([x])

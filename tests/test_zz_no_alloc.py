@@ -42,6 +42,9 @@ def test_static_norm_matches_allocating_entry_point(dtype):
         ref = F.frobenius_norm2(mats).cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.allclose(got, ref, rtol=1e-5, atol=0.0), (got, ref)
+        # and the plain FP64 sum of squares of the same stored values
+        exact = np.array([float(np.sum(m.double().cpu().numpy() ** 2)) for m in mats])
+        assert np.allclose(got, exact, rtol=1e-5, atol=0.0), (got, exact)
 
 
 def test_static_norm_rejects_oversized_batch():
