@@ -6,12 +6,32 @@ import os
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+def _depth(v, key):
+    """Smallest L whose IFNSO distance to U V^T is at or below NS5's on every
+    swept matrix of the shape (and on the first matrix's full NS5 iteration)."""
+    sw = v["sweep"]
+    return min(L for L in range(4, 21)
+               if v[f"{key}{L}"] <= v["ns5"]
+               and all(a <= b for a, b in zip(sw[f"{key}{L}"], sw["ns5_spectral"])))
+
+
+def test_equal_polar_sweep_is_consistent():
+    with open(os.path.join(ROOT, "tests", "golden", "equal_polar.json")) as f:
+        eq = json.load(f)
+    for v in eq.values():
+        sw = v["sweep"]
+        assert len(sw["seeds"]) == 8
+        # the first swept matrix is the one written out in full; its spectral NS5
+        # distance agrees with the NS5 iteration evaluated as a matrix
+        assert sw["seeds"][0] == v["seed"]
+        assert abs(v["ns5_spectral"] - v["ns5"]) <= 1e-6 * v["ns5"]
+        assert sw["ifnso_L14"][0] == v["ifnso_L14"]
+
+
 def test_bench_depth_matches_equal_polar_analysis():
     with open(os.path.join(ROOT, "tests", "golden", "equal_polar.json")) as f:
         eq = json.load(f)
-    chosen = set()
-    for shape, v in eq.items():
-        chosen.add(min(L for L in range(4, 21) if v[f"ifnso_L{L}"] <= v["ns5"]))
+    chosen = {_depth(v, "ifnso_L") for v in eq.values()}
     spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
@@ -23,7 +43,7 @@ def test_gelfand2_depth_matches_equal_polar_analysis():
     # reaches NS5's distance to U V^T on every shape of the list
     with open(os.path.join(ROOT, "tests", "golden", "equal_polar.json")) as f:
         eq = json.load(f)
-    chosen = {min(L for L in range(4, 21) if v[f"ifnso_gelfand2_L{L}"] <= v["ns5"]) for v in eq.values()}
+    chosen = {_depth(v, "ifnso_gelfand2_L") for v in eq.values()}
     spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
