@@ -407,9 +407,10 @@ def run_muon(args):
 def run_shard(args):
     """Strong scaling over N ranks: every rank holds the same list (seeds
     0..n-1), orthogonalizes the share that greedy LPT on Algorithm 1's
-    nominal FLOPs gives it, and the results are then broadcast from their
-    owners, so that every rank ends with all of them (a replicated Muon
-    update).  The timed step is the library call plus the exchange."""
+    nominal FLOPs gives it, and the results are then exchanged by one
+    all-gather of the ranks' packed results, so that every rank ends with all
+    of them (a replicated Muon update).  The timed step is the library call
+    plus the exchange."""
     import numpy as np
     import torch
 
@@ -474,8 +475,8 @@ def run_shard(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": args.workload + ": " + wl["desc"], "L": L,
-                       "parallelism": f"list sharded over {world} ranks (greedy LPT on FLOPs), results broadcast "
-                                      "from their owners",
+                       "parallelism": f"list sharded over {world} ranks (greedy LPT on FLOPs), results "
+                                      "exchanged by one all-gather of the packed shares",
                        "matrices_per_rank": [len(p) for p in parts],
                        "flop_share_max_over_mean": max(loads) / (sum(loads) / len(loads))},
         }), flush=True)
@@ -521,7 +522,9 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload + ": " + wl["desc"], "L": L, "parallelism": "host cores"},
+        "config": {"workload": args.workload + ": " + wl["desc"], "L": L, "parallelism": "host cores",
+                   "timing": "projected: each step times the FP64 oracle on one matrix of every distinct "
+                             "shape; ms_per_step and value are the whole list's, projected from that sample"},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
@@ -529,6 +532,28 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def averaged_pass_times(plan, step, k):
+    """Per-pass milliseconds of `step` (a call, or a graph replay, of a plan
+    with IFNSO_OPT_TIMING on) averaged over k runs, each read back after a
+    synchronize: the pass events are recorded inside the step, so they hold
+    one step's passes at a time.  Returns (array, runs averaged)."""
+    import numpy as np
+    import torch
+
+    plan.pass_times()
+    acc, n = None, 0
+    for _ in range(k):
+        step()
+        torch.cuda.synchronize()
+        pm, c = plan.pass_times()
+        if c < 1:
+            continue
+        pm = np.asarray(pm, dtype=np.float64) / c
+        acc = pm if acc is None else acc + pm
+        n += 1
+    return (acc / n if n else np.zeros(0)), n
 
 
 def main():
@@ -660,8 +685,13 @@ def main():
     launches = ifnso_launches * args.steps if ifnso_launches is not None else F.launch_count() - n0
     ms_total = max_over_ranks(e0.elapsed_time(e1))
     clk = clocks.stop()
-    pass_ms, calls = plan.pass_times()
     ms_step = ms_total / args.steps
+    # Per-pass durations.  The library's pass events are recorded inside the
+    # step (graph record nodes, or eager records), so they hold one step's
+    # passes at a time: after the timed region, K more steps run, each read
+    # back after a synchronize, and every pass is averaged over those K steps.
+    pass_ms, n_pass_steps = averaged_pass_times(plan, ifnso_step, args.steps)
+    calls = 1
     value = whole_job_rate(world, n, args.steps, ms_total)
     fl = sum(flops_ifnso(h, w, L) for h, w in hw)
     tflops = world * fl * args.steps / (ms_total / 1000.0) / 1e12
@@ -712,11 +742,16 @@ def main():
                 "executed_tflops": sq_exec / (sq_launch_ms / 1000.0) / 1e12,
                 "peak_source": f"bf16_tflops_sustained ({peak_src})",
                 "squarings": {k: {"launches": len(v), "ms": float(np.mean(v))} for k, v in sorted(variants.items())},
-                "pass_ms_per_step": per_step}
+                "pass_ms_per_step": per_step,
+                "pass_timing": f"CUDA events on the launching stream around every pass, averaged over "
+                               f"{n_pass_steps} steps run after the timed region (each read after a synchronize)",
+                "pass_sum_ms": float(sum(per_step)),
+                "pass_sum_over_step": float(sum(per_step)) / ms_step}
 
     # 5-step quintic Newton-Schulz on the same list
     nsplan = F.Plan(hmax, wmax, "bf16", L=1)
     nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
+    nsplan.set(F.IFNSO_OPT_TIMING, 1)
     nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
     zs = [torch.empty_like(x) for x in xs]
     for _ in range(max(args.warmup, 3)):
@@ -733,6 +768,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     ns_ms = max_over_ranks(e0.elapsed_time(e1))
+    ns_pass, _ = averaged_pass_times(nsplan, ns_step, args.steps)
     ns_value = whole_job_rate(world, n, args.steps, ns_ms)
     ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
     del nsws, zs
@@ -804,7 +840,9 @@ def main():
                                  "gelfand2": "X = A / ||(A A^T)^2||_F^(1/4) (Gelfand, q = 2)"}[args.scale]},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
-                    "ifnso_over_ns5": value / ns_value},
+                    "ifnso_over_ns5": value / ns_value,
+                    "pass_ms_per_step": [float(x) for x in ns_pass],
+                    "passes": "norm and scalars, then per step: Gram S = X X^T, B = b S + c S^2, X <- a X + B X"},
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
