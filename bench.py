@@ -34,17 +34,39 @@ WORKLOADS = {
     "muon_1b": {
         "desc": "synthetic 1B transformer weight-gradient list: 24 layers x {Q,K,V,O 2048x2048; gate, up "
                 "2048x5632; down 5632x2048}, 168 BF16 rank-32 + noise (10:1) matrices, seeds 0..167",
-        "list": "list_1b", "L": 14, "L_gelfand2": 13,
+        "kind": "lowrank", "list": "list_1b", "L": 14, "L_gelfand2": 13,
     },
     "muon_1b_4l": {
         "desc": "first 4 layers of the synthetic 1B list (28 BF16 matrices, 412 MB of input > L2): the "
                 "small case used for ncu captures",
-        "list": "list_1b_4l", "L": 14, "L_gelfand2": 13,
+        "kind": "lowrank", "list": "list_1b_4l", "L": 14, "L_gelfand2": 13,
     },
     "muon_7b": {
         "desc": "synthetic 7B transformer weight-gradient list: 32 layers x {4 x 4096x4096; gate, up "
                 "4096x14336; down 14336x4096}, 224 BF16 rank-32 + noise (10:1) matrices, seeds 0..223",
-        "list": "list_7b", "L": 14, "L_gelfand2": 13,
+        "kind": "lowrank", "list": "list_7b", "L": 14, "L_gelfand2": 13,
+    },
+    "config1_f32": {
+        "desc": "one 256x512 FP32 matrix of i.i.d. N(0,1) entries (seed 0), L = 4 (exponents {1, 2, 4, 8}), "
+                "the FP32 path",
+        "kind": "gaussian", "shapes": [(256, 512, 0)], "dtype": "f32", "L": 4, "L_gelfand2": 4,
+    },
+    "config2": {
+        "desc": "the precision-path pair in one call: BF16 4096x4096 (seed 0) and 4096x11008 (seed 1), "
+                "U diag(sigma) V^T with Haar U, V and sigma = 1e3 * 10^U(-4, 0)",
+        "kind": "spectral", "shapes": [(4096, 4096, 0), (4096, 11008, 1)], "L": 14, "L_gelfand2": 13,
+    },
+    "heldout_2k": {
+        "desc": "the 2000 shapes of the coefficient network's held-out set (seeds 1000000..1001999: h ~ "
+                "U{64..1024}, w = round(h U[1, 4])), BF16 rank-32 + noise (10:1) entries from the GPU "
+                "generator (the entries do not change the work), L = 4 (K = 5 slots)",
+        "kind": "heldout", "n": 2000, "L": 4, "L_gelfand2": 4,
+    },
+    "table1": {
+        "desc": "the Table 1 shapes 128x128, 128x512, 128x1024 (Sec. 3.4), 10 N(0,1) BF16 matrices of "
+                "each (seeds 0..9), 30 in one call, L = 14",
+        "kind": "gaussian", "shapes": [(128, c, s) for c in (128, 512, 1024) for s in range(10)], "L": 14,
+        "L_gelfand2": 13,
     },
 }
 
@@ -100,11 +122,25 @@ def flops_ns5(h, w, steps=5):
 
 
 def workload_list(wl):
+    """[(name, rows, cols)] of the workload's matrices, in call order."""
     import synth
 
-    if wl["list"] == "list_1b_4l":
-        return synth.transformer_list(4, 2048, 5632)
-    return getattr(synth, wl["list"])()
+    kind = wl.get("kind", "lowrank")
+    if kind == "lowrank":
+        if wl["list"] == "list_1b_4l":
+            return synth.transformer_list(4, 2048, 5632)
+        return getattr(synth, wl["list"])()
+    if kind == "heldout":
+        out = []
+        for i in range(wl["n"]):
+            h, w, _, _ = synth.mlp_spectrum(1000000 + i)
+            out.append((f"heldout{i}", h, w))
+        return out
+    return [(f"m{i}", r, c) for i, (r, c, _) in enumerate(wl["shapes"])]
+
+
+def workload_dtype(wl):
+    return wl.get("dtype", "bf16")
 
 
 def oriented(r, c):
@@ -205,50 +241,102 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(F, torch, shapes, seed0, device):
+def host_matrix(wl, i):
+    """Matrix i of a gaussian or spectral workload, FP64, from synth/ (as the
+    parity tests build it)."""
     import synth
 
-    alpha, beta = synth.lowrank_constants()
+    r, c, seed = wl["shapes"][i]
+    if wl["kind"] == "gaussian":
+        return synth.gaussian(seed, r, c)
+    h = min(r, c)
+    M = synth.spectral(seed, r, c, synth.loguniform_sigma(seed, h))
+    return synth.round_bf16(M) if workload_dtype(wl) == "bf16" else M
+
+
+def like(torch, x, pinned=False):
+    """An uninitialised tensor with x's shape and row pitch (BF16 rows are
+    padded to a multiple of 8 elements), on x's device or page-locked on the host."""
+    r, c = x.shape
+    ld = x.stride(0)
+    if pinned:
+        return torch.empty((r, ld), dtype=x.dtype, pin_memory=True)[:, :c]
+    return torch.empty((r, ld), dtype=x.dtype, device=x.device)[:, :c]
+
+
+def make_inputs(F, torch, shapes, seed0, device, wl=None):
+    """Device inputs of the workload.  Low-rank lists (and the held-out
+    shapes) come from the library's Philox generator on the GPU, seeds
+    seed0 + i; gaussian and spectral matrices from synth/ on the host."""
+    import synth
+
+    wl = wl or WORKLOADS["muon_1b"]
+    kind = wl.get("kind", "lowrank")
     xs = []
-    for i, (_, r, c) in enumerate(shapes):
-        x = torch.empty((r, c), dtype=torch.bfloat16, device=device)
-        F.synth_lowrank_bf16(x, seed0 + i, float(alpha), float(beta))
-        xs.append(x)
+    if kind in ("lowrank", "heldout"):
+        alpha, beta = synth.lowrank_constants()
+        for i, (_, r, c) in enumerate(shapes):
+            ld = (c + 7) // 8 * 8
+            buf = torch.empty((r, ld), dtype=torch.bfloat16, device=device)
+            x = buf[:, :c]
+            F.synth_lowrank_bf16(x, seed0 + i, float(alpha), float(beta))
+            xs.append(x)
+        return xs
+    dt = torch.float32 if workload_dtype(wl) == "f32" else torch.bfloat16
+    for i in range(len(shapes)):
+        xs.append(torch.tensor(host_matrix(wl, i), dtype=torch.float32).to(device=device, dtype=dt))
     return xs
 
 
-def cpu_oracle_sample(shapes, L, budget_s=20.0):
-    """Time the FP64 oracle (Algorithm 1) on one matrix of each distinct shape;
-    project the time of the whole list.  Returns (matrices/s, sample text, cores)."""
+def oracle_input(wl, shapes, i, seed0=0):
+    """Matrix i of the workload as the FP64 oracle sees it (the same values
+    the device computes on)."""
+    import synth
+
+    if wl.get("kind", "lowrank") in ("lowrank", "heldout"):
+        _, r, c = shapes[i]
+        return synth.bf16_bits_to_f64(synth.lowrank_noise_bf16(seed0 + i, r, c))
+    return host_matrix(wl, i)
+
+
+def cpu_oracle_sample(wl, shapes, L, budget_s=20.0):
+    """Time the FP64 oracle (Algorithm 1) on one matrix of each distinct
+    shape, in list order, until about budget_s seconds are spent; project the
+    time of the whole list (per shape when every distinct shape was timed,
+    else by Algorithm 1's FLOPs).  Returns (matrices/s, sample text, cores)."""
     import numpy as np
 
-    import synth
     from oracle import coeffs as OC
     from oracle import ifnso as O
 
     w = OC.complete(np.zeros(L - 1), L)  # timing does not depend on the coefficient values
-    distinct = {}
-    for i, (nm, r, c) in enumerate(shapes):
-        distinct.setdefault((r, c), []).append(i)
-    per_shape = {}
+    first = {}
+    for i, (_, r, c) in enumerate(shapes):
+        first.setdefault((r, c), i)
+    timed = {}
     t_used = 0.0
-    for (r, c), idx in distinct.items():
-        M = synth.bf16_bits_to_f64(synth.lowrank_noise_bf16(idx[0], r, c))
+    for (r, c), i in first.items():
+        M = oracle_input(wl, shapes, i)
         t0 = time.perf_counter()
         O.ifnso_alg1(M, w)
         dt = time.perf_counter() - t0
-        per_shape[(r, c)] = dt
+        timed[(r, c)] = dt
         t_used += dt
         if t_used > budget_s:
             break
-    total = 0.0
-    for (r, c), idx in distinct.items():
-        if (r, c) not in per_shape:
-            return None, "sample incomplete", os.cpu_count()
-        total += per_shape[(r, c)] * len(idx)
+    fl = {k: flops_ifnso(*oriented(*k), L) for k in first}
+    if len(timed) == len(first):
+        total = sum(timed[(r, c)] for _, r, c in shapes)
+        how = f"list time projected per shape over {len(shapes)} matrices"
+    else:
+        rate = sum(fl[k] for k in timed) / sum(timed.values())
+        total = sum(fl[(r, c)] for _, r, c in shapes) / rate
+        how = (f"{len(timed)} of {len(first)} distinct shapes timed; list time projected by Algorithm 1's "
+               f"FLOPs over {len(shapes)} matrices")
+    shown = list(timed.items())[:6]
     sample = ("FP64 oracle (Algorithm 1, numpy) on one matrix of each distinct shape "
-              + ", ".join(f"{r}x{c}: {t:.2f}s" for (r, c), t in per_shape.items())
-              + f"; list time projected over {len(shapes)} matrices")
+              + ", ".join(f"{r}x{c}: {t:.2f}s" for (r, c), t in shown)
+              + (", ..." if len(timed) > len(shown) else "") + f"; {how}")
     return len(shapes) / total, sample, os.cpu_count()
 
 
@@ -489,10 +577,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import synth
+    import numpy as np
+
     from oracle import coeffs as OC
     from oracle import ifnso as O
-    import numpy as np
 
     wl = WORKLOADS[args.workload]
     shapes = workload_list(wl)
@@ -501,9 +589,9 @@ def run_reference(args):
     distinct = {}
     for i, (nm, r, c) in enumerate(shapes):
         distinct.setdefault((r, c), []).append(i)
-    keys = list(distinct)
-    mats = {k: synth.bf16_bits_to_f64(synth.lowrank_noise_bf16(distinct[k][0], *k)) for k in keys}
-    # one step = one matrix of every distinct shape (a bounded sample of the list)
+    # one step = one matrix of each of (at most 8) distinct shapes: a bounded sample of the list
+    keys = list(distinct)[:8]
+    mats = {k: oracle_input(wl, shapes, distinct[k][0]) for k in keys}
     times = {k: [] for k in keys}
     for s in range(args.warmup + max(1, args.steps)):
         for k in keys:
@@ -512,12 +600,19 @@ def run_reference(args):
             dt = time.perf_counter() - t0
             if s >= args.warmup:
                 times[k].append(dt)
-    list_time = sum(float(np.mean(times[k])) * len(distinct[k]) for k in keys)
+    mean = {k: float(np.mean(times[k])) for k in keys}
+    if len(keys) == len(distinct):
+        list_time = sum(mean[k] * len(distinct[k]) for k in keys)
+        how = "per shape"
+    else:
+        rate = sum(flops_ifnso(*oriented(*k), L) for k in keys) / sum(mean.values())
+        list_time = sum(flops_ifnso(*oriented(r, c), L) for _, r, c in shapes) / rate
+        how = "by Algorithm 1's FLOPs"
     value = len(shapes) / list_time
     step_ms = 1000.0 * list_time  # the whole list, projected from the sample
-    sample = (f"each step: FP64 oracle (Algorithm 1, numpy) on one matrix of every distinct shape "
-              + ", ".join(f"{r}x{c}: {float(np.mean(times[k])):.2f}s" for (r, c), k in zip(keys, keys))
-              + f"; the time of the {len(shapes)}-matrix list is projected from it (ms_per_step)")
+    sample = (f"each step: FP64 oracle (Algorithm 1, numpy) on one matrix of {len(keys)} distinct shapes "
+              + ", ".join(f"{r}x{c}: {mean[(r, c)]:.2f}s" for (r, c) in keys)
+              + f"; the time of the {len(shapes)}-matrix list is projected from it {how} (ms_per_step)")
     line = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -600,8 +695,9 @@ def main():
     hmax = max(h for h, _ in hw)
     wmax = max(w for _, w in hw)
     seed0 = rank_seed0(rank)
-    xs = make_inputs(F, torch, shapes, seed0, device)
-    ys = [torch.empty_like(x) for x in xs]
+    dtype = workload_dtype(wl)
+    xs = make_inputs(F, torch, shapes, seed0, device, wl)
+    ys = [like(torch, x) for x in xs]
     batch = F.Batch(xs)
 
     # fixed coefficients from the library's own GPU learner (Sec. 2.3 / 3.1.1)
@@ -632,7 +728,7 @@ def main():
         mlp_info = {"train_spectra": n_train, "steps": args.mlp_steps, "batch": 512,
                     "loss_first_50": float(np.mean(curve[:50])), "loss_last_50": float(np.mean(curve[-50:]))}
 
-    plan = F.Plan(hmax, wmax, "bf16", L=L, precision=args.precision, scale=args.scale)
+    plan = F.Plan(hmax, wmax, dtype, L=L, precision=args.precision, scale=args.scale)
     plan.set(F.IFNSO_OPT_SPLIT_SQUARINGS, args.split_squarings)
     plan.set(F.IFNSO_OPT_TIMING, 1)
     plan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
@@ -640,7 +736,7 @@ def main():
     ws = F.Workspace(plan.workspace_bytes(batch), device=device)
     stream = torch.cuda.current_stream()
     tuned = None
-    if args.autotune and args.cta_group == 0:
+    if args.autotune and args.cta_group == 0 and dtype == "bf16":
         # untimed set-up: per-CTA vs CTA-pair MMAs per pass kind on this list
         modes = plan.autotune(batch, coef, ys, reps=2, ws=ws)
         tuned = dict(zip(["gram", "split_squaring", "plain_squaring", "product"], modes))
@@ -669,21 +765,41 @@ def main():
     torch.cuda.synchronize()
     plan.pass_times()
 
+    # Inputs smaller than twice L2 (129 MB) would stay cached from one step to
+    # the next: such workloads write a 512 MB buffer before every step and time
+    # the steps alone (a pair of events around each).
+    in_bytes = sum(x.numel() * x.element_size() for x in xs)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device) if in_bytes < (258 << 20) else None
+
+    def timed_steps(step, k):
+        """Milliseconds of k steps (max over ranks), the L2 flushed before each if needed."""
+        barrier()
+        torch.cuda.synchronize()
+        if flush is None:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            return max_over_ranks(a.elapsed_time(b))
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in evs:
+            flush.fill_(1)
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = F.launch_count()
-    e0.record(stream)
-    for _ in range(args.steps):
-        ifnso_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    ms_total = timed_steps(ifnso_step, args.steps)
     launches = ifnso_launches * args.steps if ifnso_launches is not None else F.launch_count() - n0
-    ms_total = max_over_ranks(e0.elapsed_time(e1))
     clk = clocks.stop()
     ms_step = ms_total / args.steps
     # Per-pass durations.  The library's pass events are recorded inside the
@@ -748,26 +864,51 @@ def main():
                 "pass_sum_ms": float(sum(per_step)),
                 "pass_sum_over_step": float(sum(per_step)) / ms_step}
 
+    kind = wl.get("kind", "lowrank")
+    if dtype == "f32":
+        # the FP32 path runs on the SIMT FP32 units (FFMA): 152 SMs x 128 lanes x 2 FLOP per clock
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        ach = fl / (ms_step / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "traffic": None, "kernel": "whole step (every FP32 SIMT pass of Algorithm 1)",
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz (max SM clock)",
+                "pass_ms_per_step": per_step, "pass_sum_ms": float(sum(per_step)),
+                "pass_sum_over_step": float(sum(per_step)) / ms_step}
+    elif kind in ("heldout", "gaussian"):
+        # many small matrices: the whole step against HBM or the tensor pipe, by
+        # its intensity (Algorithm 1's FLOPs over the bytes of A read twice and Y written)
+        alg_bytes = sum(3 * h * w * 2 for h, w in hw)
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        tpk = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        intensity = fl / alg_bytes
+        ridge = tpk * 1e12 / (hbm * 1e9)
+        bw = alg_bytes / (ms_step / 1000.0) / 1e9
+        tf = fl / (ms_step / 1000.0) / 1e12
+        on_hbm = intensity < ridge
+        roof = {"bound": "hbm" if on_hbm else "tensor", "achieved": bw if on_hbm else tf,
+                "peak": hbm if on_hbm else tpk, "unit": "GB/s" if on_hbm else "TFLOP/s",
+                "frac": bw / hbm if on_hbm else tf / tpk, "traffic": None,
+                "kernel": "whole step (every pass of Algorithm 1 on the batch)",
+                "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge,
+                "hbm_frac": bw / hbm, "tensor_frac": tf / tpk, "algorithmic_bytes_per_step": alg_bytes,
+                "peak_source": f"hbm_gbs and bf16_tflops_sustained ({peak_src})",
+                "pass_ms_per_step": per_step, "pass_sum_ms": float(sum(per_step)),
+                "pass_sum_over_step": float(sum(per_step)) / ms_step}
+
     # 5-step quintic Newton-Schulz on the same list
-    nsplan = F.Plan(hmax, wmax, "bf16", L=1)
+    nsplan = F.Plan(hmax, wmax, dtype, L=1)
     nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
     nsplan.set(F.IFNSO_OPT_TIMING, 1)
     nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
-    zs = [torch.empty_like(x) for x in xs]
+    zs = [like(torch, x) for x in xs]
     for _ in range(max(args.warmup, 3)):
         nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
     torch.cuda.synchronize()
     ns_step, _ = make_step(lambda: nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws))
     ns_step()
     torch.cuda.synchronize()
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        ns_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ns_ms = max_over_ranks(e0.elapsed_time(e1))
+    ns_ms = timed_steps(ns_step, args.steps)
     ns_pass, _ = averaged_pass_times(nsplan, ns_step, args.steps)
     ns_value = whole_job_rate(world, n, args.steps, ns_ms)
     ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
@@ -778,8 +919,8 @@ def main():
     # group on overlapping streams
     e2e = None
     if not args.no_e2e:
-        hin = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
-        hout = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+        hin = [like(torch, x, pinned=True) for x in xs]
+        hout = [like(torch, x, pinned=True) for x in xs]
         for h_, x in zip(hin, xs):
             h_.copy_(x)
         bi = sum(x.numel() * x.element_size() for x in xs)
@@ -790,37 +931,64 @@ def main():
         for _ in range(max(args.warmup, 3)):
             e2e_step()
         torch.cuda.synchronize()
-        barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        e1.record(stream)
+        e2e_ms = timed_steps(e2e_step, args.steps)
+        # where the time goes: the last step's per-group timeline, and the
+        # copies alone (each direction by itself, then both at once)
+        tl, first = plan.host_timeline()
         torch.cuda.synchronize()
-        barrier()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+        e0.record(stream)
+        for h_, x in zip(hin, xs):
+            x.copy_(h_, non_blocking=True)
+        e1.record(stream)
+        for h_, y in zip(hout, ys):
+            h_.copy_(y, non_blocking=True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms, d2h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        s_up.wait_stream(stream)
+        s_dn.wait_stream(stream)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s_up):
+            for h_, x in zip(hin, xs):
+                x.copy_(h_, non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            for h_, y in zip(hout, ys):
+                h_.copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+        both_ms = 1000.0 * (time.perf_counter() - t0)
         e2e = {"value": whole_job_rate(world, n, args.steps, e2e_ms), "unit": "matrices/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "ms_per_step": e2e_ms / args.steps,
                "api": "ifnso_orthogonalize_host, page-locked host buffers, "
-                      + (f"{args.groups} groups" if args.groups > 0 else "default grouping")}
+                      + (f"{args.groups} groups" if args.groups > 0 else "default grouping"),
+               "copies_alone": {"h2d_ms": h2d_ms, "h2d_GBs": bi / h2d_ms / 1e6, "d2h_ms": d2h_ms,
+                                "d2h_GBs": bi / d2h_ms / 1e6, "both_directions_at_once_ms": both_ms},
+               "timeline": {"what": "last timed step, per group: [uploads done, passes done, downloads done] "
+                                    "in ms since the call's start",
+                            "group_first_matrix": first,
+                            "ms": [[round(float(v), 3) for v in row] for row in tl]}}
         plan.pass_times()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, sample, cores = cpu_oracle_sample(shapes, L)
+        v, sample, cores = cpu_oracle_sample(wl, shapes, L)
         cpu = {"value": v, "unit": "matrices/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload + ": " + wl["desc"], "L": L,
                        "precision": {F.IFNSO_PREC_PLAIN: "plain FP16 squarings, BF16 P",
                                      F.IFNSO_PREC_SPLIT: "split FP16 hi+lo squarings, BF16 hi+lo P",
                                      F.IFNSO_PREC_MIXED: f"mixed: first {k_split} squarings split FP16 hi+lo, "
                                                          f"last {L - 1 - k_split} plain FP16, BF16 hi+lo P"}.get(mode),
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
-                       "l2": "inputs larger than L2 (no flush)",
+                       "l2": ("inputs larger than L2 (no flush)" if flush is None else
+                              "inputs smaller than twice L2: a 512 MB buffer is written before every step, "
+                              "and only the steps are timed (CUDA events around each)"),
                        "launch": "CUDA graph of one step, replayed" if args.graph else "eager calls",
                        "mma": ({k: ("CTA pair (M = 256)" if v == 2 else "per CTA (M = 128), whole B tile per CTA")
                                 for k, v in tuned.items()} if tuned else

@@ -314,6 +314,18 @@ ifnso_status ifnso_device_status(const ifnso_plan* plan, const void* workspace, 
 ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_passes,
                               int32_t* n_passes, int32_t* n_calls);
 
+/* Measurement aid (no counterpart in the paper): the timeline of the last
+ * eager ifnso_orthogonalize_host call on a plan with IFNSO_OPT_TIMING on.
+ * Waits for that call, then writes, for each of its *n_groups groups (at most
+ * max_groups are written), three times in milliseconds since the call's
+ * start into ms_out (host, 3 * max_groups entries): the group's uploads done,
+ * its passes done, its downloads done.  group_first (host, may be NULL,
+ * max_groups + 1 entries) receives the first matrix of each group and then
+ * the matrix count.  *n_groups is 0 if no such call was made (or it was
+ * captured into a graph). */
+ifnso_status ifnso_host_timeline(ifnso_plan* plan, double* ms_out, int32_t max_groups, int32_t* n_groups,
+                                 int32_t* group_first);
+
 /* Testing aid: device pointer and leading dimension (elements) of an h_pad x
  * h_pad intermediate of matrix `index` in a workspace used by
  * ifnso_orthogonalize.  which: 0 = T_0 then P (FP32), 1/2 = D buffer 0 hi/lo

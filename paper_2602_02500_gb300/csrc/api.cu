@@ -57,6 +57,12 @@ struct ifnso_plan {
   int host_streams = 2;
   cudaEvent_t ev_start = nullptr, ev_last = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_done;
+  // timeline of the last ifnso_orthogonalize_host call (IFNSO_OPT_TIMING, eager calls):
+  // tl_start, then per group uploads done, passes done, downloads done
+  cudaEvent_t tl_start = nullptr;
+  std::vector<cudaEvent_t> tl_ev;
+  int tl_groups = 0;
+  std::vector<int> tl_first;  // first matrix of each group, and the count
   int groups = 1;  // groups the item lists of the cached metadata are built for
   std::vector<size_t> sym_off, app_off;  // first work item of each group
   std::mutex mu;
@@ -1005,6 +1011,14 @@ ifnso_status ensure_copy_streams(ifnso_plan* plan, int groups) {
       IFNSO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
       v->push_back(e);
     }
+  if (plan->timing) {
+    if (!plan->tl_start) IFNSO_CUDA(cudaEventCreate(&plan->tl_start), "cudaEventCreate");
+    while (static_cast<int>(plan->tl_ev.size()) < 3 * groups) {
+      cudaEvent_t e;
+      IFNSO_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+      plan->tl_ev.push_back(e);
+    }
+  }
   return IFNSO_OK;
 }
 
@@ -1569,6 +1583,13 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
   if ((st = upload_ifnso_meta(plan, ly, dev_batch, dev_out, ws, coeffs, gb, stream)) != IFNSO_OK) return st;
   if ((st = ensure_copy_streams(plan, ng)) != IFNSO_OK) return st;
   const size_t esz = plan->dtype == IFNSO_BF16 ? 2 : 4;
+  // timeline events only for eager calls (a captured event would stay reserved for its graph)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  IFNSO_CUDA(cudaStreamIsCapturing(stream, &cap), "cudaStreamIsCapturing");
+  const bool tl = plan->timing && cap == cudaStreamCaptureStatusNone;
+  plan->tl_groups = tl ? ng : 0;
+  if (tl) plan->tl_first = gb;
+  if (tl) IFNSO_CUDA(cudaEventRecord(plan->tl_start, stream), "cudaEventRecord");
   // the copies come after everything already queued on `stream`
   IFNSO_CUDA(cudaEventRecord(plan->ev_start, stream), "cudaEventRecord");
   IFNSO_CUDA(cudaStreamWaitEvent(plan->s_in, plan->ev_start, 0), "cudaStreamWaitEvent");
@@ -1590,6 +1611,7 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
                    "input upload");
     }
     IFNSO_CUDA(cudaEventRecord(plan->ev_in[g], plan->s_in), "cudaEventRecord");
+    if (tl) IFNSO_CUDA(cudaEventRecord(plan->tl_ev[3 * g], plan->s_in), "cudaEventRecord");
   }
   int hpad_max = 0;
   for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
@@ -1604,6 +1626,7 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
                   plan->app_off[g + 1]);
     if (st != IFNSO_OK) return st;
     IFNSO_CUDA(cudaEventRecord(plan->ev_done[g], cs), "cudaEventRecord");
+    if (tl) IFNSO_CUDA(cudaEventRecord(plan->tl_ev[3 * g + 1], cs), "cudaEventRecord");
     IFNSO_CUDA(cudaStreamWaitEvent(plan->s_out, plan->ev_done[g], 0), "cudaStreamWaitEvent");
     for (int i = gb[g]; i < gb[g + 1]; ++i) {
       const Shape& s = shp[i];
@@ -1611,6 +1634,7 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
                                  plan->s_out),
                  "output download");
     }
+    if (tl) IFNSO_CUDA(cudaEventRecord(plan->tl_ev[3 * g + 2], plan->s_out), "cudaEventRecord");
   }
   // later work on `stream` comes after the last download
   IFNSO_CUDA(cudaEventRecord(plan->ev_last, plan->s_out), "cudaEventRecord");
@@ -1765,6 +1789,24 @@ ifnso_status ifnso_pass_times(ifnso_plan* plan, double* ms_out, int32_t max_pass
   if (!plan || !ms_out || !n_passes || max_passes < 0) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(plan->mu);
   return pass_times_locked(plan, ms_out, max_passes, n_passes, n_calls);
+}
+
+ifnso_status ifnso_host_timeline(ifnso_plan* plan, double* ms_out, int32_t max_groups, int32_t* n_groups,
+                                 int32_t* group_first) {
+  if (!plan || !ms_out || !n_groups || max_groups < 0) return fail(IFNSO_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  *n_groups = plan->tl_groups;
+  if (plan->tl_groups == 0) return IFNSO_OK;
+  IFNSO_CUDA(cudaEventSynchronize(plan->tl_ev[3 * plan->tl_groups - 1]), "cudaEventSynchronize");
+  for (int g = 0; g < plan->tl_groups && g < max_groups; ++g)
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      IFNSO_CUDA(cudaEventElapsedTime(&ms, plan->tl_start, plan->tl_ev[3 * g + k]), "cudaEventElapsedTime");
+      ms_out[3 * g + k] = ms;
+    }
+  if (group_first)
+    for (int g = 0; g <= plan->tl_groups && g <= max_groups; ++g) group_first[g] = plan->tl_first[g];
+  return IFNSO_OK;
 }
 
 ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch, void* workspace,

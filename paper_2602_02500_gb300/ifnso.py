@@ -51,7 +51,8 @@ EXPORTED = [
     "ifnso_workspace_bytes", "ifnso_orthogonalize", "ifnso_orthogonalize_host", "ifnso_plan_autotune",
     "ifnso_muon_step", "ns_iterate",
     "ns_workspace_bytes",
-    "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_frobenius_norm2",
+    "ifnso_device_status", "ifnso_workspace_view", "ifnso_pass_times", "ifnso_host_timeline",
+    "ifnso_frobenius_norm2",
     "ifnso_frobenius_norm2_static", "ifnso_learn_coefficients", "ifnso_synth_lowrank_bf16", "ifnso_last_error",
     "ifnso_launch_count", "ifnso_mlp_param_count", "ifnso_mlp_create", "ifnso_mlp_destroy",
     "ifnso_mlp_get_params", "ifnso_mlp_set_params", "ifnso_mlp_set_data", "ifnso_mlp_loss_grad",
@@ -90,6 +91,8 @@ _sig = {
                                       C.POINTER(C.c_double), _P]),
     "ifnso_pass_times": (C.c_int, [_P, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
+    "ifnso_host_timeline": (C.c_int, [_P, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int32)]),
     "ifnso_workspace_view": (C.c_int, [_P, C.POINTER(ifnso_batch_desc), _P, C.c_int32, C.c_int32,
                                        C.POINTER(_P), C.POINTER(C.c_int64)]),
     "ifnso_frobenius_norm2": (C.c_int, [C.POINTER(ifnso_batch_desc), C.c_int, _P, _P]),
@@ -359,6 +362,17 @@ class Plan:
         calls = C.c_int32()
         check(ifnso_pass_times(self.handle, ms, max_passes, C.byref(n), C.byref(calls)), "ifnso_pass_times")
         return np.array(ms[:n.value]), calls.value
+
+    def host_timeline(self, max_groups=64):
+        """Per group of the last eager orthogonalize_host call (IFNSO_OPT_TIMING on):
+        (array of [uploads done, passes done, downloads done] in ms since the
+        call's start, first matrix of each group followed by the count)."""
+        ms = (C.c_double * (3 * max_groups))()
+        first = (C.c_int32 * (max_groups + 1))()
+        n = C.c_int32()
+        check(ifnso_host_timeline(self.handle, ms, max_groups, C.byref(n), first), "ifnso_host_timeline")
+        g = min(n.value, max_groups)
+        return np.array(ms[:3 * g]).reshape(g, 3), list(first[:g + 1])
 
     def workspace_view(self, batch, index, which, ws=None):
         """(device pointer, ld) of an intermediate h_pad x h_pad buffer."""
