@@ -255,8 +255,9 @@ def host_matrix(wl, i):
 
 
 def like(torch, x, pinned=False):
-    """An uninitialised tensor with x's shape and row pitch (BF16 rows are
-    padded to a multiple of 8 elements), on x's device or page-locked on the host."""
+    """An uninitialised tensor with x's shape and row pitch (BF16 input rows
+    are padded to a multiple of 8 elements), on x's device or page-locked on
+    the host: the host copy of an input."""
     r, c = x.shape
     ld = x.stride(0)
     if pinned:
@@ -697,7 +698,7 @@ def main():
     seed0 = rank_seed0(rank)
     dtype = workload_dtype(wl)
     xs = make_inputs(F, torch, shapes, seed0, device, wl)
-    ys = [like(torch, x) for x in xs]
+    ys = [torch.empty(x.shape, dtype=x.dtype, device=device) for x in xs]  # outputs are dense (ld = cols)
     batch = F.Batch(xs)
 
     # fixed coefficients from the library's own GPU learner (Sec. 2.3 / 3.1.1)
@@ -901,7 +902,7 @@ def main():
     nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
     nsplan.set(F.IFNSO_OPT_TIMING, 1)
     nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
-    zs = [like(torch, x) for x in xs]
+    zs = [torch.empty(x.shape, dtype=x.dtype, device=device) for x in xs]
     for _ in range(max(args.warmup, 3)):
         nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
     torch.cuda.synchronize()
@@ -920,7 +921,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         hin = [like(torch, x, pinned=True) for x in xs]
-        hout = [like(torch, x, pinned=True) for x in xs]
+        hout = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
         for h_, x in zip(hin, xs):
             h_.copy_(x)
         bi = sum(x.numel() * x.element_size() for x in xs)
@@ -997,6 +998,10 @@ def main():
                                 1: "per-CTA tcgen05 MMAs, each CTA loading its whole B tile",
                                 2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group]),
                        "autotuned": tuned is not None,
+                       "small_matrices": ({1: "on-chip path (one CTA per matrix, all of Algorithm 1 in one launch)",
+                                           2: "tiled passes"}.get(plan.get(F.IFNSO_OPT_SMALL_TUNED),
+                                                                  "not applicable (a matrix has h > 128)")
+                                          if dtype == "bf16" else "FP32 SIMT passes"),
                        "coefficients": ("per-matrix proposals of the coefficient network, computed inside each "
                                         "call after the first squaring" if args.coeffs == "mlp" else
                                         "fixed, learned on the GPU by ifnso_learn_coefficients (Sec. 3.1.1 "

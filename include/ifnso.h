@@ -120,7 +120,25 @@ typedef enum {
    * group's passes can start on the SMs another group's pass is leaving
    * (the groups share no buffers).  Either way the call is ordered after
    * earlier work on the caller's stream and later work waits for it. */
-  IFNSO_OPT_HOST_STREAMS = 11
+  IFNSO_OPT_HOST_STREAMS = 11,
+  /* Shape bucket of matrices with h <= 128 (no counterpart in the paper's
+   * code; Algorithm 1 is unchanged).  Such a matrix fits one 128 x 128
+   * tensor-core tile, and one CTA can run the whole of Algorithm 1 on chip:
+   * the Gram into tensor memory, D_l and P in shared and tensor memory
+   * through all L - 1 squarings, then the product, in one launch for the
+   * whole batch, where the tiled passes launch once per pass and pad h to
+   * 256.  0 (default): the on-chip path when every matrix of a call has
+   * h <= 128 and the call uses nothing it lacks (the proposal network inside
+   * the call, IFNSO_SCALE_GELFAND2, IFNSO_OPT_GRAM_E4M3, ifnso_muon_step,
+   * IFNSO_OPT_STOP_AFTER, IFNSO_OPT_INJECT_STALL), unless
+   * ifnso_plan_autotune measured the tiled passes faster on such a batch;
+   * 1: the on-chip path whenever it applies; 2: always the tiled passes.
+   * With IFNSO_OPT_TIMING the on-chip path reports a single pass. */
+  IFNSO_OPT_SMALL_MATRICES = 12,
+  /* Read only (ifnso_plan_get): what ifnso_plan_autotune chose for batches
+   * the on-chip path applies to: 0 not measured, 1 the on-chip path, 2 the
+   * tiled passes. */
+  IFNSO_OPT_SMALL_TUNED = 13
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };
@@ -244,7 +262,11 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
  * kind, the faster mode.  The kinds are the Gram, the split squarings, the
  * plain squarings and the final product.  Later calls with
  * IFNSO_OPT_CTA_GROUP = 0 (the default) use those modes.  `chosen` (host,
- * 4 entries, or NULL) receives them in that order.  Same arguments and rules as
+ * 4 entries, or NULL) receives them in that order.  When every matrix of the
+ * batch has h <= 128 and the on-chip path applies to the call
+ * (IFNSO_OPT_SMALL_MATRICES), it then also times that path (1 + reps calls)
+ * against the tiled passes in their chosen modes and keeps the faster for
+ * such batches (IFNSO_OPT_SMALL_TUNED).  Same arguments and rules as
  * ifnso_orthogonalize; `out` holds a valid result afterwards.  Synchronises
  * `stream`.  BF16 plans only (IFNSO_ERR_UNSUPPORTED otherwise); reps in
  * [1, 100]. */

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libifnso.so")
-SOURCES = ["tc_gemm.cu", "simt.cu", "learn.cu", "mlp.cu", "api.cu"]
+SOURCES = ["tc_gemm.cu", "small.cu", "simt.cu", "learn.cu", "mlp.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

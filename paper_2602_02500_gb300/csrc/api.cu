@@ -38,6 +38,8 @@ struct ifnso_plan {
   int inject_stall = 0;  // testing aid: the Gram pass's first CTA loads nothing
   int cta_group = 0;     // tensor-core passes: 0 auto, 1 per-CTA MMAs, 2 MMAs of the CTA pair
   int gram_e4m3 = 0;     // Gram from a scaled E4M3 copy of A
+  int small = 0;         // IFNSO_OPT_SMALL_MATRICES: 0 auto, 1 on-chip path where eligible, 2 tiled passes
+  int small_tuned = 0;   // the autotuner's choice for eligible batches (0: not measured, 1 on chip, 2 tiled)
   bool tuned = false;    // ifnso_plan_autotune chose cg_kind
   int cg_kind[4] = {1, 2, 1, 1};  // MMA mode per pass kind (Gram, split squaring, plain squaring, product)
   int num_sms = 0;
@@ -184,6 +186,7 @@ struct Layout {
   std::vector<Shape> shp;
   // metadata
   size_t off_mats = 0, off_probs = 0, off_items_sym = 0, off_items_app = 0, off_coef = 0, off_rows = 0;
+  size_t off_small = 0;  // SmProblem per matrix (BF16 plans): the on-chip path for h <= 128
   size_t n_probs = 0, n_sym = 0, n_app = 0;
   size_t prob_bytes = 0;
   size_t meta_bytes = 0;
@@ -386,6 +389,10 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   off = a64(off + sizeof(double) * (K > 0 ? K : 1));
   ly.off_rows = off;  // per-matrix coefficient rows written by the proposal network
   off = a64(off + n * kRowSlots * sizeof(float));
+  if (!ly.f32 && !ns) {
+    ly.off_small = off;
+    off = a64(off + n * sizeof(SmProblem));
+  }
   ly.meta_bytes = off;
   off = a1k(off);
   ly.off_scal = off;
@@ -695,6 +702,29 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     // a Muon step reads the weights where the update goes (M's shape, contiguous)
     a.aux0 = mi.out;
     a.ld_aux = s.cols;
+  }
+  // the on-chip path's views of every matrix with h <= 128
+  SmProblem* sp = reinterpret_cast<SmProblem*>(meta + ly.off_small);
+  for (int i = 0; i < n; ++i) {
+    const Shape& s = ly.shp[i];
+    if (s.h > kSmallH) continue;
+    SmProblem& q = sp[i];
+    bool ok;
+    if (!s.trans) {
+      // Gram: M K-major (128 rows x 64 K); product: B(n, k) = M[k][n], MN-major chunks 64 x 64
+      ok = encode2d(&q.mapG, bf16_t(), mats[i].in, s.cols, s.rows, s.ld, 64, 128) &&
+           encode2d(&q.mapY, bf16_t(), mats[i].in, s.cols, s.rows, s.ld, 64, 64);
+    } else {
+      // Gram: A = M^T, MN-major chunks 64 x 64; product: B(n, k) = M[n][k], K-major (256 rows x 64 K)
+      ok = encode2d(&q.mapG, bf16_t(), mats[i].in, s.cols, s.rows, s.ld, 64, 64) &&
+           encode2d(&q.mapY, bf16_t(), mats[i].in, s.cols, s.rows, s.ld, 64, 256);
+    }
+    if (!ok) return fail(IFNSO_ERR_CUDA, "cuTensorMapEncodeTiled failed (matrix %d, on-chip path)", i);
+    q.out = mats[i].out;
+    q.ld_out = s.cols;
+    q.h = static_cast<int32_t>(s.h);
+    q.w = static_cast<int32_t>(s.w);
+    q.trans = static_cast<int32_t>(s.trans);
   }
   std::vector<WorkItem> sy, ap;
   sym_items(ly.shp, gb, sy);
@@ -1117,11 +1147,55 @@ ifnso_status run_f32(const Run& r) {
   return IFNSO_OK;
 }
 
+// The on-chip path (small.cu) runs a call when every matrix has h <= 128 and
+// the call needs nothing it does not do: the proposal network inside the
+// call, Gelfand's q = 2 bound, the E4M3 Gram, the fused Muon update and the
+// stop-after testing aid stay on the tiled passes.
+bool small_eligible(const ifnso_plan* plan, const Layout& ly, const ifnso_coeffs* coeffs, bool update) {
+  if (ly.f32 || ly.ns || ly.e4m3 || update || plan->stop_after >= 0 || plan->inject_stall) return false;
+  if (plan->scale == IFNSO_SCALE_GELFAND2 || (coeffs && coeffs->mlp)) return false;
+  if (ly.L > 30) return false;
+  for (const Shape& s : ly.shp)
+    if (s.h > kSmallH) return false;
+  return true;
+}
+
+bool use_small(const ifnso_plan* plan, const Layout& ly, const ifnso_coeffs* coeffs, bool update) {
+  if (plan->small == 2 || !small_eligible(plan, ly, coeffs, update)) return false;
+  if (plan->small == 1) return true;
+  return plan->small_tuned != 2;
+}
+
+ifnso_status run_small(const Run& r, int first, int count) {
+  ifnso_plan* plan = r.plan;
+  const Layout& ly = *r.ly;
+  uint8_t* ws = r.ws;
+  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal + first * sizeof(MatScalars), 0, count * sizeof(MatScalars),
+                             r.stream),
+             "scalar reset");
+  if (r.whole) IFNSO_CUDA(mark(plan, r.stream, true), "timing event");
+  const TcParams base = base_params<TcParams>(ws, ly, r.coeffs);
+  SmParams p{};
+  p.probs = reinterpret_cast<const SmProblem*>(ws + ly.off_small);
+  p.scal = base.scal;
+  p.coef = base.coef;
+  p.first = first;
+  p.L = ly.L;
+  p.k_split = ly.prec.k_split;
+  p.p_split = ly.prec.p_split;
+  p.frob = plan->scale == IFNSO_SCALE_FROB;
+  p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
+  IFNSO_CUDA(launch_small(p, count, r.stream), "on-chip pass");
+  if (r.whole) IFNSO_CUDA(mark(plan, r.stream, false), "timing event");
+  return IFNSO_OK;
+}
+
 // BF16 plans: every pass of Algorithm 1 for matrices [first, first + count),
 // whose work items are [sym0, sym1) and [app0, app1) of the metadata's lists.
 ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1, size_t app0, size_t app1) {
   ifnso_plan* plan = r.plan;
   const Layout& ly = *r.ly;
+  if (use_small(plan, ly, r.coeffs, r.update)) return run_small(r, first, count);
   uint8_t* ws = r.ws;
   cudaStream_t stream = r.stream;
   const int L = ly.L;
@@ -1379,6 +1453,10 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       if (value != 1 && value != 2) return fail(IFNSO_ERR_INVALID_ARG, "host streams %lld (1 or 2)", (long long)value);
       plan->host_streams = static_cast<int>(value);
       return IFNSO_OK;  // the metadata does not depend on it
+    case IFNSO_OPT_SMALL_MATRICES:
+      if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "small matrices %lld (0, 1 or 2)", (long long)value);
+      plan->small = static_cast<int>(value);
+      return IFNSO_OK;  // the metadata holds both paths' views
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -1402,6 +1480,8 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_GRAM_E4M3: *value = plan->gram_e4m3; return IFNSO_OK;
     case IFNSO_OPT_SPLIT_SQUARINGS: *value = resolve_prec(plan).k_split; return IFNSO_OK;
     case IFNSO_OPT_HOST_STREAMS: *value = plan->host_streams; return IFNSO_OK;
+    case IFNSO_OPT_SMALL_MATRICES: *value = plan->small; return IFNSO_OK;
+    case IFNSO_OPT_SMALL_TUNED: *value = plan->small_tuned; return IFNSO_OK;
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }
@@ -1522,11 +1602,12 @@ ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch
     if (pass >= 2 && pass <= L) return (pass - 1) <= pc.k_split ? kSplit : kPlain;
     return -1;
   };
-  const int saved_cg = plan->cta_group, saved_stop = plan->stop_after;
+  const int saved_cg = plan->cta_group, saved_stop = plan->stop_after, saved_small = plan->small;
   const bool saved_timing = plan->timing, saved_tuned = plan->tuned;
   plan->stop_after = -1;
   plan->timing = true;
   plan->tuned = false;
+  plan->small = 2;  // the MMA modes are those of the tiled passes
   double ms[3][kKinds] = {};
   ifnso_status st = IFNSO_OK;
   std::vector<double> pt(L + 2);
@@ -1544,14 +1625,42 @@ ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch
     }
   }
   plan->cta_group = saved_cg;
-  plan->stop_after = saved_stop;
-  plan->timing = saved_timing;
   if (st != IFNSO_OK) {
+    plan->stop_after = saved_stop;
+    plan->timing = saved_timing;
     plan->tuned = saved_tuned;
+    plan->small = saved_small;
     return st;
   }
   for (int k = 0; k < kKinds; ++k) plan->cg_kind[k] = ms[2][k] < ms[1][k] ? 2 : 1;
   plan->tuned = true;
+  // the shape bucket h <= 128: the on-chip path against the tiled passes (in their tuned modes)
+  {
+    std::vector<Shape> shp;
+    ifnso_status sb = read_batch(plan, batch, shp);
+    if (sb == IFNSO_OK) {
+      const Layout ly = make_layout(plan, shp, 0, 0, L + 1);
+      if (small_eligible(plan, ly, coeffs, false)) {
+        double tot[3] = {0.0, 0.0, 0.0};
+        for (int mode = 1; mode <= 2 && st == IFNSO_OK; ++mode) {
+          plan->small = mode;
+          for (int r = 0; r <= reps && st == IFNSO_OK; ++r) {
+            st = orthogonalize_locked(plan, batch, coeffs, out, workspace, workspace_bytes, stream);
+            if (st != IFNSO_OK) break;
+            int np = 0;
+            st = pass_times_locked(plan, pt.data(), static_cast<int>(pt.size()), &np, nullptr);
+            if (r == 0) continue;
+            for (int k = 0; k < np; ++k) tot[mode] += pt[k];
+          }
+        }
+        if (st == IFNSO_OK) plan->small_tuned = tot[1] <= tot[2] ? 1 : 2;
+      }
+    }
+  }
+  plan->small = saved_small;
+  plan->stop_after = saved_stop;
+  plan->timing = saved_timing;
+  if (st != IFNSO_OK) return st;
   plan->sig_valid = false;
   if (chosen)
     for (int k = 0; k < kKinds; ++k) chosen[k] = plan->cg_kind[k];

@@ -15,6 +15,7 @@ constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;
 constexpr int HPAD = 256;
+constexpr int kSmallH = 128;  // matrices with h <= kSmallH fit the on-chip path (small.cu)
 
 enum EpiKind : int {
   EPI_GRAM = 0,      // T_0 tile -> FP32 buffer (direct + mirrored), sum T_0^2 and tr T_0
@@ -161,12 +162,39 @@ struct MatInfo {
   int64_t a8ld;
 };
 
+// One matrix of the on-chip path for h <= 128 (small.cu): the whole of
+// Algorithm 1 in one CTA.  The tensor maps view the input M itself.
+struct SmProblem {
+  CUtensorMap mapG;  // the Gram's operand: M K-major (box 64 x 128), or, M tall, M^T MN-major (box 64 x 64)
+  CUtensorMap mapY;  // the product's B operand: M MN-major (box 64 x 64), or, M tall, K-major (box 64 x 256)
+  void* out;         // Y in M's shape, BF16, leading dimension ld_out
+  int64_t ld_out;
+  int32_t h, w;      // oriented shape (h <= 128)
+  int32_t trans;     // M is tall: A = M^T
+  int32_t pad;
+};
+static_assert(sizeof(SmProblem) % 64 == 0, "SmProblem arrays must keep every tensor map 64-byte aligned");
+
+struct SmParams {
+  const SmProblem* probs;
+  MatScalars* scal;
+  CoefTable coef;
+  int32_t first;    // matrix index of CTA 0
+  int32_t L;
+  int32_t k_split;  // squarings 1..k_split multiply split (hi + lo) FP16 operands
+  int32_t p_split;  // P enters the product as BF16 hi + lo
+  int32_t frob;     // scale by ||A||_F^2 instead of ||A A^T||_F
+  uint32_t wait_ms;
+};
+
 // ------------------------------------------------------------ launchers
 // (defined in tc_gemm.cu / simt.cu / learn.cu; called by api.cu)
 // Launches clusters of two CTAs (at most max_clusters, at most one per item;
 // items are pairs of tiles, see WorkItem), in the MMA mode p.cta_group.
 cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s);
 int tc_smem_bytes(int na, int nb, int cta_group);
+// One CTA per matrix first .. first + count - 1 (every one with h <= 128).
+cudaError_t launch_small(const SmParams& p, int count, cudaStream_t s);
 
 cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,
                          int64_t out_stride, int grid_x, cudaStream_t s);

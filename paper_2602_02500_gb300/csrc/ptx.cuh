@@ -299,6 +299,23 @@ __device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])              \
       : "r"(taddr))
 
+// Thread t of the warp writes r[0..31] to row (lane base + t), columns
+// [col, col + 32) of TMEM (the inverse of IFNSO_TMEM_LD32).
+#define IFNSO_TMEM_ST32(taddr, r)                                                                 \
+  asm volatile(                                                                                   \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, " \
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "  \
+      "%30, %31, %32};"                                                                           \
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),  \
+      "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), \
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),          \
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),          \
+      "r"(r[29]), "r"(r[30]), "r"(r[31])                                                          \
+      : "memory")
+
+// Wait until this thread's tcgen05.st have been performed.
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Wait for outstanding tcgen05.ld; the registers are tied in so that no use
 // of them can be scheduled before the wait.
 #define IFNSO_TMEM_WAIT_LD(r)                                                                      \

@@ -1,0 +1,529 @@
+// Algorithm 1 (Sec. 2.4) for matrices with h <= 128, one CTA per matrix,
+// entirely on chip (sm_103a).
+//
+// A matrix this small fits one 128 x 128 tensor-core tile, so the tiled
+// passes (one launch per pass, every intermediate through HBM, h padded to
+// 256) spend their time on launches and padding.  Here one CTA runs the
+// whole chain:
+//   Gram      T_0 = A A^T on tcgen05 (M = N = 128, K = w streamed by TMA),
+//             accumulator in TMEM;
+//   scalars   o = ||T_0||_F (or ||A||_F^2), tr T_0, 1/o, 1/sqrt(o), the
+//             D-basis identity weight c_0 = 1 + sum_l w_l (FP64);
+//   squarings D_1 = T_0 / o, D_{l+1} = 2 D_l - D_l^2 (l = 1..L-1): D_l lives
+//             in shared memory as the FP16 operand of the next product (hi,
+//             or hi + lo for the leading squarings of the mixed precision,
+//             three products hi hi + hi lo + lo hi) and in FP32 in the
+//             epilogue warps' registers; P = c_0 I - sum_l w_l D_l in FP32
+//             in TMEM (columns 128..255) beside the products' accumulator;
+//   product   Y = P A / sqrt(o) with P as BF16 hi + lo in shared memory and
+//             A streamed again in 256-column tiles, written in M's shape.
+// Rows and columns past h are zero (TMA zero fill), so they drop out of
+// every product.
+//
+// Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
+// issuer, warps 2..9 epilogue (two per TMEM lane quadrant; each thread owns
+// one row and 64 columns of the 128 x 128 intermediates).  Every wait is
+// bounded as in the tiled kernels (ptx.cuh): a timeout records
+// IFNSO_DEV_TIMEOUT for the matrix, lets issued copies and products land,
+// frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace ifnso {
+namespace {
+
+constexpr int kThreads = 320;
+constexpr uint32_t kOpBuf = 128 * 128 * 2;        // one 128 x 128 16-bit operand: two 64-wide K blocks
+constexpr uint32_t kKBlock = 128 * 64 * 2;        // 16 KB: 128 rows x 64 K (128-byte swizzled rows)
+constexpr uint32_t kApplyStage = 256 * 64 * 2;    // 32 KB: 256 B-operand rows x 64 K
+constexpr uint32_t kRing = 4 * kApplyStage;       // 128 KB, shared by the Gram (8 x 16 KB) and product (4 x 32 KB) rings
+constexpr int kGramStages = static_cast<int>(kRing / kKBlock);
+constexpr int kApplyStages = static_cast<int>(kRing / kApplyStage);
+constexpr uint32_t kSmem = 1024 + kRing + 2 * kOpBuf + 512;
+constexpr int kDevTimeout = 4, kDevZero = 1, kDevNonFinite = 2;
+
+// Barrier slots (8 bytes each) after the buffers.
+enum Bar {
+  kGFull = 0,
+  kGEmpty = kGFull + kGramStages,
+  kAFull = kGEmpty + kGramStages,
+  kAEmpty = kAFull + kApplyStages,
+  kTFull = kAEmpty + kApplyStages,  // Gram / squaring accumulator ready (one phase per product)
+  kDReady,                          // D_1 .. D_{L-1} written (8 epilogue warps per phase)
+  kPReady,                          // P written (8 epilogue warps)
+  kGDone,                           // the Gram's products have read their ring stages
+  kT2Full,                          // product accumulators 0, 1 ready
+  kT2Empty = kT2Full + 2,           // product accumulators 0, 1 drained (8 warps each)
+  kDrain = kT2Empty + 2,
+  kNumBars
+};
+static_assert(kNumBars * 8 + 8 + 8 * 8 <= 512, "barriers, TMEM slot, abort flag, 8 partial sums");
+
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
+  // byte offset of 16-byte chunk `chunk` (0..7) of row `row` in a 128-byte
+  // swizzled K-major block (8-row groups 1024 bytes apart)
+  return static_cast<uint32_t>((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+template <typename T>
+__device__ __forceinline__ uint4 pack8(const float* x);
+template <>
+__device__ __forceinline__ uint4 pack8<__half>(const float* x) {
+  uint4 u;
+  __half2* h = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) h[t] = __floats2half2_rn(x[2 * t], x[2 * t + 1]);
+  return u;
+}
+template <>
+__device__ __forceinline__ uint4 pack8<__nv_bfloat16>(const float* x) {
+  uint4 u;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) h[t] = __floats2bfloat162_rn(x[2 * t], x[2 * t + 1]);
+  return u;
+}
+
+// Row `row`'s 64 values v of K block `kb` into a 128 x 128 operand buffer
+// (K-major, 128-byte swizzle), rounded to T; with lo, also the rounding
+// remainder into the second buffer and v replaced by hi + lo.
+template <typename T>
+__device__ __forceinline__ void put_row(uint8_t* buf, uint8_t* buf_lo, int row, int kb, float* v, bool split) {
+  uint8_t* blk = buf + kb * kKBlock;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if constexpr (std::is_same_v<T, __half>)
+        hi[t] = __half2float(__float2half_rn(v[8 * q + t]));
+      else
+        hi[t] = __bfloat162float(__float2bfloat16_rn(v[8 * q + t]));
+      lo[t] = v[8 * q + t] - hi[t];
+    }
+    *reinterpret_cast<uint4*>(blk + sw128_off(row, q)) = pack8<T>(hi);
+    if (split) {
+      *reinterpret_cast<uint4*>(buf_lo + kb * kKBlock + sw128_off(row, q)) = pack8<T>(lo);
+      // the value the products see: hi + lo, each rounded to T
+      float lr[8];
+      const uint4 u = pack8<T>(lo);
+      const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if constexpr (std::is_same_v<T, __half>)
+          lr[t] = __half2float(e[t]);
+        else
+          lr[t] = __bfloat162float(e[t]);
+        v[8 * q + t] = hi[t] + lr[t];
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[8 * q + t] = hi[t];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constant__ SmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t ring = base;
+  uint8_t* dhi = base_ptr + kRing;
+  uint8_t* dlo = dhi + kOpBuf;
+  const uint32_t dhi_s = base + kRing, dlo_s = dhi_s + kOpBuf;
+  const uint32_t bar0 = base + kRing + 2 * kOpBuf;
+  auto bar = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(i); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + kRing + 2 * kOpBuf + 8 * kNumBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float2* red = reinterpret_cast<float2*>(tmem_slot + 2);  // 8 epilogue warps' partial sums
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int mi = p.first + static_cast<int>(blockIdx.x);
+  const SmProblem& pr = p.probs[mi];
+  const int L = p.L;
+  const int h = pr.h, w = pr.w;
+  const int n_kb = (w + 63) / 64;               // K blocks of the Gram
+  const int n_nt = (w + 255) / 256;             // 256-column tiles of the product
+  const unsigned long long tmo = p.wait_ms ? p.wait_ms * 1000000ull : kWaitTimeoutNs;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGramStages; ++s) {
+      mbar_init(bar(kGFull + s), 1);
+      mbar_init(bar(kGEmpty + s), 1);
+    }
+    for (int s = 0; s < kApplyStages; ++s) {
+      mbar_init(bar(kAFull + s), 1);
+      mbar_init(bar(kAEmpty + s), 1);
+    }
+    mbar_init(bar(kTFull), 1);
+    mbar_init(bar(kDReady), 8);
+    mbar_init(bar(kPReady), 8);
+    mbar_init(bar(kGDone), 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(bar(kT2Full + a), 1);
+      mbar_init(bar(kT2Empty + a), 8);
+    }
+    mbar_init(bar(kDrain), 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc<1>(smem_u32(tmem_slot), 512);
+    tmem_relinquish<1>();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  MatScalars* sc = p.scal + mi;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      tmap_acquire(&pr.mapG);
+      tmap_acquire(&pr.mapY);
+      bool ok = true;
+      int filled = 0, afilled = 0;
+      for (int kb = 0; kb < n_kb && ok; ++kb) {
+        const int s = kb % kGramStages;
+        if (!mbar_wait(bar(kGEmpty + s), ((kb / kGramStages) & 1) ^ 1u, abort_flag, tmo)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = bar(kGFull + s);
+        mbar_arrive_expect_tx(fb, kKBlock);
+        const uint32_t dst = ring + s * kKBlock;
+        if (!pr.trans) {
+          tma_load_2d(dst, &pr.mapG, fb, 64 * kb, 0);  // A = M: 128 rows x 64 K
+        } else {
+          tma_load_2d(dst, &pr.mapG, fb, 0, 64 * kb);  // A = M^T: two 64-wide MN chunks
+          tma_load_2d(dst + 8192, &pr.mapG, fb, 64, 64 * kb);
+        }
+        ++filled;
+      }
+      // the product's stages overlay the Gram's: wait until its products have read them
+      if (ok && !mbar_wait(bar(kGDone), 0, abort_flag, tmo)) ok = false;
+      for (int t = 0; ok && t < 2 * n_nt; ++t) {
+        const int nt = t >> 1, kb = t & 1;
+        const int s = t % kApplyStages;
+        if (!mbar_wait(bar(kAEmpty + s), ((t / kApplyStages) & 1) ^ 1u, abort_flag, tmo)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = bar(kAFull + s);
+        mbar_arrive_expect_tx(fb, kApplyStage);
+        const uint32_t dst = ring + s * kApplyStage;
+        if (!pr.trans) {
+          // B(n, k) = A(k, n) = M(k, n): four 64-wide MN chunks of the tile
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tma_load_2d(dst + 8192 * j, &pr.mapY, fb, 256 * nt + 64 * j, 64 * kb);
+        } else {
+          // B(n, k) = M(n, k): 256 K-major rows
+          tma_load_2d(dst, &pr.mapY, fb, 64 * kb, 256 * nt);
+        }
+        ++afilled;
+      }
+      if (!ok) {
+        atomicOr(&sc->status, kDevTimeout);
+        // let the Gram copies already issued land before the CTA exits
+        for (int s = 0; s < kGramStages && s < filled; ++s) {
+          const int last = s + ((filled - 1 - s) / kGramStages) * kGramStages;
+          mbar_wait_bounded(bar(kGFull + s), (last / kGramStages) & 1, tmo);
+        }
+        for (int s = 0; s < kApplyStages && s < afilled; ++s) {
+          const int last = s + ((afilled - 1 - s) / kApplyStages) * kApplyStages;
+          mbar_wait_bounded(bar(kAFull + s), (last / kApplyStages) & 1, tmo);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      bool ok = true;
+      const uint32_t acc = tmem_base;  // columns [0, 128): T_0, then each D_l^2
+      // Gram: A and B are the same 128 x 64 tile (T_0 = A A^T)
+      const uint32_t id_g = idesc_f16(1u, 128, 128, pr.trans ? 1u : 0u, pr.trans ? 1u : 0u);
+      for (int kb = 0; kb < n_kb && ok; ++kb) {
+        const int s = kb % kGramStages;
+        if (!mbar_wait(bar(kGFull + s), (kb / kGramStages) & 1, abort_flag, tmo)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = ring + s * kKBlock;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t d = pr.trans ? sdesc_sw128(sa + k * 2048, 8192, 1024) : sdesc_sw128(sa + k * 32, 16, 1024);
+          umma_f16<1>(acc, d, d, id_g, (kb | k) != 0 ? 1u : 0u);
+        }
+        umma_commit<1>(bar(kGEmpty + s));
+      }
+      if (ok) {
+        umma_commit<1>(bar(kTFull));
+        umma_commit<1>(bar(kGDone));
+      }
+      // squarings: D_l D_l from the FP16 operand buffers (D symmetric: B = A)
+      const uint32_t id_s = idesc_f16(0u, 128, 128, 0u, 0u);
+      for (int j = 1; j <= L - 1 && ok; ++j) {
+        if (!mbar_wait(bar(kDReady), (j - 1) & 1, abort_flag, tmo)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const bool split = j <= p.k_split;
+        const int np = split ? 3 : 1;
+        int first = 1;
+#pragma unroll 1
+        for (int kb = 0; kb < 2; ++kb) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            for (int q = 0; q < np; ++q) {
+              // hi hi, hi lo, lo hi
+              const uint32_t sa = (q == 2 ? dlo_s : dhi_s) + kb * kKBlock + k * 32;
+              const uint32_t sb = (q == 1 ? dlo_s : dhi_s) + kb * kKBlock + k * 32;
+              umma_f16<1>(acc, sdesc_sw128(sa, 16, 1024), sdesc_sw128(sb, 16, 1024), id_s, first ? 0u : 1u);
+              first = 0;
+            }
+          }
+        }
+        umma_commit<1>(bar(kTFull));
+      }
+      // the product Y = P A: P hi (+ lo) as the A operand, A's columns as B
+      if (ok && !mbar_wait(bar(kPReady), 0, abort_flag, tmo)) ok = false;
+      if (ok) tc_fence_after();
+      const uint32_t id_y = idesc_f16(1u, 128, 256, 0u, pr.trans ? 0u : 1u);
+      const int np = p.p_split ? 2 : 1;
+      for (int nt = 0; nt < n_nt && ok; ++nt) {
+        const int b = nt & 1;
+        if (!mbar_wait(bar(kT2Empty + b), ((nt >> 1) & 1) ^ 1u, abort_flag, tmo)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_t = tmem_base + static_cast<uint32_t>(256 * b);
+        for (int kb = 0; kb < 2 && ok; ++kb) {
+          const int t = 2 * nt + kb;
+          const int s = t % kApplyStages;
+          if (!mbar_wait(bar(kAFull + s), (t / kApplyStages) & 1, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sb = ring + s * kApplyStage;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t bd = pr.trans ? sdesc_sw128(sb + k * 32, 16, 1024) : sdesc_sw128(sb + k * 2048, 8192, 1024);
+            for (int q = 0; q < np; ++q) {
+              const uint32_t sa = (q ? dlo_s : dhi_s) + kb * kKBlock + k * 32;
+              umma_f16<1>(d_t, sdesc_sw128(sa, 16, 1024), bd, id_y, (kb | k | q) != 0 ? 1u : 0u);
+            }
+          }
+          umma_commit<1>(bar(kAEmpty + s));
+        }
+        if (ok) umma_commit<1>(bar(kT2Full + b));
+      }
+      if (!ok) atomicOr(&sc->status, kDevTimeout);
+      umma_commit<1>(bar(kDrain));
+      mbar_wait_bounded(bar(kDrain), 0, tmo);
+    }
+  } else {
+    // -------------------------------------------------- epilogue (warps 2..9)
+    const int q = warp & 3;               // TMEM lane quadrant: rows 32 q .. 32 q + 31
+    const int half = (warp - 2) >> 2;     // columns 64 half .. 64 half + 63
+    const int row = 32 * q + lane;
+    const uint32_t trow = tmem_base + (static_cast<uint32_t>(32 * q) << 16);
+    auto wait_bar = [&](uint32_t b, uint32_t parity) {
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(b, parity, abort_flag, tmo) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok) tc_fence_after();
+      return ok != 0;
+    };
+    auto load64 = [&](uint32_t col, float* v) {
+      uint32_t u[32];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        IFNSO_TMEM_LD32(trow + col + 32 * c, u);
+        IFNSO_TMEM_WAIT_LD(u);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) v[32 * c + t] = __uint_as_float(u[t]);
+      }
+    };
+    // P (FP32) lives in TMEM columns 128..255: this thread's row, 64 columns
+    const uint32_t tp = trow + 128 + 64 * half;
+    auto p_store = [&](const float* v) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t u[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) u[t] = __float_as_uint(v[32 * c + t]);
+        IFNSO_TMEM_ST32(tp + 32 * c, u);
+      }
+      tmem_wait_st();
+    };
+    float d[64];
+    bool ok = wait_bar(bar(kTFull), 0);
+    float inv_s2 = 0.f, inv_s = 0.f;
+    double c0 = 1.0;
+    {
+      float ss = 0.f, tr = 0.f;
+      if (ok) {
+        load64(64 * half, d);
+#pragma unroll
+        for (int t = 0; t < 64; ++t) {
+          ss = fmaf(d[t], d[t], ss);
+          if (64 * half + t == row) tr += d[t];
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        tr += __shfl_xor_sync(0xffffffffu, tr, o);
+      }
+      if (lane == 0) red[warp - 2] = make_float2(ss, tr);
+      // every epilogue warp reaches this barrier, whether or not its wait succeeded
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+    }
+    if (ok) {
+      double o2 = 0.0, trace = 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        o2 += static_cast<double>(red[k].x);
+        trace += static_cast<double>(red[k].y);
+      }
+      const double s2 = p.frob ? trace : sqrt(o2);
+      for (int l = 1; l <= L; ++l) c0 += coef_at(p.coef, mi, l);
+      const bool fin = isfinite(s2) && isfinite(c0);
+      const bool pos = fin && s2 > 0.0;
+      inv_s2 = pos ? static_cast<float>(1.0 / s2) : 0.f;
+      inv_s = pos ? static_cast<float>(1.0 / sqrt(s2)) : 0.f;
+      if (warp == 2 && lane == 0) {
+        sc->o2 = o2;
+        sc->trace = trace;
+        sc->s2 = s2;
+        sc->c0 = c0;
+        sc->inv_s2 = inv_s2;
+        sc->inv_s = inv_s;
+        atomicOr(&sc->status, (!fin ? kDevNonFinite : 0) | ((fin && s2 == 0.0) ? kDevZero : 0));
+      }
+      // D_1 = T_0 / o as the first squaring's operand (hi + lo when it is split)
+#pragma unroll
+      for (int t = 0; t < 64; ++t) d[t] *= inv_s2;
+      if (L >= 2) put_row<__half>(dhi, dlo, row, half, d, 1 <= p.k_split);
+      const float c0f = static_cast<float>(c0);
+      const float w1 = static_cast<float>(coef_at(p.coef, mi, 1));
+      {
+        float pv[64];
+#pragma unroll
+        for (int t = 0; t < 64; ++t) pv[t] = fmaf(-w1, d[t], (64 * half + t == row) ? c0f : 0.f);
+        p_store(pv);
+      }
+      if (L >= 2) {
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(kDReady));
+      }
+    }
+    for (int j = 1; j <= L - 1 && ok; ++j) {
+      if (!(ok = wait_bar(bar(kTFull), j & 1))) break;
+      const float wn = static_cast<float>(coef_at(p.coef, mi, j + 1));
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t u[32], pu[32];
+        IFNSO_TMEM_LD32(trow + 64 * half + 32 * c, u);
+        IFNSO_TMEM_LD32(tp + 32 * c, pu);
+        IFNSO_TMEM_WAIT_LD(u);
+        IFNSO_TMEM_WAIT_LD(pu);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const float dn = 2.0f * d[32 * c + t] - __uint_as_float(u[t]);  // D_{j+1} = 2 D_j - D_j^2
+          d[32 * c + t] = dn;
+          pu[t] = __float_as_uint(fmaf(-wn, dn, __uint_as_float(pu[t])));  // P -= w_{j+1} D_{j+1}
+        }
+        IFNSO_TMEM_ST32(tp + 32 * c, pu);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      if (j < L - 1) {
+        put_row<__half>(dhi, dlo, row, half, d, j + 1 <= p.k_split);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar(kDReady));
+      }
+    }
+    if (ok) {
+      // P as BF16 hi (+ lo): the A operand of the product (P is symmetric)
+      load64(128 + 64 * half, d);
+      tc_fence_before();  // the product's accumulator 0 overwrites these TMEM columns
+      put_row<__nv_bfloat16>(dhi, dlo, row, half, d, p.p_split != 0);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(kPReady));
+    }
+    // Y = P A / sqrt(o): this warp's rows, 128 of each tile's 256 columns
+    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(pr.out);
+    for (int nt = 0; nt < n_nt && ok; ++nt) {
+      const int b = nt & 1;
+      if (!(ok = wait_bar(bar(kT2Full + b), (nt >> 1) & 1))) break;
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        const int col = 256 * nt + 128 * half + 32 * c;  // first output column (of A's w)
+        uint32_t u[32];
+        __syncwarp();
+        IFNSO_TMEM_LD32(trow + static_cast<uint32_t>(256 * b + 128 * half + 32 * c), u);
+        IFNSO_TMEM_WAIT_LD(u);
+        if (row >= h || col >= w) continue;  // (the loop head reconverges the warp before the next load)
+        float y[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) y[t] = __uint_as_float(u[t]) * inv_s;
+        if (!pr.trans) {
+          __nv_bfloat16* dst = out + static_cast<int64_t>(row) * pr.ld_out + col;
+          if ((pr.ld_out & 7) == 0 && col + 32 <= w) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) reinterpret_cast<uint4*>(dst)[t] = pack8<__nv_bfloat16>(y + 8 * t);
+          } else {
+            for (int t = 0; t < 32 && col + t < w; ++t) dst[t] = __float2bfloat16_rn(y[t]);
+          }
+        } else {
+          // M is tall: Y^T, element (row, col + t) goes to out[col + t][row]
+          for (int t = 0; t < 32 && col + t < w; ++t)
+            out[static_cast<int64_t>(col + t) * pr.ld_out + row] = __float2bfloat16_rn(y[t]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(kT2Empty + b));
+    }
+    if (!ok && lane == 0) atomicOr(&sc->status, kDevTimeout);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc<1>(tmem_base, 512);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_small(const SmParams& p, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  small_kernel<<<count, kThreads, kSmem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ifnso
