@@ -815,10 +815,9 @@ def main():
 
     # The dominant kernel: the squaring instantiation with the most time per
     # step.  Squarings j = 1..L-1 take split operands for j <= k (the rest
-    # plain FP16), and every squaring whose P update has no D_l term folds
-    # -2 D_l into its MMAs (a separate kernel instantiation): with fixed
-    # coefficients the even ones, with proposed coefficients the odd ones
-    # from 3 on.
+    # plain FP16).  With fixed coefficients every squaring folds -2 D_l into
+    # its MMAs and adds its own P term; with proposed coefficients the odd
+    # ones from 3 on fold and the others read D_l for two P terms.
     peaks, peak_src = load_peaks()
     mode = plan.get(F.IFNSO_OPT_PRECISION)
     k_split = plan.get(F.IFNSO_OPT_SPLIT_SQUARINGS)
@@ -826,7 +825,7 @@ def main():
     sq = per_step[2:2 + (L - 1)] if L > 1 else []
 
     def folded(j):
-        return (j % 2 == 0) if args.coeffs == "fixed" else (j % 2 == 1 and j >= 3)
+        return True if args.coeffs == "fixed" else (j % 2 == 1 and j >= 3)
 
     variants = {}
     for j, t in enumerate(sq, start=1):
@@ -849,8 +848,8 @@ def main():
         traffic = load_traffic().get(f"{args.workload}:squaring_{dominant}")
         ach = sq_alg / (sq_launch_ms / 1000.0) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        what = ("D_{l+1} = 2 D_l - D_l^2, -2 D_l folded into the MMAs" if dominant.endswith("_fold")
-                else "D_{l+1} = 2 D_l - D_l^2 with the P update fused")
+        what = ("D_{l+1} = 2 D_l - D_l^2, -2 D_l folded into the MMAs, its P term added in L2"
+                if dominant.endswith("_fold") else "D_{l+1} = 2 D_l - D_l^2 with two P terms, D_l read")
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic,
                 "kernel": f"tc_gemm_kernel squaring pass, {dominant.split('_')[0]} operands ({what})",
@@ -933,6 +932,12 @@ def main():
             e2e_step()
         torch.cuda.synchronize()
         e2e_ms = timed_steps(e2e_step, args.steps)
+        # host time spent enqueueing one call (the GPU waits if this exceeds the call's device time)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        host_ms = 1000.0 * (time.perf_counter() - t0)
+        torch.cuda.synchronize()
         # where the time goes: the last step's per-group timeline, and the
         # copies alone (each direction by itself, then both at once)
         tl, first = plan.host_timeline()
@@ -963,6 +968,7 @@ def main():
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "ms_per_step": e2e_ms / args.steps,
                "api": "ifnso_orthogonalize_host, page-locked host buffers, "
                       + (f"{args.groups} groups" if args.groups > 0 else "default grouping"),
+               "host_enqueue_ms": host_ms,
                "copies_alone": {"h2d_ms": h2d_ms, "h2d_GBs": bi / h2d_ms / 1e6, "d2h_ms": d2h_ms,
                                 "d2h_GBs": bi / d2h_ms / 1e6, "both_directions_at_once_ms": both_ms},
                "timeline": {"what": "last timed step, per group: [uploads done, passes done, downloads done] "

@@ -67,6 +67,7 @@ struct ifnso_plan {
   std::vector<int> tl_first;  // first matrix of each group, and the count
   int groups = 1;  // groups the item lists of the cached metadata are built for
   std::vector<size_t> sym_off, app_off;  // first work item of each group
+  std::vector<int32_t> small_idx;         // matrices the on-chip path computes (ascending)
   std::mutex mu;
 };
 
@@ -187,6 +188,7 @@ struct Layout {
   // metadata
   size_t off_mats = 0, off_probs = 0, off_items_sym = 0, off_items_app = 0, off_coef = 0, off_rows = 0;
   size_t off_small = 0;  // SmProblem per matrix (BF16 plans): the on-chip path for h <= 128
+  size_t off_small_idx = 0;  // int32 per matrix: the matrices the on-chip path computes
   size_t n_probs = 0, n_sym = 0, n_app = 0;
   size_t prob_bytes = 0;
   size_t meta_bytes = 0;
@@ -307,14 +309,16 @@ std::vector<int> heavy_first(const std::vector<Shape>& shp, int first, int last)
 }
 
 // Work items of the symmetric passes, group after group; off[g] = first item of group g.
+// skip_small: the on-chip path computes the matrices with h <= kSmallH (no items for them).
 void sym_items(const std::vector<Shape>& shp, const std::vector<int>& gb, std::vector<WorkItem>& items,
-               std::vector<size_t>* off = nullptr) {
+               std::vector<size_t>* off = nullptr, bool skip_small = false) {
   if (off) off->clear();
   for (size_t g = 0; g + 1 < gb.size(); ++g) {
     if (off) off->push_back(items.size());
     // one item per upper 256 x 256 block (I <= J): its two 128-row halves go
     // to the two CTAs of a cluster
     for (int m : heavy_first(shp, gb[g], gb[g + 1])) {
+      if (skip_small && shp[m].h <= kSmallH) continue;
       const int nb = static_cast<int>(shp[m].hpad / 256);
       for (int I = 0; I < nb; ++I)
         for (int J = I; J < nb; ++J)
@@ -326,13 +330,14 @@ void sym_items(const std::vector<Shape>& shp, const std::vector<int>& gb, std::v
 }
 
 void app_items(const std::vector<Shape>& shp, const std::vector<int>& gb, std::vector<WorkItem>& items,
-               std::vector<size_t>* off = nullptr) {
+               std::vector<size_t>* off = nullptr, bool skip_small = false) {
   if (off) off->clear();
   for (size_t g = 0; g + 1 < gb.size(); ++g) {
     if (off) off->push_back(items.size());
     // one item per pair of 128-row tiles sharing a 256-column block (rows past
     // h are computed on zero padding and not stored)
     for (int m : heavy_first(shp, gb[g], gb[g + 1])) {
+      if (skip_small && shp[m].h <= kSmallH) continue;
       const int pairs = static_cast<int>((shp[m].h + 2 * BM - 1) / (2 * BM));
       const int tns = static_cast<int>((shp[m].w + BN - 1) / BN);
       for (int tn = 0; tn < tns; ++tn)
@@ -392,6 +397,8 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   if (!ly.f32 && !ns) {
     ly.off_small = off;
     off = a64(off + n * sizeof(SmProblem));
+    ly.off_small_idx = off;
+    off = a64(off + n * sizeof(int32_t));
   }
   ly.meta_bytes = off;
   off = a1k(off);
@@ -548,11 +555,15 @@ CUtensorMapDataType f16_t() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 
 // ---------------------------------------------------------------- IFNSO metadata
 ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void* const* out, uint8_t* ws,
-                              const double* host_coef, int K, const std::vector<int>& gb, uint8_t* meta) {
+                              const double* host_coef, int K, const std::vector<int>& gb, uint8_t* meta,
+                              bool on_chip = false) {
   memset(meta, 0, ly.meta_bytes);
   const int n = ly.count;
   MatInfo* mats = reinterpret_cast<MatInfo*>(meta + ly.off_mats);
-  for (int i = 0; i < n; ++i) mats[i] = mat_info(ly, b, out, ws, i);
+  for (int i = 0; i < n; ++i) {
+    mats[i] = mat_info(ly, b, out, ws, i);
+    mats[i].on_chip = (on_chip && ly.shp[i].h <= kSmallH) ? 1 : 0;
+  }
   if (host_coef) {
     double* c = reinterpret_cast<double*>(meta + ly.off_coef);
     for (int k = 0; k < K; ++k) c[k] = host_coef[k];
@@ -726,9 +737,12 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     q.w = static_cast<int32_t>(s.w);
     q.trans = static_cast<int32_t>(s.trans);
   }
+  int32_t* sidx = reinterpret_cast<int32_t*>(meta + ly.off_small_idx);
+  for (int i = 0, k = 0; i < n; ++i)
+    if (ly.shp[i].h <= kSmallH) sidx[k++] = i;
   std::vector<WorkItem> sy, ap;
-  sym_items(ly.shp, gb, sy);
-  app_items(ly.shp, gb, ap);
+  sym_items(ly.shp, gb, sy, nullptr, on_chip);
+  app_items(ly.shp, gb, ap, nullptr, on_chip);
   memcpy(meta + ly.off_items_sym, sy.data(), sy.size() * sizeof(WorkItem));
   memcpy(meta + ly.off_items_app, ap.data(), ap.size() * sizeof(WorkItem));
   return IFNSO_OK;
@@ -1056,19 +1070,22 @@ ifnso_status ensure_copy_streams(ifnso_plan* plan, int groups) {
 // already describes it (item lists grouped by gb).
 ifnso_status upload_ifnso_meta(ifnso_plan* plan, const Layout& ly, const ifnso_batch_desc* batch, void* const* out,
                                uint8_t* ws, const ifnso_coeffs* coeffs, const std::vector<int>& gb,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, bool on_chip = false) {
   const int groups = static_cast<int>(gb.size()) - 1;
-  const uint64_t sig = batch_sig(plan, batch, out, ws, coeffs, nullptr, 0, 0, 1000 + groups);
+  const uint64_t sig = batch_sig(plan, batch, out, ws, coeffs, nullptr, 0, 0, (on_chip ? 2000000 : 1000) + groups);
   if (plan->sig_valid && plan->sig == sig) return IFNSO_OK;
   ifnso_status st;
   if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
   uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
-  if ((st = build_ifnso_meta(ly, batch, out, ws, coeffs->host, coeffs->K, gb, meta)) != IFNSO_OK) return st;
+  if ((st = build_ifnso_meta(ly, batch, out, ws, coeffs->host, coeffs->K, gb, meta, on_chip)) != IFNSO_OK) return st;
   IFNSO_CUDA(cudaMemcpyAsync(ws, meta, ly.meta_bytes, cudaMemcpyHostToDevice, stream), "metadata upload");
+  plan->small_idx.clear();
+  for (int i = 0; i < ly.count; ++i)
+    if (ly.shp[i].h <= kSmallH) plan->small_idx.push_back(i);
   std::vector<WorkItem> tmp;
-  sym_items(ly.shp, gb, tmp, &plan->sym_off);
+  sym_items(ly.shp, gb, tmp, &plan->sym_off, on_chip);
   tmp.clear();
-  app_items(ly.shp, gb, tmp, &plan->app_off);
+  app_items(ly.shp, gb, tmp, &plan->app_off, on_chip);
   plan->sig = sig;
   plan->sig_valid = true;
   plan->groups = groups;
@@ -1086,6 +1103,7 @@ struct Run {
   bool whole;  // the whole batch in one go: per-pass timing events and IFNSO_OPT_STOP_AFTER apply
   bool update = false;  // the product updates weights in place: W <- W - lr s Y (ifnso_muon_step)
   float lr = 0.f;
+  bool on_chip = false;  // the on-chip path computes the matrices with h <= 128 (use_small)
 };
 
 // Coefficient rows of matrix `first` onwards (the SIMT kernels index a group from 0).
@@ -1147,45 +1165,55 @@ ifnso_status run_f32(const Run& r) {
   return IFNSO_OK;
 }
 
-// The on-chip path (small.cu) runs a call when every matrix has h <= 128 and
-// the call needs nothing it does not do: the proposal network inside the
-// call, Gelfand's q = 2 bound, the E4M3 Gram, the fused Muon update and the
-// stop-after testing aid stay on the tiled passes.
-bool small_eligible(const ifnso_plan* plan, const Layout& ly, const ifnso_coeffs* coeffs, bool update) {
+// The on-chip path (small.cu) takes the matrices with h <= 128 of a call
+// that needs nothing it does not do: the proposal network inside the call,
+// Gelfand's q = 2 bound, the E4M3 Gram, the fused Muon update and the
+// testing aids stay on the tiled passes.  In a batch that mixes sizes the
+// tiled passes skip those matrices (no work items; the scalar and set-up
+// kernels see their MatInfo flag).
+bool small_applies(const ifnso_plan* plan, const Layout& ly, const ifnso_coeffs* coeffs, bool update) {
   if (ly.f32 || ly.ns || ly.e4m3 || update || plan->stop_after >= 0 || plan->inject_stall) return false;
   if (plan->scale == IFNSO_SCALE_GELFAND2 || (coeffs && coeffs->mlp)) return false;
   if (ly.L > 30) return false;
   for (const Shape& s : ly.shp)
-    if (s.h > kSmallH) return false;
-  return true;
+    if (s.h <= kSmallH) return true;
+  return false;
 }
 
 bool use_small(const ifnso_plan* plan, const Layout& ly, const ifnso_coeffs* coeffs, bool update) {
-  if (plan->small == 2 || !small_eligible(plan, ly, coeffs, update)) return false;
+  if (plan->small == 2 || !small_applies(plan, ly, coeffs, update)) return false;
   if (plan->small == 1) return true;
   return plan->small_tuned != 2;
 }
 
-ifnso_status run_small(const Run& r, int first, int count) {
-  ifnso_plan* plan = r.plan;
+// The on-chip kernel over matrices first .. first + count - 1 (all with
+// h <= 128), or over the n_idx matrices listed at d_idx.
+cudaError_t launch_on_chip(const Run& r, int first, int count, const int32_t* d_idx) {
   const Layout& ly = *r.ly;
-  uint8_t* ws = r.ws;
-  IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal + first * sizeof(MatScalars), 0, count * sizeof(MatScalars),
-                             r.stream),
-             "scalar reset");
-  if (r.whole) IFNSO_CUDA(mark(plan, r.stream, true), "timing event");
-  const TcParams base = base_params<TcParams>(ws, ly, r.coeffs);
+  const TcParams base = base_params<TcParams>(r.ws, ly, r.coeffs);
   SmParams p{};
-  p.probs = reinterpret_cast<const SmProblem*>(ws + ly.off_small);
+  p.probs = reinterpret_cast<const SmProblem*>(r.ws + ly.off_small);
+  p.idx = d_idx;
   p.scal = base.scal;
   p.coef = base.coef;
   p.first = first;
   p.L = ly.L;
   p.k_split = ly.prec.k_split;
   p.p_split = ly.prec.p_split;
-  p.frob = plan->scale == IFNSO_SCALE_FROB;
-  p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
-  IFNSO_CUDA(launch_small(p, count, r.stream), "on-chip pass");
+  p.frob = r.plan->scale == IFNSO_SCALE_FROB;
+  p.wait_ms = static_cast<uint32_t>(r.plan->wait_ms);
+  return launch_small(p, count, r.stream);
+}
+
+// A range of matrices that all have h <= 128: one launch, timed as one pass.
+ifnso_status run_small(const Run& r, int first, int count) {
+  ifnso_plan* plan = r.plan;
+  const Layout& ly = *r.ly;
+  IFNSO_CUDA(cudaMemsetAsync(r.ws + ly.off_scal + first * sizeof(MatScalars), 0, count * sizeof(MatScalars),
+                             r.stream),
+             "scalar reset");
+  if (r.whole) IFNSO_CUDA(mark(plan, r.stream, true), "timing event");
+  IFNSO_CUDA(launch_on_chip(r, first, count, nullptr), "on-chip pass");
   if (r.whole) IFNSO_CUDA(mark(plan, r.stream, false), "timing event");
   return IFNSO_OK;
 }
@@ -1195,7 +1223,11 @@ ifnso_status run_small(const Run& r, int first, int count) {
 ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1, size_t app0, size_t app1) {
   ifnso_plan* plan = r.plan;
   const Layout& ly = *r.ly;
-  if (use_small(plan, ly, r.coeffs, r.update)) return run_small(r, first, count);
+  if (r.on_chip) {
+    bool all = true;
+    for (int i = first; i < first + count; ++i) all = all && ly.shp[i].h <= kSmallH;
+    if (all) return run_small(r, first, count);
+  }
   uint8_t* ws = r.ws;
   cudaStream_t stream = r.stream;
   const int L = ly.L;
@@ -1207,6 +1239,16 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   auto mark_pass = [&](bool start) { return whole ? mark(plan, stream, start) : cudaSuccess; };
   auto stop = [&](int stage) { return whole && plan->stop_after == stage; };
   IFNSO_CUDA(mark_pass(true), "timing event");
+  if (r.on_chip) {
+    // the matrices with h <= 128 in this range, on chip (timed with the Gram pass)
+    const auto& si = plan->small_idx;
+    const auto lo = std::lower_bound(si.begin(), si.end(), first);
+    const auto hi = std::lower_bound(si.begin(), si.end(), first + count);
+    if (hi > lo) {
+      const int32_t* d_idx = reinterpret_cast<const int32_t*>(ws + ly.off_small_idx) + (lo - si.begin());
+      IFNSO_CUDA(launch_on_chip(r, 0, static_cast<int>(hi - lo), d_idx), "on-chip pass");
+    }
+  }
   TcParams p = base_params<TcParams>(ws, ly, r.coeffs);
   // the tensor-core passes address scalars and coefficient rows by matrix
   // index; the SIMT kernels by position in the group
@@ -1264,9 +1306,10 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     IFNSO_CUDA(tc_launch(EPI_SQR_NORM, 1, 1, p, grid_for(plan, n_sym), stream), "Gelfand norm pass");
     IFNSO_CUDA(launch_gelfand(count, scal, stream), "Gelfand scale");
   }
-  // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo)
+  // prep stores D_1 as hi + lo when the first squaring is split (for L = 1: P as hi + lo);
+  // with fixed coefficients it also starts P = c_0 I - w_1 D_1
   const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
-  IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream), "prep");
+  IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream, 0, net ? 0 : 1), "prep");
   IFNSO_CUDA(mark_pass(false), "timing event");
   if (stop(1)) return IFNSO_OK;
   for (int j = 1; j <= L - 1; ++j) {
@@ -1281,9 +1324,10 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
     p.cta_group = cta_group(split ? kSplit : kPlain);
     if (!net) {
-      // P collects w_l D_l two terms at a time (squaring 1 writes it, odd squarings
-      // add D_j and D_{j+1}, even ones skip it; an even last squaring adds D_L)
-      p.p_mode = j == 1 ? 1 : ((j & 1) ? 2 : (j == L - 1 ? 3 : 0));
+      // every squaring folds -2 D_j into its MMAs and adds its own term
+      // -w_{j+1} D_{j+1}, from the FP32 accumulator, to P (started by prep);
+      // none reads D_j in its epilogue
+      p.p_mode = 3;
       p.feat = 0;
     } else {
       // proposed coefficients: squaring 1 only measures tr(D_1^4); squaring 2
@@ -1360,14 +1404,18 @@ ifnso_status orthogonalize_locked(ifnso_plan* plan, const ifnso_batch_desc* batc
   Layout ly = make_layout(plan, shp, 0, 0, plan->L + 1);
   if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
   uint8_t* ws = static_cast<uint8_t*>(workspace);
-  if ((st = upload_ifnso_meta(plan, ly, batch, out, ws, coeffs, {0, ly.count}, stream)) != IFNSO_OK) return st;
+  const bool on_chip = use_small(plan, ly, coeffs, update);
+  if ((st = upload_ifnso_meta(plan, ly, batch, out, ws, coeffs, {0, ly.count}, stream, on_chip)) != IFNSO_OK)
+    return st;
   int hpad_max = 0;
   for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
   Run r{plan, &ly, ws, coeffs, hpad_max, stream, true};
   r.update = update;
   r.lr = lr;
+  r.on_chip = on_chip;
   if (ly.f32) return run_f32(r);
-  return run_tc(r, 0, ly.count, 0, ly.n_sym, 0, ly.n_app);
+  // the item counts of the uploaded lists (without the on-chip path's matrices)
+  return run_tc(r, 0, ly.count, 0, plan->sym_off.back(), 0, plan->app_off.back());
 }
 
 }  // namespace
@@ -1640,7 +1688,7 @@ ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch
     ifnso_status sb = read_batch(plan, batch, shp);
     if (sb == IFNSO_OK) {
       const Layout ly = make_layout(plan, shp, 0, 0, L + 1);
-      if (small_eligible(plan, ly, coeffs, false)) {
+      if (small_applies(plan, ly, coeffs, false)) {
         double tot[3] = {0.0, 0.0, 0.0};
         for (int mode = 1; mode <= 2 && st == IFNSO_OK; ++mode) {
           plan->small = mode;
@@ -1689,7 +1737,8 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
   const int want = ly.f32 ? 1 : std::min(groups <= 0 ? 8 : groups, n);
   const std::vector<int> gb = group_bounds(shp, want, true);
   const int ng = static_cast<int>(gb.size()) - 1;
-  if ((st = upload_ifnso_meta(plan, ly, dev_batch, dev_out, ws, coeffs, gb, stream)) != IFNSO_OK) return st;
+  const bool on_chip = use_small(plan, ly, coeffs, false);
+  if ((st = upload_ifnso_meta(plan, ly, dev_batch, dev_out, ws, coeffs, gb, stream, on_chip)) != IFNSO_OK) return st;
   if ((st = ensure_copy_streams(plan, ng)) != IFNSO_OK) return st;
   const size_t esz = plan->dtype == IFNSO_BF16 ? 2 : 4;
   // timeline events only for eager calls (a captured event would stay reserved for its graph)
@@ -1726,7 +1775,8 @@ ifnso_status ifnso_orthogonalize_host(ifnso_plan* plan, const void* const* host_
   for (auto& sh : shp) hpad_max = std::max<int>(hpad_max, static_cast<int>(sh.hpad));
   for (int g = 0; g < ng; ++g) {
     cudaStream_t cs = (two && (g & 1)) ? plan->s_comp : stream;
-    const Run r{plan, &ly, ws, coeffs, hpad_max, cs, ly.f32 != 0};
+    Run r{plan, &ly, ws, coeffs, hpad_max, cs, ly.f32 != 0};
+    r.on_chip = on_chip;
     IFNSO_CUDA(cudaStreamWaitEvent(cs, plan->ev_in[g], 0), "cudaStreamWaitEvent");
     if (ly.f32)
       st = run_f32(r);

@@ -152,6 +152,8 @@ struct MatInfo {
   void* out;
   int64_t rows, cols, ld;  // M's own shape
   int32_t h, w, hpad, trans;
+  int32_t on_chip;         // the on-chip path (small.cu) computes this matrix: the tiled passes skip it
+  int32_t pad_;
   float* gp;               // h_pad x h_pad FP32: T_0, then P
   void* d[4];              // D buffer 0 hi, lo; D buffer 1 hi, lo
   void* x[2];              // NS: X ping-pong (M's layout, leading dimension xld)
@@ -179,7 +181,9 @@ struct SmParams {
   const SmProblem* probs;
   MatScalars* scal;
   CoefTable coef;
-  int32_t first;    // matrix index of CTA 0
+  const int32_t* idx;  // matrix of CTA b: idx[b] (a list of the batch's matrices with h <= 128), or
+                       // first + b when idx is null
+  int32_t first;    // matrix index of CTA 0 (idx null)
   int32_t L;
   int32_t k_split;  // squarings 1..k_split multiply split (hi + lo) FP16 operands
   int32_t p_split;  // P enters the product as BF16 hi + lo
@@ -201,8 +205,10 @@ cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out
 cudaError_t launch_scalars(const MatInfo* d_mats, int count, MatScalars* scal, CoefTable coef,
                            int L, int scale_frob, int from_norm2, cudaStream_t s);
 // d_only: write D_1 only (no P, T_0 kept), for the norm pass of Gelfand scaling.
+// write_p (tensor-core path): also write P = c_0 I - w_1 D_1 (FP32) over T_0.
 cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
-                        CoefTable coef, int L, int split, int f32, cudaStream_t s, int d_only = 0);
+                        CoefTable coef, int L, int split, int f32, cudaStream_t s, int d_only = 0,
+                        int write_p = 0);
 // Gelfand scaling with q = 2: from o = ||T_0||_F and spare[0] = ||(T_0/o)^2||_F^2,
 // o <- ||T_0^2||_F^(1/2) = o spare[0]^(1/4), with 1/o and 1/sqrt(o) to match.
 cudaError_t launch_gelfand(int count, MatScalars* scal, cudaStream_t s);

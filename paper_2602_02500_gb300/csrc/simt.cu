@@ -196,9 +196,10 @@ __global__ void __launch_bounds__(256) k_cast_e4m3(const MatInfo* mats, const Ma
 // Gram scaling of Sec. 2, ||A||_F^2 = tr T_0 for the Frobenius scaling), its
 // FP32 reciprocals, the D-basis identity weight c0 = 1 + sum_{l=1}^L w_l in
 // FP64, and the zero / non-finite status bits.
-__global__ void k_scalars(int count, MatScalars* scal, CoefTable coef, int L, int frob) {
+__global__ void k_scalars(const MatInfo* mats, int count, MatScalars* scal, CoefTable coef, int L, int frob) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= count) return;
+  if (mats && mats[m].on_chip) return;  // the on-chip path wrote this matrix's scalars
   MatScalars& s = scal[m];
   const double s2 = frob ? s.trace : sqrt(s.o2);
   int st = s.status;
@@ -241,9 +242,10 @@ __global__ void k_gelfand(int count, MatScalars* scal) {
 // is no squaring: P itself is written as BF16 (hi, lo) into D buffer 0.
 // FP32 plans store D_1 in FP32 in D buffer 0 and P in place of T_0.
 __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* scal, CoefTable coef,
-                                              int L, int split, int f32, int d_only) {
+                                              int L, int split, int f32, int d_only, int write_p) {
   const int m = blockIdx.y;
   const MatInfo& mi = mats[m];
+  if (mi.on_chip) return;  // computed by the on-chip path
   const int64_t hp = mi.hpad;
   const int64_t n = hp * hp;
   const float inv = scal[m].inv_s2;
@@ -321,7 +323,12 @@ __global__ void __launch_bounds__(256) k_prep(const MatInfo* mats, MatScalars* s
       }
       *reinterpret_cast<uint4*>(static_cast<__half*>(mi.d[0]) + e) = uh;
       if (split) *reinterpret_cast<uint4*>(static_cast<__half*>(mi.d[1]) + e) = ul;
-      // P itself is first written by the first squaring (with its first two terms)
+      if (write_p) {
+        // P = c0 I - w_1 D_1 in FP32, over T_0 (the squarings add their terms to it)
+        reinterpret_cast<float4*>(gp + e)[0] = make_float4(p[0], p[1], p[2], p[3]);
+        reinterpret_cast<float4*>(gp + e)[1] = make_float4(p[4], p[5], p[6], p[7]);
+      }
+      // (otherwise the first squaring writes P, with its first two terms)
     }
   }
 }
@@ -494,16 +501,16 @@ cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out
   return cudaGetLastError();
 }
 
-cudaError_t launch_scalars(const MatInfo*, int count, MatScalars* scal, CoefTable coef, int L,
+cudaError_t launch_scalars(const MatInfo* d_mats, int count, MatScalars* scal, CoefTable coef, int L,
                            int scale_frob, int, cudaStream_t s) {
   if (count == 0) return cudaSuccess;
-  k_scalars<<<(count + 127) / 128, 128, 0, s>>>(count, scal, coef, L, scale_frob);
+  k_scalars<<<(count + 127) / 128, 128, 0, s>>>(d_mats, count, scal, coef, L, scale_frob);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScalars* scal,
-                        CoefTable coef, int L, int split, int f32, cudaStream_t s, int d_only) {
+                        CoefTable coef, int L, int split, int f32, cudaStream_t s, int d_only, int write_p) {
   if (count == 0) return cudaSuccess;
   const int64_t n = static_cast<int64_t>(hpad_max) * hpad_max;
   int gx = static_cast<int>((n + 256 * 8 - 1) / (256 * 8));
@@ -513,7 +520,7 @@ cudaError_t launch_prep(const MatInfo* d_mats, int count, int hpad_max, MatScala
     gx = nb * (nb + 1) / 2;
   }
   dim3 grid(gx, count);
-  k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32, d_only);
+  k_prep<<<grid, 256, 0, s>>>(d_mats, scal, coef, L, split, f32, d_only, write_p);
   count_launch();
   return cudaGetLastError();
 }

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int mi = p.first + static_cast<int>(blockIdx.x);
+  const int mi = p.idx ? p.idx[blockIdx.x] : p.first + static_cast<int>(blockIdx.x);
   const SmProblem& pr = p.probs[mi];
   const int L = p.L;
   const int h = pr.h, w = pr.w;

@@ -129,3 +129,45 @@ def test_autotuner_measures_the_small_bucket():
     torch.cuda.synchronize()
     for x, y in zip(xs, ys):
         assert rel(to_np(y), O.ifnso_alg1(to_np(x), w)) < 2e-2
+
+
+@pytest.mark.parametrize("L", [4, 14])
+def test_mixed_batch_small_on_chip_rest_tiled(L):
+    """A batch mixing h <= 128 and larger matrices: the small ones go to the
+    on-chip path, the tiled passes skip them; every output matches the
+    oracle, and the same batch with the on-chip path off agrees."""
+    import torch
+
+    F = lib()
+    shapes = [(128, 512), (300, 700), (64, 64), (256, 256), (640, 100), (96, 1000), (513, 1030), (17, 33),
+              (129, 400)]
+    mats = [synth.gaussian(500 + i, r, c) for i, (r, c) in enumerate(shapes)]
+    plan, xs, ys, w, st, o, tr = run(F, mats, L, small=1)
+    assert np.all(st == 0)
+    _, _, yt, _, st2, o2, tr2 = run(F, mats, L, small=2)
+    for x, y, z, oo, oo2 in zip(xs, ys, yt, o, o2):
+        A = to_np(x)
+        ref = O.ifnso_alg1(A, w)
+        assert rel(y, ref) < 2e-2, A.shape
+        assert rel(z, ref) < 2e-2, A.shape
+        Ao = O.orient(A)[0]
+        G = Ao @ Ao.T
+        assert abs(oo - np.linalg.norm(G)) <= 1e-5 * np.linalg.norm(G)
+        assert abs(oo2 - np.linalg.norm(G)) <= 1e-5 * np.linalg.norm(G)
+    # the large ones took the same tiled passes either way
+    for i, (r, c) in enumerate(shapes):
+        if min(r, c) > 128:
+            assert np.array_equal(ys[i], yt[i]), shapes[i]
+    # grouped host-buffer path over the mixed batch
+    hin = []
+    for x in xs:
+        r, c = x.shape
+        buf = torch.empty((r, x.stride(0)), dtype=x.dtype, pin_memory=True)[:, :c]
+        buf.copy_(x)
+        hin.append(buf)
+    hout = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+    dev_out = [torch.empty(x.shape, dtype=x.dtype, device="cuda") for x in xs]
+    plan.orthogonalize_host(hin, F.Batch(xs), np.r_[1.0, w], dev_out, hout, groups=3)
+    torch.cuda.synchronize()
+    for i in range(len(xs)):
+        assert rel(to_np(hout[i]), ys[i]) < 1e-6, shapes[i]
