@@ -772,19 +772,24 @@ def main():
     in_bytes = sum(x.numel() * x.element_size() for x in xs)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=device) if in_bytes < (258 << 20) else None
 
-    def timed_steps(step, k):
-        """Milliseconds of k steps (max over ranks), the L2 flushed before each if needed."""
+    per_step_ms = {}
+
+    def timed_steps(step, k, name=None):
+        """Milliseconds of k steps (max over ranks), the L2 flushed before each if needed.
+        Events between the steps (recorded without a synchronize) give each step's time."""
         barrier()
         torch.cuda.synchronize()
         if flush is None:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(k):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+            evs[0].record(stream)
+            for i in range(k):
                 step()
-            b.record(stream)
+                evs[i + 1].record(stream)
             torch.cuda.synchronize()
             barrier()
-            return max_over_ranks(a.elapsed_time(b))
+            if name:
+                per_step_ms[name] = [round(evs[i].elapsed_time(evs[i + 1]), 3) for i in range(k)]
+            return max_over_ranks(evs[0].elapsed_time(evs[k]))
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         for a, b in evs:
             flush.fill_(1)
@@ -799,7 +804,7 @@ def main():
     clocks.start()
     time.sleep(0.3)
     n0 = F.launch_count()
-    ms_total = timed_steps(ifnso_step, args.steps)
+    ms_total = timed_steps(ifnso_step, args.steps, "ifnso")
     launches = ifnso_launches * args.steps if ifnso_launches is not None else F.launch_count() - n0
     clk = clocks.stop()
     ms_step = ms_total / args.steps
@@ -931,7 +936,7 @@ def main():
         for _ in range(max(args.warmup, 3)):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_ms = timed_steps(e2e_step, args.steps)
+        e2e_ms = timed_steps(e2e_step, args.steps, "e2e")
         # host time spent enqueueing one call (the GPU waits if this exceeds the call's device time)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -969,6 +974,7 @@ def main():
                "api": "ifnso_orthogonalize_host, page-locked host buffers, "
                       + (f"{args.groups} groups" if args.groups > 0 else "default grouping"),
                "host_enqueue_ms": host_ms,
+               "per_step_ms": per_step_ms.get("e2e"),
                "copies_alone": {"h2d_ms": h2d_ms, "h2d_GBs": bi / h2d_ms / 1e6, "d2h_ms": d2h_ms,
                                 "d2h_GBs": bi / d2h_ms / 1e6, "both_directions_at_once_ms": both_ms},
                "timeline": {"what": "last timed step, per group: [uploads done, passes done, downloads done] "

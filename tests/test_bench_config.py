@@ -80,7 +80,7 @@ def test_committed_traffic_counters_belong_to_the_kernel_source():
     # algorithmic bytes per launch on the 1B list: 168 matrices with h = 2048, upper
     # 256-blocks (36 of 64) of 2048 x 2048, bytes per element as in the pass profiles
     upper = 36 * 256 * 256
-    per = {"squaring_split_p": 16, "squaring_split_fold": 8, "squaring_plain_p": 12, "squaring_plain_fold": 4}
+    per = {"squaring_split_fold": 16, "squaring_plain_fold": 12}
     for k, b in per.items():
         alg = 168 * upper * b
         assert 0.85 * alg <= t["muon_1b:" + k] <= 1.15 * alg, (k, t["muon_1b:" + k], alg)
