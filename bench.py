@@ -904,6 +904,9 @@ def main():
     # 5-step quintic Newton-Schulz on the same list
     nsplan = F.Plan(hmax, wmax, dtype, L=1)
     nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
+    if dtype == "bf16" and plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS):
+        # the baseline runs its passes in the modes the autotuner chose for IFNSO's passes of the same shape
+        nsplan.set(F.IFNSO_OPT_CTA_GROUP_KINDS, plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS))
     nsplan.set(F.IFNSO_OPT_TIMING, 1)
     nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
     zs = [torch.empty(x.shape, dtype=x.dtype, device=device) for x in xs]
@@ -1025,6 +1028,8 @@ def main():
                                  "gelfand2": "X = A / ||(A A^T)^2||_F^(1/4) (Gelfand, q = 2)"}[args.scale]},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
+                    "mma": "the autotuned modes of IFNSO's Gram, plain squarings and product"
+                           if dtype == "bf16" and plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS) else "per-CTA MMAs",
                     "ifnso_over_ns5": value / ns_value,
                     "pass_ms_per_step": [float(x) for x in ns_pass],
                     "passes": "norm and scalars, then per step: Gram S = X X^T, B = b S + c S^2, X <- a X + B X"},

@@ -138,7 +138,16 @@ typedef enum {
   /* Read only (ifnso_plan_get): what ifnso_plan_autotune chose for batches
    * the on-chip path applies to: 0 not measured, 1 the on-chip path, 2 the
    * tiled passes. */
-  IFNSO_OPT_SMALL_TUNED = 13
+  IFNSO_OPT_SMALL_TUNED = 13,
+  /* The MMA mode per pass kind that the tensor-core passes use when
+   * IFNSO_OPT_CTA_GROUP is 0, packed two bits per kind (bits 0-1 the Gram,
+   * 2-3 the split squarings, 4-5 the plain squarings, 6-7 the product; each
+   * 1 or 2 as for IFNSO_OPT_CTA_GROUP).  Get: what ifnso_plan_autotune chose,
+   * or 0 before it ran.  Set: those modes, e.g. another plan's choice on the
+   * same batch; 0 returns to the untuned defaults.  ns_iterate runs its Gram,
+   * its squaring S^2 and its product in the Gram's, the plain squarings' and
+   * the product's modes. */
+  IFNSO_OPT_CTA_GROUP_KINDS = 14
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };

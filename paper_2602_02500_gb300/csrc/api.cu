@@ -189,6 +189,7 @@ struct Layout {
   size_t off_mats = 0, off_probs = 0, off_items_sym = 0, off_items_app = 0, off_coef = 0, off_rows = 0;
   size_t off_small = 0;  // SmProblem per matrix (BF16 plans): the on-chip path for h <= 128
   size_t off_small_idx = 0;  // int32 per matrix: the matrices the on-chip path computes
+  size_t off_small_ns = 0;   // SmNsProblem per matrix (BF16 Newton-Schulz layouts)
   size_t n_probs = 0, n_sym = 0, n_app = 0;
   size_t prob_bytes = 0;
   size_t meta_bytes = 0;
@@ -399,6 +400,10 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
     off = a64(off + n * sizeof(SmProblem));
     ly.off_small_idx = off;
     off = a64(off + n * sizeof(int32_t));
+  }
+  if (!ly.f32 && ns) {
+    ly.off_small_ns = off;
+    off = a64(off + n * sizeof(SmNsProblem));
   }
   ly.meta_bytes = off;
   off = a1k(off);
@@ -756,6 +761,32 @@ ifnso_status build_ns_meta(const Layout& ly, const ifnso_batch_desc* b, void* co
   const int steps = ly.steps;
   MatInfo* mats = reinterpret_cast<MatInfo*>(meta + ly.off_mats);
   for (int i = 0; i < n; ++i) mats[i] = mat_info(ly, b, out, ws, i);
+  if (!ly.f32) {
+    // the on-chip path's views (h <= 128): the input and the two X buffers, M's layout
+    SmNsProblem* sp = reinterpret_cast<SmNsProblem*>(meta + ly.off_small_ns);
+    for (int i = 0; i < n; ++i) {
+      const Shape& s = ly.shp[i];
+      if (s.h > kSmallH) continue;
+      SmNsProblem& q = sp[i];
+      const void* src[3] = {mats[i].in, mats[i].x[0], mats[i].x[1]};
+      const int64_t ld[3] = {s.ld, mats[i].xld, mats[i].xld};
+      for (int m = 0; m < 3; ++m) {
+        bool ok;
+        if (!s.trans)
+          ok = encode2d(&q.mapG[m], bf16_t(), src[m], s.cols, s.rows, ld[m], 64, 128) &&
+               encode2d(&q.mapY[m], bf16_t(), src[m], s.cols, s.rows, ld[m], 64, 64);
+        else
+          ok = encode2d(&q.mapG[m], bf16_t(), src[m], s.cols, s.rows, ld[m], 64, 64) &&
+               encode2d(&q.mapY[m], bf16_t(), src[m], s.cols, s.rows, ld[m], 64, 256);
+        if (!ok) return fail(IFNSO_ERR_CUDA, "cuTensorMapEncodeTiled failed (matrix %d, on-chip NS)", i);
+      }
+      q.out = mats[i].out;
+      q.ld_out = s.cols;
+      q.h = static_cast<int32_t>(s.h);
+      q.w = static_cast<int32_t>(s.w);
+      q.trans = static_cast<int32_t>(s.trans);
+    }
+  }
   auto xcur = [&](int i, int st) -> const void* { return st == 0 ? mats[i].in : mats[i].x[(st - 1) % 2]; };
   auto xcur_ld = [&](int i, int st) -> int64_t { return st == 0 ? ly.shp[i].ld : mats[i].xld; };
   auto xnext = [&](int i, int st) -> void* { return st == steps - 1 ? mats[i].out : mats[i].x[st % 2]; };
@@ -1505,6 +1536,21 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "small matrices %lld (0, 1 or 2)", (long long)value);
       plan->small = static_cast<int>(value);
       return IFNSO_OK;  // the metadata holds both paths' views
+    case IFNSO_OPT_CTA_GROUP_KINDS: {
+      if (value == 0) {
+        plan->tuned = false;
+        return IFNSO_OK;
+      }
+      int m[kKinds];
+      for (int k = 0; k < kKinds; ++k) {
+        m[k] = static_cast<int>((value >> (2 * k)) & 3);
+        if (m[k] != 1 && m[k] != 2) return fail(IFNSO_ERR_INVALID_ARG, "cta group kinds %lld", (long long)value);
+      }
+      if (value >> (2 * kKinds)) return fail(IFNSO_ERR_INVALID_ARG, "cta group kinds %lld", (long long)value);
+      for (int k = 0; k < kKinds; ++k) plan->cg_kind[k] = m[k];
+      plan->tuned = true;
+      return IFNSO_OK;
+    }
     default:
       return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
@@ -1530,6 +1576,13 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_HOST_STREAMS: *value = plan->host_streams; return IFNSO_OK;
     case IFNSO_OPT_SMALL_MATRICES: *value = plan->small; return IFNSO_OK;
     case IFNSO_OPT_SMALL_TUNED: *value = plan->small_tuned; return IFNSO_OK;
+    case IFNSO_OPT_CTA_GROUP_KINDS: {
+      int64_t v = 0;
+      if (plan->tuned)
+        for (int k = 0; k < kKinds; ++k) v |= static_cast<int64_t>(plan->cg_kind[k]) << (2 * k);
+      *value = v;
+      return IFNSO_OK;
+    }
     default: return fail(IFNSO_ERR_INVALID_ARG, "unknown option %d", (int)option);
   }
 }
@@ -1850,6 +1903,24 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
   }
   IFNSO_CUDA(cudaMemsetAsync(ws + ly.off_scal, 0, n * sizeof(MatScalars), stream), "scalar reset");
   IFNSO_CUDA(mark(plan, stream, true), "timing event");
+  bool all_small = !ly.f32 && plan->small != 2 && !plan->inject_stall;
+  for (auto& sh : shp) all_small = all_small && sh.h <= kSmallH;
+  if (all_small) {
+    // every matrix has h <= 128: the whole iteration on chip, one launch
+    SmNsParams q{};
+    q.probs = reinterpret_cast<const SmNsProblem*>(ws + ly.off_small_ns);
+    q.scal = scal;
+    q.first = 0;
+    q.steps = steps;
+    q.degree = degree;
+    q.wait_ms = static_cast<uint32_t>(plan->wait_ms);
+    q.a = static_cast<float>(poly[0]);
+    q.b = static_cast<float>(poly[1]);
+    q.c = degree == 5 ? static_cast<float>(poly[2]) : 0.f;
+    IFNSO_CUDA(launch_small_ns(q, n, stream), "on-chip NS");
+    IFNSO_CUDA(mark(plan, stream, false), "timing event");
+    return IFNSO_OK;
+  }
   // ||A||_F^2 into the trace slot, then the scalars with the Frobenius scale
   int gx = std::max(1, std::min(1024, 16 * plan->num_sms / std::max(1, n)));
   IFNSO_CUDA(launch_norm2(d_mats, n, plan->dtype == IFNSO_BF16, &scal[0].trace,
@@ -1887,7 +1958,10 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
   }
   TcParams p{};
   p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
-  p.cta_group = plan->cta_group ? plan->cta_group : 1;
+  // MMA mode per pass: the plan's setting, else the autotuned mode of the
+  // IFNSO pass of the same shape (Gram; squaring of one h x h operand;
+  // product), else per-CTA MMAs
+  auto ns_cg = [&](int kind) { return plan->cta_group ? plan->cta_group : (plan->tuned ? plan->cg_kind[kind] : 1); };
   p.scal = scal;
   p.ns_a = a;
   p.ns_b = b;
@@ -1901,16 +1975,19 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
     p.probs = probs + ly.pi_ns_gram + s * n;
     p.items = sym;
     p.n_items = static_cast<int32_t>(ly.n_sym);
+    p.cta_group = ns_cg(kGram);
     IFNSO_CUDA(tc_launch(EPI_NS_GRAM, 1, 1, p, grid_for(plan, ly.n_sym), stream), "NS Gram");
     IFNSO_CUDA(mark(plan, stream, false), "timing event");
     if (degree == 5) {
       p.probs = probs + ly.pi_ns_sqr;
+      p.cta_group = ns_cg(kPlain);
       IFNSO_CUDA(tc_launch(EPI_NS_SQR, 1, 1, p, grid_for(plan, ly.n_sym), stream), "NS square");
       IFNSO_CUDA(mark(plan, stream, false), "timing event");
     }
     p.probs = probs + ly.pi_ns_apply + s * n;
     p.items = app;
     p.n_items = static_cast<int32_t>(ly.n_app);
+    p.cta_group = ns_cg(kApply);
     IFNSO_CUDA(tc_launch(EPI_NS_APPLY, 1, 1, p, grid_for(plan, ly.n_app), stream), "NS apply");
     IFNSO_CUDA(mark(plan, stream, false), "timing event");
   }

@@ -191,6 +191,29 @@ struct SmParams {
   uint32_t wait_ms;
 };
 
+// One matrix of the on-chip Newton-Schulz baseline (h <= 128): views of the
+// input A and of two workspace buffers X0, X1 (M's layout) for the Gram
+// (mapG) and as the product's B operand and store target (mapY).
+struct SmNsProblem {
+  CUtensorMap mapG[3];  // A, X0, X1
+  CUtensorMap mapY[3];
+  void* out;            // Y in M's shape, BF16, leading dimension ld_out
+  int64_t ld_out;
+  int32_t h, w, trans, pad;
+  int32_t pad2[8];
+};
+static_assert(sizeof(SmNsProblem) % 64 == 0, "SmNsProblem arrays must keep every tensor map 64-byte aligned");
+
+struct SmNsParams {
+  const SmNsProblem* probs;
+  MatScalars* scal;
+  int32_t first;
+  int32_t steps;
+  int32_t degree;  // 5 quintic, 3 cubic
+  uint32_t wait_ms;
+  float a, b, c;   // X <- a X + (b S + c S^2) X
+};
+
 // ------------------------------------------------------------ launchers
 // (defined in tc_gemm.cu / simt.cu / learn.cu; called by api.cu)
 // Launches clusters of two CTAs (at most max_clusters, at most one per item;
@@ -199,6 +222,7 @@ cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_cluste
 int tc_smem_bytes(int na, int nb, int cta_group);
 // One CTA per matrix first .. first + count - 1 (every one with h <= 128).
 cudaError_t launch_small(const SmParams& p, int count, cudaStream_t s);
+cudaError_t launch_small_ns(const SmNsParams& p, int count, cudaStream_t s);
 
 cudaError_t launch_norm2(const MatInfo* d_mats, int count, int bf16, double* out,
                          int64_t out_stride, int grid_x, cudaStream_t s);

@@ -129,6 +129,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint
       "l"(tmap), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
+// Tiled store of the box at `src` (this CTA's shared memory, laid out as the
+// tensor map's box) to the tensor at coordinates (x, y), in this thread's
+// current bulk async-group; the box is clipped to the tensor's extents.
+__device__ __forceinline__ void tma_store_2d(const void* tmap, uint32_t src, int32_t x, int32_t y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(tmap),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+
 // A load into this CTA's shared memory whose completion is counted on an
 // mbarrier of the CTA pair (tcgen05 cta_group::2 kernels): `bar` may be the
 // peer CTA's barrier (a shared::cluster address from mapa_shared).
@@ -362,6 +371,12 @@ __device__ __forceinline__ uint64_t sdesc_plain(uint32_t saddr, uint32_t lbo, ui
 // async proxy (tensor-core operand reads).
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Order this thread's completed global writes (including bulk stores it has
+// waited for) before later async-proxy (TMA) reads of global memory.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // Instruction descriptor, kind::f16 with FP32 accumulation.

@@ -511,7 +511,453 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
   }
 }
 
+
+// ------------------------------------------------------------------------
+// The Newton-Schulz baseline (Sec. 1, Eqs. one_iteration_matrix and
+// iteration_jordan) on chip for h <= 128, one CTA per matrix: per step
+//   S = X X^T (tcgen05, X streamed over K = w), B = b S + c S^2 (quintic;
+//   the cubic iteration takes B = b S), X <- a X + B X (X streamed again in
+//   256-column tiles).
+// X_0 = A / ||A||_F with ||A||_F^2 = tr(A A^T) from the first Gram.  The
+// product's epilogue reads X from the shared-memory stages that hold its B
+// operand and writes X_{k+1} back into them; a TMA store moves them to a
+// workspace buffer (M's layout) that the next step streams in.  The last step
+// writes Y in M's shape.
+enum NsBar {
+  nGFull = 0,
+  nGEmpty = nGFull + kGramStages,
+  nAFull = nGEmpty + kGramStages,
+  nAEmpty = nAFull + kApplyStages,  // released by the epilogue once X_{k+1} has left the stage
+  nTFull = nAEmpty + kApplyStages,  // S, then S^2, in TMEM columns 0..127
+  nSReady,                          // S (BF16) written (8 epilogue warps)
+  nBReady,                          // B (BF16) written (8 epilogue warps)
+  nGDone,                           // this step's Gram products have read their stages
+  nT2Full,
+  nT2Empty = nT2Full + 2,
+  nXReady = nT2Empty + 2,           // X_{k+1} stored in global memory (one arrival)
+  nTileDone,                        // the 8 epilogue warps are done with a product tile's stages
+  nDrain,
+  nNumBars
+};
+static_assert(nNumBars * 8 + 8 + 8 * 8 <= 512, "barriers, TMEM slot, abort flag, 8 partial sums");
+
+// X(i, n) of a 256-column B-operand tile held as two K blocks (rows i of X),
+// from a stage laid out for the product: MN-major 64 x 64 chunks (M wide) or
+// 256 K-major rows (M tall, the tile's rows are n).
+__device__ __forceinline__ uint32_t xstage_off(bool trans, int i, int nl) {
+  const int kb = i >> 6, k = i & 63;
+  if (!trans) {
+    const int j = nl >> 6, c = nl & 63;
+    return static_cast<uint32_t>(kb * kApplyStage + 8192 * j + (k >> 3) * 1024 + (k & 7) * 128 +
+                                 ((((c >> 3) ^ (k & 7))) << 4) + (c & 7) * 2);
+  }
+  return static_cast<uint32_t>(kb * kApplyStage + (nl >> 3) * 1024 + (nl & 7) * 128 +
+                               ((((k >> 3) ^ (nl & 7))) << 4) + (k & 7) * 2);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_constant__ SmNsParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t ring = base;
+  uint8_t* sbuf = base_ptr + kRing;  // S (BF16 operand)
+  uint8_t* bbuf = sbuf + kOpBuf;     // B (BF16 operand)
+  const uint32_t sbuf_s = base + kRing, bbuf_s = sbuf_s + kOpBuf;
+  const uint32_t bar0 = base + kRing + 2 * kOpBuf;
+  auto bar = [&](int i) { return bar0 + 8u * static_cast<uint32_t>(i); };
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + kRing + 2 * kOpBuf + 8 * nNumBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float2* red = reinterpret_cast<float2*>(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int mi = p.first + static_cast<int>(blockIdx.x);
+  const SmNsProblem& pr = p.probs[mi];
+  const int h = pr.h, w = pr.w, steps = p.steps;
+  const bool quintic = p.degree == 5;
+  const int n_kb = (w + 63) / 64;
+  const int n_nt = (w + 255) / 256;
+  const unsigned long long tmo = p.wait_ms ? p.wait_ms * 1000000ull : kWaitTimeoutNs;
+  auto src_of = [&](int s) { return s == 0 ? 0 : 1 + ((s - 1) & 1); };  // A, X0, X1
+  auto dst_of = [&](int s) { return 1 + (s & 1); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGramStages; ++s) {
+      mbar_init(bar(nGFull + s), 1);
+      mbar_init(bar(nGEmpty + s), 1);
+    }
+    for (int s = 0; s < kApplyStages; ++s) {
+      mbar_init(bar(nAFull + s), 1);
+      mbar_init(bar(nAEmpty + s), 1);
+    }
+    mbar_init(bar(nTFull), 1);
+    mbar_init(bar(nSReady), 8);
+    mbar_init(bar(nBReady), 8);
+    mbar_init(bar(nGDone), 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(bar(nT2Full + a), 1);
+      mbar_init(bar(nT2Empty + a), 8);
+    }
+    mbar_init(bar(nXReady), 1);
+    mbar_init(bar(nTileDone), 8);
+    mbar_init(bar(nDrain), 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc<1>(smem_u32(tmem_slot), 512);
+    tmem_relinquish<1>();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  MatScalars* sc = p.scal + mi;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      for (int m = 0; m < 3; ++m) {
+        tmap_acquire(&pr.mapG[m]);
+        tmap_acquire(&pr.mapY[m]);
+      }
+      bool ok = true;
+      int g = 0, t = 0;  // Gram and product loads issued so far (over all steps)
+      for (int st = 0; st < steps && ok; ++st) {
+        const int si = src_of(st);
+        // X_st has been stored (and the previous step's stages are all free)
+        if (st > 0 && !mbar_wait(bar(nXReady), (st - 1) & 1, abort_flag, tmo)) ok = false;
+        if (st > 0) fence_proxy_async_global();
+        for (int kb = 0; kb < n_kb && ok; ++kb, ++g) {
+          const int s = g % kGramStages;
+          if (!mbar_wait(bar(nGEmpty + s), ((g / kGramStages) & 1) ^ 1u, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = bar(nGFull + s);
+          mbar_arrive_expect_tx(fb, kKBlock);
+          const uint32_t dst = ring + s * kKBlock;
+          if (!pr.trans) {
+            tma_load_2d(dst, &pr.mapG[si], fb, 64 * kb, 0);
+          } else {
+            tma_load_2d(dst, &pr.mapG[si], fb, 0, 64 * kb);
+            tma_load_2d(dst + 8192, &pr.mapG[si], fb, 64, 64 * kb);
+          }
+        }
+        if (ok && !mbar_wait(bar(nGDone), st & 1, abort_flag, tmo)) ok = false;
+        for (int q = 0; ok && q < 2 * n_nt; ++q, ++t) {
+          const int nt = q >> 1, kb = q & 1;
+          const int s = t % kApplyStages;
+          if (!mbar_wait(bar(nAEmpty + s), ((t / kApplyStages) & 1) ^ 1u, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = bar(nAFull + s);
+          mbar_arrive_expect_tx(fb, kApplyStage);
+          const uint32_t dst = ring + s * kApplyStage;
+          if (!pr.trans) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tma_load_2d(dst + 8192 * j, &pr.mapY[si], fb, 256 * nt + 64 * j, 64 * kb);
+          } else {
+            tma_load_2d(dst, &pr.mapY[si], fb, 64 * kb, 256 * nt);
+          }
+        }
+      }
+      if (!ok) {
+        atomicOr(&sc->status, kDevTimeout);
+        // let the copies issued last land: every ring stage's latest phase
+        for (int s = 0; s < kGramStages && s < g; ++s) {
+          const int last = s + ((g - 1 - s) / kGramStages) * kGramStages;
+          mbar_wait_bounded(bar(nGFull + s), (last / kGramStages) & 1, tmo);
+        }
+        for (int s = 0; s < kApplyStages && s < t; ++s) {
+          const int last = s + ((t - 1 - s) / kApplyStages) * kApplyStages;
+          mbar_wait_bounded(bar(nAFull + s), (last / kApplyStages) & 1, tmo);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      bool ok = true;
+      const uint32_t acc = tmem_base;
+      const uint32_t id_g = idesc_f16(1u, 128, 128, pr.trans ? 1u : 0u, pr.trans ? 1u : 0u);
+      const uint32_t id_s = idesc_f16(1u, 128, 128, 0u, 0u);
+      const uint32_t id_y = idesc_f16(1u, 128, 256, 0u, pr.trans ? 0u : 1u);
+      int g = 0, t = 0, ntg = 0;
+      for (int st = 0; st < steps && ok; ++st) {
+        if (st > 0) {
+          // the previous step's epilogue has drained every accumulator
+          if (!mbar_wait(bar(nXReady), (st - 1) & 1, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+        }
+        for (int kb = 0; kb < n_kb && ok; ++kb, ++g) {
+          const int s = g % kGramStages;
+          if (!mbar_wait(bar(nGFull + s), (g / kGramStages) & 1, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = ring + s * kKBlock;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t d = pr.trans ? sdesc_sw128(sa + k * 2048, 8192, 1024) : sdesc_sw128(sa + k * 32, 16, 1024);
+            umma_f16<1>(acc, d, d, id_g, (kb | k) != 0 ? 1u : 0u);
+          }
+          umma_commit<1>(bar(nGEmpty + s));
+        }
+        if (!ok) break;
+        umma_commit<1>(bar(nTFull));
+        umma_commit<1>(bar(nGDone));
+        if (quintic) {
+          if (!mbar_wait(bar(nSReady), st & 1, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t d = sdesc_sw128(sbuf_s + kb * kKBlock + k * 32, 16, 1024);
+              umma_f16<1>(acc, d, d, id_s, (kb | k) != 0 ? 1u : 0u);
+            }
+          umma_commit<1>(bar(nTFull));
+        }
+        if (!mbar_wait(bar(nBReady), st & 1, abort_flag, tmo)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int nt = 0; nt < n_nt && ok; ++nt, ++ntg) {
+          const int b = ntg & 1;
+          if (!mbar_wait(bar(nT2Empty + b), ((ntg >> 1) & 1) ^ 1u, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_t = tmem_base + static_cast<uint32_t>(256 * b);
+          for (int kb = 0; kb < 2 && ok; ++kb, ++t) {
+            const int s = t % kApplyStages;
+            if (!mbar_wait(bar(nAFull + s), (t / kApplyStages) & 1, abort_flag, tmo)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sb = ring + s * kApplyStage;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t bd = pr.trans ? sdesc_sw128(sb + k * 32, 16, 1024) : sdesc_sw128(sb + k * 2048, 8192, 1024);
+              const uint64_t ad = sdesc_sw128(bbuf_s + kb * kKBlock + k * 32, 16, 1024);
+              umma_f16<1>(d_t, ad, bd, id_y, (kb | k) != 0 ? 1u : 0u);
+            }
+            // (the stage is released by the epilogue, which reads X from it)
+          }
+          if (ok) umma_commit<1>(bar(nT2Full + b));
+        }
+      }
+      if (!ok) atomicOr(&sc->status, kDevTimeout);
+      umma_commit<1>(bar(nDrain));
+      mbar_wait_bounded(bar(nDrain), 0, tmo);
+    }
+  } else {
+    // -------------------------------------------------- epilogue (warps 2..9)
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = 32 * q + lane;
+    const uint32_t trow = tmem_base + (static_cast<uint32_t>(32 * q) << 16);
+    const bool leader = warp == 2 && lane == 0;
+    auto wait_bar = [&](uint32_t b, uint32_t parity) {
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(b, parity, abort_flag, tmo) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok) tc_fence_after();
+      return ok != 0;
+    };
+    auto load64 = [&](uint32_t col, float* v) {
+      uint32_t u[32];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        IFNSO_TMEM_LD32(trow + col + 32 * c, u);
+        IFNSO_TMEM_WAIT_LD(u);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) v[32 * c + t] = __uint_as_float(u[t]);
+      }
+    };
+    float d[64];
+    float inv_s2 = 0.f, inv_s = 0.f;
+    bool ok = true;
+    int tf = 0, ntg = 0, t = 0;
+    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(pr.out);
+    for (int st = 0; st < steps && ok; ++st) {
+      const bool last = st == steps - 1;
+      // S = X X^T (step 0: A A^T / ||A||_F^2)
+      ok = wait_bar(bar(nTFull), (tf++) & 1);
+      if (st == 0) {
+        float tr = 0.f;
+        if (ok) {
+          load64(64 * half, d);
+#pragma unroll
+          for (int k = 0; k < 64; ++k)
+            if (64 * half + k == row) tr += d[k];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        if (lane == 0) red[warp - 2] = make_float2(0.f, tr);
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // reached by every epilogue warp
+        double trace = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) trace += static_cast<double>(red[k].y);
+        const bool fin = isfinite(trace);
+        const bool pos = fin && trace > 0.0;
+        inv_s2 = pos ? static_cast<float>(1.0 / trace) : 0.f;
+        inv_s = pos ? static_cast<float>(1.0 / sqrt(trace)) : 0.f;
+        if (leader && ok) {
+          sc->trace = trace;
+          sc->s2 = trace;
+          sc->inv_s2 = inv_s2;
+          sc->inv_s = inv_s;
+          atomicOr(&sc->status, (!fin ? kDevNonFinite : 0) | ((fin && trace == 0.0) ? kDevZero : 0));
+        }
+#pragma unroll
+        for (int k = 0; k < 64; ++k) d[k] *= inv_s2;
+      } else if (ok) {
+        load64(64 * half, d);
+      }
+      if (!ok) break;
+      put_row<__nv_bfloat16>(sbuf, nullptr, row, half, d, false);  // d becomes the BF16 S
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(nSReady));
+      // B = b S + c S^2 (or b S)
+      if (quintic) {
+        if (!(ok = wait_bar(bar(nTFull), (tf++) & 1))) break;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint32_t u[32];
+          IFNSO_TMEM_LD32(trow + 64 * half + 32 * c, u);
+          IFNSO_TMEM_WAIT_LD(u);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) d[32 * c + k] = fmaf(p.c, __uint_as_float(u[k]), p.b * d[32 * c + k]);
+        }
+        tc_fence_before();
+      } else {
+#pragma unroll
+        for (int k = 0; k < 64; ++k) d[k] *= p.b;
+      }
+      put_row<__nv_bfloat16>(bbuf, nullptr, row, half, d, false);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(nBReady));
+      // X <- a X + B X, tile by tile; X comes from the stages of the product's B operand
+      const float sx = st == 0 ? inv_s : 1.f;
+      const int di = dst_of(st);
+      for (int nt = 0; nt < n_nt; ++nt, ++ntg, t += 2) {
+        const int b = ntg & 1;
+        if (!(ok = wait_bar(bar(nT2Full + b), (ntg >> 1) & 1))) break;
+        const uint8_t* stage0 = base_ptr + (t % kApplyStages) * kApplyStage;  // the tile's two stages are adjacent
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          const int nl = 128 * half + 32 * c;  // first column within the tile
+          const int col = 256 * nt + nl;
+          uint32_t u[32];
+          __syncwarp();
+          IFNSO_TMEM_LD32(trow + static_cast<uint32_t>(256 * b + nl), u);
+          IFNSO_TMEM_WAIT_LD(u);
+          float y[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const uint32_t off = xstage_off(pr.trans, row, nl + k);
+            const float x = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage0 + off));
+            y[k] = sx * fmaf(p.a, x, __uint_as_float(u[k]));
+          }
+          if (last) {
+            if (row < h && col < w) {
+              if (!pr.trans) {
+                __nv_bfloat16* dst = out + static_cast<int64_t>(row) * pr.ld_out + col;
+                if ((pr.ld_out & 7) == 0 && col + 32 <= w) {
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) reinterpret_cast<uint4*>(dst)[k] = pack8<__nv_bfloat16>(y + 8 * k);
+                } else {
+                  for (int k = 0; k < 32 && col + k < w; ++k) dst[k] = __float2bfloat16_rn(y[k]);
+                }
+              } else {
+                for (int k = 0; k < 32 && col + k < w; ++k)
+                  out[static_cast<int64_t>(col + k) * pr.ld_out + row] = __float2bfloat16_rn(y[k]);
+              }
+            }
+          } else {
+            // X_{st+1}(row, col + k) back into the stage, where the TMA store reads it
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+              *reinterpret_cast<__nv_bfloat16*>(const_cast<uint8_t*>(stage0) + xstage_off(pr.trans, row, nl + k)) =
+                  __float2bfloat16_rn(y[k]);
+          }
+        }
+        tc_fence_before();
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(bar(nT2Empty + b));
+          mbar_arrive(bar(nTileDone));
+        }
+        // the leader waits (bounded) until all 8 warps are done with the tile's stages
+        if (leader && !mbar_wait(bar(nTileDone), ntg & 1, abort_flag, tmo)) ok = false;
+        if (leader && ok) {
+          const int s0 = t % kApplyStages;
+          if (!last) {
+            const uint32_t src = ring + s0 * kApplyStage;
+            // only boxes that start inside X (the rest of a box is clipped)
+            for (int kb = 0; kb < 2 && 64 * kb < h; ++kb) {
+              if (!pr.trans) {
+                for (int j = 0; j < 4 && 256 * nt + 64 * j < w; ++j)
+                  tma_store_2d(&pr.mapY[di], src + kb * kApplyStage + 8192 * j, 256 * nt + 64 * j, 64 * kb);
+              } else {
+                tma_store_2d(&pr.mapY[di], src + kb * kApplyStage, 64 * kb, 256 * nt);
+              }
+            }
+            bulk_commit();
+            bulk_wait_read();  // the stages may be refilled once the stores have read them
+          }
+          mbar_arrive(bar(nAEmpty + s0));
+          mbar_arrive(bar(nAEmpty + (s0 + 1) % kApplyStages));
+        }
+      }
+      if (!ok) break;
+      if (!last && leader) {
+        bulk_wait_all();  // X_{st+1} is in global memory before the next step streams it
+        fence_proxy_async_global();
+        mbar_arrive(bar(nXReady));
+      }
+    }
+    if (leader) bulk_wait_all();  // no store in flight when the CTA exits (the timeout path)
+    if (!ok && lane == 0) atomicOr(&sc->status, kDevTimeout);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc<1>(tmem_base, 512);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_small_ns(const SmNsParams& p, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(small_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  small_ns_kernel<<<count, kThreads, kSmem, s>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t launch_small(const SmParams& p, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
