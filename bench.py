@@ -99,6 +99,8 @@ def parse():
                     help="end-to-end run: groups whose copies overlap the passes (0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the polar-distance and orthogonality report of the outputs")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
                     help="time eager calls instead of a captured CUDA graph of one step")
     ap.add_argument("--shard", action="store_true",
@@ -630,6 +632,39 @@ def run_reference(args):
     return 0
 
 
+def polar_quality(torch, shapes, xs, outs, max_shapes=3, max_h=2048):
+    """Distance to the polar factor U V^T (Frobenius, per sqrt(h)) and the
+    orthogonality error ||Y Y^T - I||_F of the GPU outputs, in FP64 on the
+    host, for the first matrix of each distinct shape (at most max_shapes
+    shapes with h <= max_h); U V^T from numpy's SVD of the same input.
+    Not timed."""
+    import numpy as np
+
+    t0 = time.perf_counter()
+    seen = {}
+    for i, (_, r, c) in enumerate(shapes):
+        if (r, c) not in seen and min(r, c) <= max_h:
+            seen[(r, c)] = i
+    res = {}
+    for (r, c), i in list(seen.items())[:max_shapes]:
+        A = xs[i].double().cpu().numpy()
+        tr = r > c
+        Ao = A.T if tr else A
+        U, _, Vt = np.linalg.svd(Ao, full_matrices=False)
+        Q = U @ Vt
+        h = Ao.shape[0]
+        entry = {}
+        for name, ys_ in outs.items():
+            Y = ys_[i].double().cpu().numpy()
+            Yo = Y.T if tr else Y
+            entry[name] = {"dist_polar": float(np.linalg.norm(Yo - Q) / np.sqrt(h)),
+                           "orth_err": float(np.linalg.norm(Yo @ Yo.T - np.eye(h)))}
+        res[f"{r}x{c}"] = entry
+    return {"what": "first matrix of each distinct shape: ||Y - U V^T||_F / sqrt(h) and ||Y Y^T - I||_F "
+                    "(oriented, h <= w), FP64 on the host from numpy's SVD of the input; not timed",
+            "shapes": res, "secs": round(time.perf_counter() - t0, 1)}
+
+
 def averaged_pass_times(plan, step, k):
     """Per-pass milliseconds of `step` (a call, or a graph replay, of a plan
     with IFNSO_OPT_TIMING on) averaged over k runs, each read back after a
@@ -919,7 +954,11 @@ def main():
     ns_ms = timed_steps(ns_step, args.steps)
     ns_pass, _ = averaged_pass_times(nsplan, ns_step, args.steps)
     ns_value = whole_job_rate(world, n, args.steps, ns_ms)
+    ns_on_chip = dtype == "bf16" and hmax <= 128
     ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
+    quality = None
+    if rank == 0 and not args.no_quality:
+        quality = polar_quality(torch, shapes, xs, {"ifnso": ys, "ns5": zs})
     del nsws, zs
 
     # end to end through the C ABI with host buffers: ifnso_orthogonalize_host
@@ -1028,11 +1067,14 @@ def main():
                                  "gelfand2": "X = A / ||(A A^T)^2||_F^(1/4) (Gelfand, q = 2)"}[args.scale]},
             "tflops": tflops,
             "ns5": {"value": ns_value, "unit": "matrices/s", "tflops": ns_tflops, "ms_per_step": ns_ms / args.steps,
-                    "mma": "the autotuned modes of IFNSO's Gram, plain squarings and product"
-                           if dtype == "bf16" and plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS) else "per-CTA MMAs",
+                    "mma": ("on-chip path (one CTA per matrix, every step in one launch)" if ns_on_chip
+                            else "the autotuned modes of IFNSO's Gram, plain squarings and product"
+                            if dtype == "bf16" and plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS) else "per-CTA MMAs"),
                     "ifnso_over_ns5": value / ns_value,
                     "pass_ms_per_step": [float(x) for x in ns_pass],
-                    "passes": "norm and scalars, then per step: Gram S = X X^T, B = b S + c S^2, X <- a X + B X"},
+                    "passes": ("one launch: per step S = X X^T, B = b S + c S^2, X <- a X + B X" if ns_on_chip else
+                               "norm and scalars, then per step: Gram S = X X^T, B = b S + c S^2, X <- a X + B X")},
+            "quality": quality,
             "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -490,12 +490,15 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
 #pragma unroll
             for (int t = 0; t < 4; ++t) reinterpret_cast<uint4*>(dst)[t] = pack8<__nv_bfloat16>(y + 8 * t);
           } else {
-            for (int t = 0; t < 32 && col + t < w; ++t) dst[t] = __float2bfloat16_rn(y[t]);
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+              if (col + t < w) dst[t] = __float2bfloat16_rn(y[t]);
           }
         } else {
           // M is tall: Y^T, element (row, col + t) goes to out[col + t][row]
-          for (int t = 0; t < 32 && col + t < w; ++t)
-            out[static_cast<int64_t>(col + t) * pr.ld_out + row] = __float2bfloat16_rn(y[t]);
+#pragma unroll
+          for (int t = 0; t < 32; ++t)
+            if (col + t < w) out[static_cast<int64_t>(col + t) * pr.ld_out + row] = __float2bfloat16_rn(y[t]);
         }
       }
       tc_fence_before();
@@ -541,16 +544,10 @@ enum NsBar {
 };
 static_assert(nNumBars * 8 + 8 + 8 * 8 <= 512, "barriers, TMEM slot, abort flag, 8 partial sums");
 
-// X(i, n) of a 256-column B-operand tile held as two K blocks (rows i of X),
-// from a stage laid out for the product: MN-major 64 x 64 chunks (M wide) or
-// 256 K-major rows (M tall, the tile's rows are n).
-__device__ __forceinline__ uint32_t xstage_off(bool trans, int i, int nl) {
+// Byte offset of X(i, n) (M tall: the tile's rows are n) in a 256-column
+// B-operand tile held as two stages of 256 K-major rows (128-byte swizzle).
+__device__ __forceinline__ uint32_t xstage_off_tall(int i, int nl) {
   const int kb = i >> 6, k = i & 63;
-  if (!trans) {
-    const int j = nl >> 6, c = nl & 63;
-    return static_cast<uint32_t>(kb * kApplyStage + 8192 * j + (k >> 3) * 1024 + (k & 7) * 128 +
-                                 ((((c >> 3) ^ (k & 7))) << 4) + (c & 7) * 2);
-  }
   return static_cast<uint32_t>(kb * kApplyStage + (nl >> 3) * 1024 + (nl & 7) * 128 +
                                ((((k >> 3) ^ (nl & 7))) << 4) + (k & 7) * 2);
 }
@@ -869,11 +866,30 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
           IFNSO_TMEM_LD32(trow + static_cast<uint32_t>(256 * b + nl), u);
           IFNSO_TMEM_WAIT_LD(u);
           float y[32];
+          // X(row, col + k): M wide, four 16-byte pieces of the row (one 128-byte
+          // swizzled row of a 64 x 64 chunk; eight consecutive rows hit eight
+          // distinct 16-byte bank groups); M tall, one value per 128-byte row
+          uint8_t* xrow = nullptr;
+          if (!pr.trans) {
+            xrow = const_cast<uint8_t*>(stage0) + (row >> 6) * kApplyStage + 8192 * (nl >> 6) + (row & 63) * 128;
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const uint32_t off = xstage_off(pr.trans, row, nl + k);
-            const float x = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage0 + off));
-            y[k] = sx * fmaf(p.a, x, __uint_as_float(u[k]));
+            for (int v = 0; v < 4; ++v) {
+              const uint4 q8 = *reinterpret_cast<const uint4*>(xrow + (((((nl & 63) >> 3) + v) ^ (row & 7)) << 4));
+              const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&q8);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const float2 f = __bfloat1622float2(e[t]);
+                y[8 * v + 2 * t] = sx * fmaf(p.a, f.x, __uint_as_float(u[8 * v + 2 * t]));
+                y[8 * v + 2 * t + 1] = sx * fmaf(p.a, f.y, __uint_as_float(u[8 * v + 2 * t + 1]));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const uint32_t off = xstage_off_tall(row, nl + k);
+              const float x = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(stage0 + off));
+              y[k] = sx * fmaf(p.a, x, __uint_as_float(u[k]));
+            }
           }
           if (last) {
             if (row < h && col < w) {
@@ -883,19 +899,29 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
 #pragma unroll
                   for (int k = 0; k < 4; ++k) reinterpret_cast<uint4*>(dst)[k] = pack8<__nv_bfloat16>(y + 8 * k);
                 } else {
-                  for (int k = 0; k < 32 && col + k < w; ++k) dst[k] = __float2bfloat16_rn(y[k]);
+#pragma unroll
+                  for (int k = 0; k < 32; ++k)
+                    if (col + k < w) dst[k] = __float2bfloat16_rn(y[k]);
                 }
               } else {
-                for (int k = 0; k < 32 && col + k < w; ++k)
-                  out[static_cast<int64_t>(col + k) * pr.ld_out + row] = __float2bfloat16_rn(y[k]);
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                  if (col + k < w) out[static_cast<int64_t>(col + k) * pr.ld_out + row] = __float2bfloat16_rn(y[k]);
               }
             }
           } else {
             // X_{st+1}(row, col + k) back into the stage, where the TMA store reads it
+            if (!pr.trans) {
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
-              *reinterpret_cast<__nv_bfloat16*>(const_cast<uint8_t*>(stage0) + xstage_off(pr.trans, row, nl + k)) =
-                  __float2bfloat16_rn(y[k]);
+              for (int v = 0; v < 4; ++v)
+                *reinterpret_cast<uint4*>(xrow + (((((nl & 63) >> 3) + v) ^ (row & 7)) << 4)) =
+                    pack8<__nv_bfloat16>(y + 8 * v);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k)
+                *reinterpret_cast<__nv_bfloat16*>(const_cast<uint8_t*>(stage0) + xstage_off_tall(row, nl + k)) =
+                    __float2bfloat16_rn(y[k]);
+            }
           }
         }
         tc_fence_before();

@@ -347,6 +347,26 @@ __device__ __forceinline__ void store_blk(T* buf, int64_t ld, int r0, int c0, co
   }
 }
 
+// Add the 32 x 32 FP32 block (lane t: row r0 + t, columns c0..c0+31) into
+// buf in L2 through the bulk-copy engine: each lane stages its row, 64 bytes
+// at a time, and issues a bulk reduction of it.  Rows 16-byte aligned.
+__device__ __forceinline__ void red_blk_bulk(float* buf, int64_t ld, int r0, int c0, const float* v, float* st) {
+  const int lane = threadIdx.x & 31;
+  uint8_t* row = reinterpret_cast<uint8_t*>(st) + lane * 80;
+  float* dst = buf + static_cast<int64_t>(r0 + lane) * ld + c0;
+#pragma unroll
+  for (int pc = 0; pc < 2; ++pc) {
+    st_acquire();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(row + 16 * q) =
+          make_float4(v[16 * pc + 4 * q], v[16 * pc + 4 * q + 1], v[16 * pc + 4 * q + 2], v[16 * pc + 4 * q + 3]);
+    fence_proxy_async_smem();
+    bulk_red_add_f32(dst + 16 * pc, smem_u32(row), 64);
+    bulk_commit();
+  }
+}
+
 // BF16 output block of the tile (rows r0.., columns c0..), clipped to the
 // output; with out_trans the tile is the transpose of the output.
 __device__ __forceinline__ void store_out_bf16(const TcProblem& pr, int r0, int c0, const float* v, float* st) {
@@ -494,8 +514,15 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
     }
     if (!p.final_pass) {
       if (p.p_mode == 2 || p.p_mode == 3) {
-        blk_put(st, pv);
-        blk_red_add(pr.pacc + static_cast<int64_t>(r0) * pr.ld_aux + c0, pr.ld_aux, st);
+        // split operands (three products per K step, a long main loop): the
+        // bulk-copy engine; one product per K step: vector reductions from the
+        // threads, which leave the bulk-copy engine to the operand loads
+        if (p.read_lo) {
+          red_blk_bulk(pr.pacc, pr.ld_aux, r0, c0, pv, st);
+        } else {
+          blk_put(st, pv);
+          blk_red_add(pr.pacc + static_cast<int64_t>(r0) * pr.ld_aux + c0, pr.ld_aux, st);
+        }
       } else if (p.p_mode != 0) {
         store_blk<float>(pr.pacc, pr.ld_aux, r0, c0, pv, st);
       }
