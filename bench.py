@@ -1017,6 +1017,7 @@ def main():
                       + (f"{args.groups} groups" if args.groups > 0 else "default grouping"),
                "host_enqueue_ms": host_ms,
                "per_step_ms": per_step_ms.get("e2e"),
+               "median_ms_per_step": (float(np.median(per_step_ms["e2e"])) if per_step_ms.get("e2e") else None),
                "copies_alone": {"h2d_ms": h2d_ms, "h2d_GBs": bi / h2d_ms / 1e6, "d2h_ms": d2h_ms,
                                 "d2h_GBs": bi / d2h_ms / 1e6, "both_directions_at_once_ms": both_ms},
                "timeline": {"what": "last timed step, per group: [uploads done, passes done, downloads done] "

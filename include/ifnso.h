@@ -338,7 +338,10 @@ ifnso_status ifnso_device_status(const ifnso_plan* plan, const void* workspace, 
  * last query with IFNSO_OPT_TIMING on) into ms_out[0..max_passes) (host);
  * *n_passes (host) receives the number of passes of the last call and
  * *n_calls (host, may be NULL) the number of calls summed.  Waits for the
- * recorded events.  Pass order of ifnso_orthogonalize: 0 Gram (with the
+ * recorded events.  A call captured into a CUDA graph counts once per query,
+ * with the durations of the graph's latest replay (none before its first);
+ * only the most recent capture is followed.  Pass order of
+ * ifnso_orthogonalize: 0 Gram (with the
  * per-matrix scalars), 1 D_1 / P initialisation, 2 .. L squarings l = 1..L-1,
  * L + 1 the final product.  ns_iterate: 0 norm and scalars, then per step
  * Gram, squaring (degree 5 only), product. */

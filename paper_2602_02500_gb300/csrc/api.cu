@@ -52,7 +52,8 @@ struct ifnso_plan {
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::vector<cudaEvent_t>> ev_calls;
-  std::vector<std::vector<cudaEvent_t>> ev_graph;  // recorded by captured calls (kept for replays)
+  std::vector<std::vector<cudaEvent_t>> ev_graph;  // recorded by the last captured call (kept for replays)
+  std::vector<cudaEvent_t> ev_retired;             // events of earlier captures (graphs may still hold them)
   // ifnso_orthogonalize_host: copy streams and the events that order them
   cudaStream_t s_in = nullptr, s_out = nullptr;
   cudaStream_t s_comp = nullptr;  // the second compute stream (IFNSO_OPT_HOST_STREAMS = 2)
@@ -122,9 +123,18 @@ cudaError_t mark(ifnso_plan* plan, cudaStream_t stream, bool first) {
   if (r != cudaSuccess) return r;
   const bool captured = cap == cudaStreamCaptureStatusActive;
   auto& calls = captured ? plan->ev_graph : plan->ev_calls;
+  if (first && captured) {
+    // a new capture: pass times follow its graph from now on; the earlier
+    // graphs' events stay alive until the plan is destroyed
+    for (auto& c : plan->ev_graph)
+      for (cudaEvent_t ev : c) plan->ev_retired.push_back(ev);
+    plan->ev_graph.clear();
+  }
   if (first) calls.emplace_back();
   cudaEvent_t e;
-  if (!plan->ev_pool.empty()) {  // (a captured event never returns to the pool)
+  // a captured call takes new events (never recorded until the graph's first
+  // replay, so the query can tell) and never returns them to the pool
+  if (!captured && !plan->ev_pool.empty()) {
     e = plan->ev_pool.back();
     plan->ev_pool.pop_back();
   } else {
@@ -1406,6 +1416,16 @@ ifnso_status pass_times_locked(ifnso_plan* plan, double* ms_out, int32_t max_pas
   for (auto* list : {&plan->ev_calls, &plan->ev_graph}) {
     for (auto& c : *list) {
       if (c.size() < 2) continue;
+      if (list == &plan->ev_graph) {
+        // a captured call whose graph has not been replayed yet has no times
+        float probe = 0.f;
+        cudaError_t e = cudaEventSynchronize(c.back());
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&probe, c.front(), c.back());
+        if (e != cudaSuccess) {
+          (void)cudaGetLastError();  // not sticky: clear it
+          continue;
+        }
+      }
       IFNSO_CUDA(cudaEventSynchronize(c.back()), "cudaEventSynchronize");
       const int np = static_cast<int>(c.size()) - 1;
       *n_passes = np;
@@ -1593,6 +1613,7 @@ ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
     for (auto& c : *list)
       for (cudaEvent_t e : c) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : plan->ev_retired) cudaEventDestroy(e);
   if (plan->s_in) {
     cudaStreamSynchronize(plan->s_in);
     cudaStreamSynchronize(plan->s_out);

@@ -387,3 +387,38 @@ def test_autotune_keeps_results():
     for x, y, r in zip(xs, outs, ref):
         assert rel(to_np(y), to_np(r)) < 1e-3
         assert rel(to_np(y), O.ifnso_alg1(to_np(x), w[1:])) < TOL["bf16"]
+
+
+# --------------------------------------------------------------- pass timing
+def test_pass_times_follow_the_latest_graph():
+    """A captured call has no times before its graph's first replay (the
+    query skips it); a second capture replaces the first in the query."""
+    import torch
+
+    F = lib()
+    xs = [to_dev(synth.gaussian(50, 256, 512), "bf16")]
+    ys = [torch.empty_like(xs[0])]
+    w = coeffs(6)
+    plan = F.Plan(256, 512, "bf16", L=6)
+    plan.set(F.IFNSO_OPT_TIMING, 1)
+    b = F.Batch(xs)
+    plan.orthogonalize(b, np.r_[1.0, w], ys)
+    torch.cuda.synchronize()
+    ms, calls = plan.pass_times()
+    assert calls == 1 and len(ms) >= 7 and all(t > 0 for t in ms[:7])
+    graphs = []
+    for _ in range(2):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.orthogonalize(b, np.r_[1.0, w], ys)
+        torch.cuda.synchronize()
+        ms, calls = plan.pass_times()  # not replayed yet: nothing to report, no error
+        assert calls == 0
+        g.replay()
+        torch.cuda.synchronize()
+        ms, calls = plan.pass_times()
+        assert calls == 1 and all(t > 0 for t in ms[:7])
+        graphs.append(g)
+    graphs[0].replay()  # the first graph still replays; its events are not followed
+    torch.cuda.synchronize()
+    assert rel(to_np(ys[0]), O.ifnso_alg1(to_np(xs[0]), w)) < TOL["bf16"]
