@@ -44,7 +44,9 @@ constexpr uint32_t kApplyStage = 256 * 64 * 2;    // 32 KB: 256 B-operand rows x
 constexpr uint32_t kRing = 4 * kApplyStage;       // 128 KB, shared by the Gram (8 x 16 KB) and product (4 x 32 KB) rings
 constexpr int kGramStages = static_cast<int>(kRing / kKBlock);
 constexpr int kApplyStages = static_cast<int>(kRing / kApplyStage);
-constexpr uint32_t kSmem = 1024 + kRing + 2 * kOpBuf + 512;
+constexpr uint32_t kTail = 1024;  // barriers, TMEM slot, abort flag, partial sums, coefficients
+constexpr uint32_t kStg = 8 * 2048;  // one 32 x 32 BF16 output staging block per epilogue warp
+constexpr uint32_t kSmem = 1024 + kRing + 2 * kOpBuf + kTail + kStg;
 constexpr int kDevTimeout = 4, kDevZero = 1, kDevNonFinite = 2;
 
 // Barrier slots (8 bytes each) after the buffers.
@@ -62,7 +64,8 @@ enum Bar {
   kDrain = kT2Empty + 2,
   kNumBars
 };
-static_assert(kNumBars * 8 + 8 + 8 * 8 <= 512, "barriers, TMEM slot, abort flag, 8 partial sums");
+static_assert(kNumBars * 8 + 8 + 8 * 8 + 32 * 8 + 8 <= kTail,
+              "barriers, TMEM slot, abort flag, 8 partial sums, 32 coefficients, 2 scalars");
 
 __device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
   // byte offset of 16-byte chunk `chunk` (0..7) of row `row` in a 128-byte
@@ -87,6 +90,38 @@ __device__ __forceinline__ uint4 pack8<__nv_bfloat16>(const float* x) {
 #pragma unroll
   for (int t = 0; t < 4; ++t) h[t] = __floats2bfloat162_rn(x[2 * t], x[2 * t + 1]);
   return u;
+}
+
+// This warp's 32 x 32 block of Y (lane t: row r0 + t, columns c0 .. c0 + 31
+// in y) to out (BF16, leading dimension ld) through the warp's 2 KB staging
+// buffer, so that each store instruction writes 64-byte row pieces of 8 rows
+// (not 16 bytes in each of 32 rows).  rows, cols: the valid extent from
+// (r0, c0).  The buffer's 16-byte pieces are swizzled by row pair: the
+// row-per-lane writes and the piece-per-lane reads are both conflict-free.
+__device__ __forceinline__ void store_block_staged(__nv_bfloat16* out, int64_t ld, int r0, int c0, int rows, int cols,
+                                                   const float* y, uint8_t* stg) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();  // the previous block's reads of the buffer are done
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    *reinterpret_cast<uint4*>(stg + lane * 64 + ((q ^ ((lane >> 1) & 3)) << 4)) = pack8<__nv_bfloat16>(y + 8 * q);
+  __syncwarp();
+  const bool vec = (ld & 7) == 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = 8 * i + (lane >> 2), q = lane & 3;
+    if (r >= rows || 8 * q >= cols) continue;
+    const uint4 v = *reinterpret_cast<const uint4*>(stg + r * 64 + ((q ^ ((r >> 1) & 3)) << 4));
+    __nv_bfloat16* dst = out + static_cast<int64_t>(r0 + r) * ld + c0 + 8 * q;
+    if (vec && 8 * q + 8 <= cols) {
+      *reinterpret_cast<uint4*>(dst) = v;
+    } else {
+      const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (8 * q + t < cols) dst[t] = e[t];
+    }
+  }
 }
 
 // Row `row`'s 64 values v of K block `kb` into a 128 x 128 operand buffer
@@ -133,6 +168,8 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
+  // this epilogue warp's output staging block (after the buffers and the tail)
+  uint8_t* stg = base_ptr + kRing + 2 * kOpBuf + kTail + 2048 * ((threadIdx.x >> 5) >= 2 ? (threadIdx.x >> 5) - 2 : 0);
   const uint32_t ring = base;
   uint8_t* dhi = base_ptr + kRing;
   uint8_t* dlo = dhi + kOpBuf;
@@ -142,6 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + kRing + 2 * kOpBuf + 8 * kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float2* red = reinterpret_cast<float2*>(tmem_slot + 2);  // 8 epilogue warps' partial sums
+  double* wco = reinterpret_cast<double*>(red + 8);         // w_0 .. w_L, then c_0 = 1 + sum w at [31]
+  float* fsc = reinterpret_cast<float*>(wco + 32);          // 1/o and 1/sqrt(o), from one thread
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -369,6 +408,17 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
       tmem_wait_st();
     };
     float d[64];
+    // the coefficients into shared memory while the Gram runs (the squaring
+    // chain then reads no global memory); the barrier below publishes them
+    if (warp == 2) {
+      if (lane <= L) wco[lane] = coef_at(p.coef, mi, lane);
+      __syncwarp();
+      if (lane == 0) {
+        double c = 1.0;
+        for (int l = 1; l <= L; ++l) c += wco[l];
+        wco[31] = c;
+      }
+    }
     bool ok = wait_bar(bar(kTFull), 0);
     float inv_s2 = 0.f, inv_s = 0.f;
     double c0 = 1.0;
@@ -391,34 +441,45 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
       // every epilogue warp reaches this barrier, whether or not its wait succeeded
       asm volatile("bar.sync 1, 256;" ::: "memory");
     }
-    if (ok) {
-      double o2 = 0.0, trace = 0.0;
+    // the FP64 scalars in one thread (the FP64 pipe is narrow: 256 threads
+    // repeating the square roots and divisions took microseconds), then shared
+    if (warp == 2 && lane == 0) {
+      float i2 = 0.f, i1 = 0.f;
+      if (ok) {
+        double o2 = 0.0, trace = 0.0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        o2 += static_cast<double>(red[k].x);
-        trace += static_cast<double>(red[k].y);
-      }
-      const double s2 = p.frob ? trace : sqrt(o2);
-      for (int l = 1; l <= L; ++l) c0 += coef_at(p.coef, mi, l);
-      const bool fin = isfinite(s2) && isfinite(c0);
-      const bool pos = fin && s2 > 0.0;
-      inv_s2 = pos ? static_cast<float>(1.0 / s2) : 0.f;
-      inv_s = pos ? static_cast<float>(1.0 / sqrt(s2)) : 0.f;
-      if (warp == 2 && lane == 0) {
+        for (int k = 0; k < 8; ++k) {
+          o2 += static_cast<double>(red[k].x);
+          trace += static_cast<double>(red[k].y);
+        }
+        const double s2 = p.frob ? trace : sqrt(o2);
+        const double c = wco[31];
+        const bool fin = isfinite(s2) && isfinite(c);
+        const bool pos = fin && s2 > 0.0;
+        i2 = pos ? static_cast<float>(1.0 / s2) : 0.f;
+        i1 = pos ? static_cast<float>(1.0 / sqrt(s2)) : 0.f;
         sc->o2 = o2;
         sc->trace = trace;
         sc->s2 = s2;
-        sc->c0 = c0;
-        sc->inv_s2 = inv_s2;
-        sc->inv_s = inv_s;
+        sc->c0 = c;
+        sc->inv_s2 = i2;
+        sc->inv_s = i1;
         atomicOr(&sc->status, (!fin ? kDevNonFinite : 0) | ((fin && s2 == 0.0) ? kDevZero : 0));
       }
+      fsc[0] = i2;
+      fsc[1] = i1;
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // reached by every epilogue warp
+    if (ok) {
+      inv_s2 = fsc[0];
+      inv_s = fsc[1];
+      c0 = wco[31];
       // D_1 = T_0 / o as the first squaring's operand (hi + lo when it is split)
 #pragma unroll
       for (int t = 0; t < 64; ++t) d[t] *= inv_s2;
       if (L >= 2) put_row<__half>(dhi, dlo, row, half, d, 1 <= p.k_split);
       const float c0f = static_cast<float>(c0);
-      const float w1 = static_cast<float>(coef_at(p.coef, mi, 1));
+      const float w1 = static_cast<float>(wco[1]);
       {
         float pv[64];
 #pragma unroll
@@ -434,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
     }
     for (int j = 1; j <= L - 1 && ok; ++j) {
       if (!(ok = wait_bar(bar(kTFull), j & 1))) break;
-      const float wn = static_cast<float>(coef_at(p.coef, mi, j + 1));
+      const float wn = static_cast<float>(wco[j + 1]);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         uint32_t u[32], pu[32];
@@ -480,22 +541,15 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
         __syncwarp();
         IFNSO_TMEM_LD32(trow + static_cast<uint32_t>(256 * b + 128 * half + 32 * c), u);
         IFNSO_TMEM_WAIT_LD(u);
-        if (row >= h || col >= w) continue;  // (the loop head reconverges the warp before the next load)
+        if (col >= w) continue;  // (warp-uniform; the loop head reconverges the warp before the next load)
         float y[32];
 #pragma unroll
         for (int t = 0; t < 32; ++t) y[t] = __uint_as_float(u[t]) * inv_s;
         if (!pr.trans) {
-          __nv_bfloat16* dst = out + static_cast<int64_t>(row) * pr.ld_out + col;
-          if ((pr.ld_out & 7) == 0 && col + 32 <= w) {
-#pragma unroll
-            for (int t = 0; t < 4; ++t) reinterpret_cast<uint4*>(dst)[t] = pack8<__nv_bfloat16>(y + 8 * t);
-          } else {
-#pragma unroll
-            for (int t = 0; t < 32; ++t)
-              if (col + t < w) dst[t] = __float2bfloat16_rn(y[t]);
-          }
-        } else {
+          store_block_staged(out, pr.ld_out, 32 * q, col, h - 32 * q, w - col, y, stg);
+        } else if (row < h) {
           // M is tall: Y^T, element (row, col + t) goes to out[col + t][row]
+          // (consecutive lanes write consecutive elements)
 #pragma unroll
           for (int t = 0; t < 32; ++t)
             if (col + t < w) out[static_cast<int64_t>(col + t) * pr.ld_out + row] = __float2bfloat16_rn(y[t]);
@@ -542,7 +596,7 @@ enum NsBar {
   nDrain,
   nNumBars
 };
-static_assert(nNumBars * 8 + 8 + 8 * 8 <= 512, "barriers, TMEM slot, abort flag, 8 partial sums");
+static_assert(nNumBars * 8 + 8 + 8 * 8 + 8 <= kTail, "barriers, TMEM slot, abort flag, 8 partial sums, 2 scalars");
 
 // Byte offset of X(i, n) (M tall: the tile's rows are n) in a 256-column
 // B-operand tile held as two stages of 256 K-major rows (128-byte swizzle).
@@ -557,6 +611,8 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
+  // this epilogue warp's output staging block (after the buffers and the tail)
+  uint8_t* stg = base_ptr + kRing + 2 * kOpBuf + kTail + 2048 * ((threadIdx.x >> 5) >= 2 ? (threadIdx.x >> 5) - 2 : 0);
   const uint32_t ring = base;
   uint8_t* sbuf = base_ptr + kRing;  // S (BF16 operand)
   uint8_t* bbuf = sbuf + kOpBuf;     // B (BF16 operand)
@@ -566,6 +622,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + kRing + 2 * kOpBuf + 8 * nNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float2* red = reinterpret_cast<float2*>(tmem_slot + 2);
+  float* fsc = reinterpret_cast<float*>(red + 8);  // 1/||A||_F^2 and 1/||A||_F, from one thread
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -805,20 +862,29 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
         for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
         if (lane == 0) red[warp - 2] = make_float2(0.f, tr);
         asm volatile("bar.sync 1, 256;" ::: "memory");  // reached by every epilogue warp
-        double trace = 0.0;
+        // the FP64 scalars in one thread, then shared
+        if (leader) {
+          float i2 = 0.f, i1 = 0.f;
+          if (ok) {
+            double trace = 0.0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) trace += static_cast<double>(red[k].y);
-        const bool fin = isfinite(trace);
-        const bool pos = fin && trace > 0.0;
-        inv_s2 = pos ? static_cast<float>(1.0 / trace) : 0.f;
-        inv_s = pos ? static_cast<float>(1.0 / sqrt(trace)) : 0.f;
-        if (leader && ok) {
-          sc->trace = trace;
-          sc->s2 = trace;
-          sc->inv_s2 = inv_s2;
-          sc->inv_s = inv_s;
-          atomicOr(&sc->status, (!fin ? kDevNonFinite : 0) | ((fin && trace == 0.0) ? kDevZero : 0));
+            for (int k = 0; k < 8; ++k) trace += static_cast<double>(red[k].y);
+            const bool fin = isfinite(trace);
+            const bool pos = fin && trace > 0.0;
+            i2 = pos ? static_cast<float>(1.0 / trace) : 0.f;
+            i1 = pos ? static_cast<float>(1.0 / sqrt(trace)) : 0.f;
+            sc->trace = trace;
+            sc->s2 = trace;
+            sc->inv_s2 = i2;
+            sc->inv_s = i1;
+            atomicOr(&sc->status, (!fin ? kDevNonFinite : 0) | ((fin && trace == 0.0) ? kDevZero : 0));
+          }
+          fsc[0] = i2;
+          fsc[1] = i1;
         }
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // reached by every epilogue warp
+        inv_s2 = fsc[0];
+        inv_s = fsc[1];
 #pragma unroll
         for (int k = 0; k < 64; ++k) d[k] *= inv_s2;
       } else if (ok) {
@@ -892,18 +958,10 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
             }
           }
           if (last) {
-            if (row < h && col < w) {
+            if (col < w) {  // (warp-uniform)
               if (!pr.trans) {
-                __nv_bfloat16* dst = out + static_cast<int64_t>(row) * pr.ld_out + col;
-                if ((pr.ld_out & 7) == 0 && col + 32 <= w) {
-#pragma unroll
-                  for (int k = 0; k < 4; ++k) reinterpret_cast<uint4*>(dst)[k] = pack8<__nv_bfloat16>(y + 8 * k);
-                } else {
-#pragma unroll
-                  for (int k = 0; k < 32; ++k)
-                    if (col + k < w) dst[k] = __float2bfloat16_rn(y[k]);
-                }
-              } else {
+                store_block_staged(out, pr.ld_out, 32 * q, col, h - 32 * q, w - col, y, stg);
+              } else if (row < h) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
                   if (col + k < w) out[static_cast<int64_t>(col + k) * pr.ld_out + row] = __float2bfloat16_rn(y[k]);
