@@ -56,7 +56,8 @@ enum Bar {
   kAFull = kGEmpty + kGramStages,
   kAEmpty = kAFull + kApplyStages,
   kTFull = kAEmpty + kApplyStages,  // Gram / squaring accumulator ready (one phase per product)
-  kDReady,                          // D_1 .. D_{L-1} written (8 epilogue warps per phase)
+  kDReady,                          // K block 0 of D_1 .. D_{L-1} written (8 epilogue warps per phase)
+  kDReady1,                         // K block 1 of the same
   kPReady,                          // P written (8 epilogue warps)
   kGDone,                           // the Gram's products have read their ring stages
   kT2Full,                          // product accumulators 0, 1 ready
@@ -163,6 +164,44 @@ __device__ __forceinline__ void put_row(uint8_t* buf, uint8_t* buf_lo, int row, 
   }
 }
 
+// Row `row`'s 32 values v (columns 8 c4 .. 8 c4 + 31 of K block `kb`) into a
+// 128 x 128 operand buffer, as put_row does for 64.
+template <typename T>
+__device__ __forceinline__ void put_row32(uint8_t* buf, uint8_t* buf_lo, int row, int kb, int c4, float* v,
+                                          bool split) {
+  uint8_t* blk = buf + kb * kKBlock;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if constexpr (std::is_same_v<T, __half>)
+        hi[t] = __half2float(__float2half_rn(v[8 * q + t]));
+      else
+        hi[t] = __bfloat162float(__float2bfloat16_rn(v[8 * q + t]));
+      lo[t] = v[8 * q + t] - hi[t];
+    }
+    *reinterpret_cast<uint4*>(blk + sw128_off(row, c4 + q)) = pack8<T>(hi);
+    if (split) {
+      const uint4 u = pack8<T>(lo);
+      *reinterpret_cast<uint4*>(buf_lo + kb * kKBlock + sw128_off(row, c4 + q)) = u;
+      const T* e = reinterpret_cast<const T*>(&u);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        float lr;
+        if constexpr (std::is_same_v<T, __half>)
+          lr = __half2float(e[t]);
+        else
+          lr = __bfloat162float(e[t]);
+        v[8 * q + t] = hi[t] + lr;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[8 * q + t] = hi[t];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constant__ SmParams p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -203,6 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
     }
     mbar_init(bar(kTFull), 1);
     mbar_init(bar(kDReady), 8);
+    mbar_init(bar(kDReady1), 8);
     mbar_init(bar(kPReady), 8);
     mbar_init(bar(kGDone), 1);
     for (int a = 0; a < 2; ++a) {
@@ -310,28 +350,33 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
       }
       // squarings: D_l D_l from the FP16 operand buffers (D symmetric: B = A)
       const uint32_t id_s = idesc_f16(0u, 128, 128, 0u, 0u);
+      // Squaring j accumulates in TMEM columns 128 ((j - 1) & 1) .. + 127, so
+      // that its K block 0 products can start while the epilogue still turns
+      // the other accumulator's K block 1 columns into the operand.
       for (int j = 1; j <= L - 1 && ok; ++j) {
-        if (!mbar_wait(bar(kDReady), (j - 1) & 1, abort_flag, tmo)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
+        const uint32_t accj = tmem_base + 128u * static_cast<uint32_t>((j - 1) & 1);
         const bool split = j <= p.k_split;
         const int np = split ? 3 : 1;
         int first = 1;
 #pragma unroll 1
         for (int kb = 0; kb < 2; ++kb) {
+          if (!mbar_wait(bar(kb ? kDReady1 : kDReady), (j - 1) & 1, abort_flag, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             for (int q = 0; q < np; ++q) {
               // hi hi, hi lo, lo hi
               const uint32_t sa = (q == 2 ? dlo_s : dhi_s) + kb * kKBlock + k * 32;
               const uint32_t sb = (q == 1 ? dlo_s : dhi_s) + kb * kKBlock + k * 32;
-              umma_f16<1>(acc, sdesc_sw128(sa, 16, 1024), sdesc_sw128(sb, 16, 1024), id_s, first ? 0u : 1u);
+              umma_f16<1>(accj, sdesc_sw128(sa, 16, 1024), sdesc_sw128(sb, 16, 1024), id_s, first ? 0u : 1u);
               first = 0;
             }
           }
         }
+        if (!ok) break;
         umma_commit<1>(bar(kTFull));
       }
       // the product Y = P A: P hi (+ lo) as the A operand, A's columns as B
@@ -375,8 +420,10 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
     const int q = warp & 3;               // TMEM lane quadrant: rows 32 q .. 32 q + 31
-    const int half = (warp - 2) >> 2;     // columns 64 half .. 64 half + 63
+    // columns 32 half .. 32 half + 31 of each K block (the K block 0 ones first)
+    const int half = (warp - 2) >> 2;
     const int row = 32 * q + lane;
+    auto col_of = [&](int t) { return (t < 32 ? 0 : 32) + 32 * half + t; };  // column of d[t]
     const uint32_t trow = tmem_base + (static_cast<uint32_t>(32 * q) << 16);
     auto wait_bar = [&](uint32_t b, uint32_t parity) {
       int ok = 0;
@@ -385,25 +432,27 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
       if (ok) tc_fence_after();
       return ok != 0;
     };
-    auto load64 = [&](uint32_t col, float* v) {
+    // this thread's 64 columns (32 of each K block) of the 128 starting at `base`
+    auto load_cols = [&](uint32_t base, float* v) {
       uint32_t u[32];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        IFNSO_TMEM_LD32(trow + col + 32 * c, u);
+        IFNSO_TMEM_LD32(trow + base + 64 * c + 32 * half, u);
         IFNSO_TMEM_WAIT_LD(u);
 #pragma unroll
         for (int t = 0; t < 32; ++t) v[32 * c + t] = __uint_as_float(u[t]);
       }
     };
-    // P (FP32) lives in TMEM columns 128..255: this thread's row, 64 columns
-    const uint32_t tp = trow + 128 + 64 * half;
+    // TMEM: the squarings' two accumulators in columns 0..255, P (FP32) in
+    // 256..383 (this thread's row, its 64 columns)
+    const uint32_t tp = trow + 256 + 32 * half;
     auto p_store = [&](const float* v) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         uint32_t u[32];
 #pragma unroll
         for (int t = 0; t < 32; ++t) u[t] = __float_as_uint(v[32 * c + t]);
-        IFNSO_TMEM_ST32(tp + 32 * c, u);
+        IFNSO_TMEM_ST32(tp + 64 * c, u);
       }
       tmem_wait_st();
     };
@@ -425,11 +474,11 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
     {
       float ss = 0.f, tr = 0.f;
       if (ok) {
-        load64(64 * half, d);
+        load_cols(0, d);
 #pragma unroll
         for (int t = 0; t < 64; ++t) {
           ss = fmaf(d[t], d[t], ss);
-          if (64 * half + t == row) tr += d[t];
+          if (col_of(t) == row) tr += d[t];
         }
       }
 #pragma unroll
@@ -477,30 +526,35 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
       // D_1 = T_0 / o as the first squaring's operand (hi + lo when it is split)
 #pragma unroll
       for (int t = 0; t < 64; ++t) d[t] *= inv_s2;
-      if (L >= 2) put_row<__half>(dhi, dlo, row, half, d, 1 <= p.k_split);
+      tc_fence_before();  // (T_0 read: squaring 1 accumulates over it)
+      if (L >= 2) {
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+          put_row32<__half>(dhi, dlo, row, kb, 4 * half, d + 32 * kb, 1 <= p.k_split);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(kb ? kDReady1 : kDReady));
+        }
+      }
       const float c0f = static_cast<float>(c0);
       const float w1 = static_cast<float>(wco[1]);
       {
         float pv[64];
 #pragma unroll
-        for (int t = 0; t < 64; ++t) pv[t] = fmaf(-w1, d[t], (64 * half + t == row) ? c0f : 0.f);
+        for (int t = 0; t < 64; ++t) pv[t] = fmaf(-w1, d[t], (col_of(t) == row) ? c0f : 0.f);
         p_store(pv);
-      }
-      if (L >= 2) {
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(kDReady));
       }
     }
     for (int j = 1; j <= L - 1 && ok; ++j) {
       if (!(ok = wait_bar(bar(kTFull), j & 1))) break;
       const float wn = static_cast<float>(wco[j + 1]);
+      const uint32_t accj = trow + 128u * static_cast<uint32_t>((j - 1) & 1);
+      // K block 0's columns first: the next squaring's first products start on them
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         uint32_t u[32], pu[32];
-        IFNSO_TMEM_LD32(trow + 64 * half + 32 * c, u);
-        IFNSO_TMEM_LD32(tp + 32 * c, pu);
+        IFNSO_TMEM_LD32(accj + 64 * c + 32 * half, u);
+        IFNSO_TMEM_LD32(tp + 64 * c, pu);
         IFNSO_TMEM_WAIT_LD(u);
         IFNSO_TMEM_WAIT_LD(pu);
 #pragma unroll
@@ -509,22 +563,24 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
           d[32 * c + t] = dn;
           pu[t] = __float_as_uint(fmaf(-wn, dn, __uint_as_float(pu[t])));  // P -= w_{j+1} D_{j+1}
         }
-        IFNSO_TMEM_ST32(tp + 32 * c, pu);
+        IFNSO_TMEM_ST32(tp + 64 * c, pu);
+        if (j < L - 1) {
+          tc_fence_before();
+          put_row32<__half>(dhi, dlo, row, c, 4 * half, d + 32 * c, j + 1 <= p.k_split);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar(c ? kDReady1 : kDReady));
+        }
       }
       tmem_wait_st();
       tc_fence_before();
-      if (j < L - 1) {
-        put_row<__half>(dhi, dlo, row, half, d, j + 1 <= p.k_split);
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar(kDReady));
-      }
     }
     if (ok) {
       // P as BF16 hi (+ lo): the A operand of the product (P is symmetric)
-      load64(128 + 64 * half, d);
-      tc_fence_before();  // the product's accumulator 0 overwrites these TMEM columns
-      put_row<__nv_bfloat16>(dhi, dlo, row, half, d, p.p_split != 0);
+      load_cols(256, d);
+      tc_fence_before();  // the product's accumulator 1 overwrites these TMEM columns
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) put_row32<__nv_bfloat16>(dhi, dlo, row, kb, 4 * half, d + 32 * kb, p.p_split != 0);
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(kPReady));

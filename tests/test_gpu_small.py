@@ -171,3 +171,16 @@ def test_mixed_batch_small_on_chip_rest_tiled(L):
     torch.cuda.synchronize()
     for i in range(len(xs)):
         assert rel(to_np(hout[i]), ys[i]) < 1e-6, shapes[i]
+
+
+def test_small_path_long_matrices():
+    """Long rows: the Gram streams 188 K blocks through the 8-stage ring and
+    the product 47 tiles through the two TMEM accumulators (many phase
+    wraps of every barrier); wide and tall, against the oracle."""
+    F = lib()
+    mats = [synth.gaussian(900, 128, 12000), synth.gaussian(901, 11001, 100), synth.gaussian(902, 64, 8192)]
+    plan, xs, ys, w, st, o, tr = run(F, mats, 14, small=1)
+    assert np.all(st == 0)
+    for x, y in zip(xs, ys):
+        A = to_np(x)
+        assert rel(y, O.ifnso_alg1(A, w)) < 2e-2, A.shape

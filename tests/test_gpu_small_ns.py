@@ -114,3 +114,14 @@ def test_small_ns_one_launch():
     plan.ns_iterate(F.Batch(xs), ONS.MUON_ABC, 5, ys)
     torch.cuda.synchronize()
     assert F.launch_count() - before == 2 + 3 * 5
+
+
+def test_small_ns_long_matrices():
+    """Long rows: many K blocks, product tiles and X round trips per step."""
+    F = lib()
+    mats = [synth.gaussian(910, 128, 12000), synth.gaussian(911, 11001, 100), synth.gaussian(912, 64, 8192)]
+    xs, ys, st, _ = run(F, mats, ONS.MUON_ABC, 5, small=1)
+    assert np.all(st == 0)
+    for x, y in zip(xs, ys):
+        A = to_np(x)
+        assert rel(y, ONS.ns_generic(A, ONS.MUON_ABC, 5)) < TOL, A.shape
