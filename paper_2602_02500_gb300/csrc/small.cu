@@ -640,15 +640,15 @@ enum NsBar {
   nGFull = 0,
   nGEmpty = nGFull + kGramStages,
   nAFull = nGEmpty + kGramStages,
-  nAEmpty = nAFull + kApplyStages,  // released by the epilogue once X_{k+1} has left the stage
-  nTFull = nAEmpty + kApplyStages,  // S, then S^2, in TMEM columns 0..127
+  nTFull = nAFull + kApplyStages,   // S, then S^2, in TMEM columns 0..127
   nSReady,                          // S (BF16) written (8 epilogue warps)
   nBReady,                          // B (BF16) written (8 epilogue warps)
   nGDone,                           // this step's Gram products have read their stages
   nT2Full,
   nT2Empty = nT2Full + 2,
-  nXReady = nT2Empty + 2,           // X_{k+1} stored in global memory (one arrival)
+  nXReady = nT2Empty + 2,           // X_{k+1} stored in global memory (the producer)
   nTileDone,                        // the 8 epilogue warps are done with a product tile's stages
+  nTileDone1 = nTileDone + 1,       // (even and odd tiles)
   nDrain,
   nNumBars
 };
@@ -699,7 +699,6 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
     }
     for (int s = 0; s < kApplyStages; ++s) {
       mbar_init(bar(nAFull + s), 1);
-      mbar_init(bar(nAEmpty + s), 1);
     }
     mbar_init(bar(nTFull), 1);
     mbar_init(bar(nSReady), 8);
@@ -711,6 +710,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
     }
     mbar_init(bar(nXReady), 1);
     mbar_init(bar(nTileDone), 8);
+    mbar_init(bar(nTileDone1), 8);
     mbar_init(bar(nDrain), 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -733,12 +733,27 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
         tmap_acquire(&pr.mapY[m]);
       }
       bool ok = true;
-      int g = 0, t = 0;  // Gram and product loads issued so far (over all steps)
+      int g = 0, t = 0, tg = 0;  // Gram and product loads, product tiles, so far (over all steps)
+      // the 8 epilogue warps are done with product tile x (its stages hold X_{k+1})
+      auto tile_done = [&](int x) { return mbar_wait(bar(nTileDone + (x & 1)), (x >> 1) & 1, abort_flag, tmo); };
+      // TMA stores of tile x (tile nt of its step) to X buffer di: only boxes
+      // that start inside X (the rest of a box is clipped)
+      auto store_tile = [&](int x, int nt, int di) {
+        const uint32_t src = ring + 2u * static_cast<uint32_t>(x & 1) * kApplyStage;
+        for (int kb = 0; kb < 2 && 64 * kb < h; ++kb) {
+          if (!pr.trans) {
+            for (int j = 0; j < 4 && 256 * nt + 64 * j < w; ++j)
+              tma_store_2d(&pr.mapY[di], src + kb * kApplyStage + 8192 * j, 256 * nt + 64 * j, 64 * kb);
+          } else {
+            tma_store_2d(&pr.mapY[di], src + kb * kApplyStage, 64 * kb, 256 * nt);
+          }
+        }
+        bulk_commit();
+      };
       for (int st = 0; st < steps && ok; ++st) {
-        const int si = src_of(st);
-        // X_st has been stored (and the previous step's stages are all free)
-        if (st > 0 && !mbar_wait(bar(nXReady), (st - 1) & 1, abort_flag, tmo)) ok = false;
-        if (st > 0) fence_proxy_async_global();
+        const int si = src_of(st), di = dst_of(st);
+        const bool last = st == steps - 1;
+        // (the previous step's tiles were stored and their stages read below)
         for (int kb = 0; kb < n_kb && ok; ++kb, ++g) {
           const int s = g % kGramStages;
           if (!mbar_wait(bar(nGEmpty + s), ((g / kGramStages) & 1) ^ 1u, abort_flag, tmo)) {
@@ -756,23 +771,51 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
           }
         }
         if (ok && !mbar_wait(bar(nGDone), st & 1, abort_flag, tmo)) ok = false;
-        for (int q = 0; ok && q < 2 * n_nt; ++q, ++t) {
-          const int nt = q >> 1, kb = q & 1;
-          const int s = t % kApplyStages;
-          if (!mbar_wait(bar(nAEmpty + s), ((t / kApplyStages) & 1) ^ 1u, abort_flag, tmo)) {
-            ok = false;
-            break;
+        // product tiles: tile x takes stages 2 (x & 1) and 2 (x & 1) + 1; before
+        // they are refilled, the tile two before has been written back by the
+        // epilogue, stored to X_{k+1} and read by the stores
+        const int tg0 = tg;
+        for (int nt = 0; ok && nt < n_nt; ++nt) {
+          const int x = tg0 + nt;
+          if (nt >= 2) {
+            if (!tile_done(x - 2)) {
+              ok = false;
+              break;
+            }
+            if (!last) {
+              store_tile(x - 2, nt - 2, di);
+              bulk_wait_read();
+            }
           }
-          const uint32_t fb = bar(nAFull + s);
-          mbar_arrive_expect_tx(fb, kApplyStage);
-          const uint32_t dst = ring + s * kApplyStage;
-          if (!pr.trans) {
+          for (int kb = 0; kb < 2; ++kb, ++t) {
+            const int s = t % kApplyStages;  // = 2 (x & 1) + kb
+            const uint32_t fb = bar(nAFull + s);
+            mbar_arrive_expect_tx(fb, kApplyStage);
+            const uint32_t dst = ring + s * kApplyStage;
+            if (!pr.trans) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) tma_load_2d(dst + 8192 * j, &pr.mapY[si], fb, 256 * nt + 64 * j, 64 * kb);
-          } else {
-            tma_load_2d(dst, &pr.mapY[si], fb, 64 * kb, 256 * nt);
+              for (int j = 0; j < 4; ++j) tma_load_2d(dst + 8192 * j, &pr.mapY[si], fb, 256 * nt + 64 * j, 64 * kb);
+            } else {
+              tma_load_2d(dst, &pr.mapY[si], fb, 64 * kb, 256 * nt);
+            }
           }
         }
+        if (ok && !last) {
+          // the step's last tiles; then X_{k+1} is in global memory for the next step
+          for (int nt = n_nt > 2 ? n_nt - 2 : 0; ok && nt < n_nt; ++nt) {
+            if (!tile_done(tg0 + nt)) {
+              ok = false;
+              break;
+            }
+            store_tile(tg0 + nt, nt, di);
+          }
+          if (ok) {
+            bulk_wait_all();
+            fence_proxy_async_global();
+            mbar_arrive(bar(nXReady));
+          }
+        }
+        tg = tg0 + n_nt;
       }
       if (!ok) {
         atomicOr(&sc->status, kDevTimeout);
@@ -786,6 +829,7 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
           mbar_wait_bounded(bar(nAFull + s), (last / kApplyStages) & 1, tmo);
         }
       }
+      bulk_wait_all();  // no store in flight when the CTA exits
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -974,7 +1018,6 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
       if (lane == 0) mbar_arrive(bar(nBReady));
       // X <- a X + B X, tile by tile; X comes from the stages of the product's B operand
       const float sx = st == 0 ? inv_s : 1.f;
-      const int di = dst_of(st);
       for (int nt = 0; nt < n_nt; ++nt, ++ntg, t += 2) {
         const int b = ntg & 1;
         if (!(ok = wait_bar(bar(nT2Full + b), (ntg >> 1) & 1))) break;
@@ -1043,38 +1086,11 @@ __global__ void __launch_bounds__(kThreads, 1) small_ns_kernel(const __grid_cons
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(bar(nT2Empty + b));
-          mbar_arrive(bar(nTileDone));
-        }
-        // the leader waits (bounded) until all 8 warps are done with the tile's stages
-        if (leader && !mbar_wait(bar(nTileDone), ntg & 1, abort_flag, tmo)) ok = false;
-        if (leader && ok) {
-          const int s0 = t % kApplyStages;
-          if (!last) {
-            const uint32_t src = ring + s0 * kApplyStage;
-            // only boxes that start inside X (the rest of a box is clipped)
-            for (int kb = 0; kb < 2 && 64 * kb < h; ++kb) {
-              if (!pr.trans) {
-                for (int j = 0; j < 4 && 256 * nt + 64 * j < w; ++j)
-                  tma_store_2d(&pr.mapY[di], src + kb * kApplyStage + 8192 * j, 256 * nt + 64 * j, 64 * kb);
-              } else {
-                tma_store_2d(&pr.mapY[di], src + kb * kApplyStage, 64 * kb, 256 * nt);
-              }
-            }
-            bulk_commit();
-            bulk_wait_read();  // the stages may be refilled once the stores have read them
-          }
-          mbar_arrive(bar(nAEmpty + s0));
-          mbar_arrive(bar(nAEmpty + (s0 + 1) % kApplyStages));
+          mbar_arrive(bar(nTileDone + b));  // the producer stores the stages and refills them
         }
       }
       if (!ok) break;
-      if (!last && leader) {
-        bulk_wait_all();  // X_{st+1} is in global memory before the next step streams it
-        fence_proxy_async_global();
-        mbar_arrive(bar(nXReady));
-      }
     }
-    if (leader) bulk_wait_all();  // no store in flight when the CTA exits (the timeout path)
     if (!ok && lane == 0) atomicOr(&sc->status, kDevTimeout);
   }
   __syncthreads();
