@@ -14,7 +14,8 @@
 //             or hi + lo for the leading squarings of the mixed precision,
 //             three products hi hi + hi lo + lo hi) and in FP32 in the
 //             epilogue warps' registers; P = c_0 I - sum_l w_l D_l in FP32
-//             in TMEM (columns 128..255) beside the products' accumulator;
+//             in TMEM (columns 256..383) beside the squarings' two
+//             accumulators (columns 0..127 and 128..255, in turn);
 //   product   Y = P A / sqrt(o) with P as BF16 hi + lo in shared memory and
 //             A streamed again in 256-column tiles, written in M's shape.
 // Rows and columns past h are zero (TMA zero fill), so they drop out of
@@ -22,7 +23,8 @@
 //
 // Warp roles (320 threads): warp 0 TMA producer, warp 1 TMEM owner and MMA
 // issuer, warps 2..9 epilogue (two per TMEM lane quadrant; each thread owns
-// one row and 64 columns of the 128 x 128 intermediates).  Every wait is
+// one row and 64 columns of the 128 x 128 intermediates, 32 in each K
+// block).  Every wait is
 // bounded as in the tiled kernels (ptx.cuh): a timeout records
 // IFNSO_DEV_TIMEOUT for the matrix, lets issued copies and products land,
 // frees TMEM and returns.
@@ -633,9 +635,10 @@ __global__ void __launch_bounds__(kThreads, 1) small_kernel(const __grid_constan
 //   256-column tiles).
 // X_0 = A / ||A||_F with ||A||_F^2 = tr(A A^T) from the first Gram.  The
 // product's epilogue reads X from the shared-memory stages that hold its B
-// operand and writes X_{k+1} back into them; a TMA store moves them to a
-// workspace buffer (M's layout) that the next step streams in.  The last step
-// writes Y in M's shape.
+// operand and writes X_{k+1} back into them; the producer, before it
+// refills those stages, moves them with TMA stores to a workspace buffer
+// (M's layout) that the next step streams in.  The last step writes Y in M's
+// shape.
 enum NsBar {
   nGFull = 0,
   nGEmpty = nGFull + kGramStages,
