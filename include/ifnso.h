@@ -147,7 +147,17 @@ typedef enum {
    * same batch; 0 returns to the untuned defaults.  ns_iterate runs its Gram,
    * its squaring S^2 and its product in the Gram's, the plain squarings' and
    * the product's modes. */
-  IFNSO_OPT_CTA_GROUP_KINDS = 14
+  IFNSO_OPT_CTA_GROUP_KINDS = 14,
+  /* The final product Y = P A / sqrt(o) of BF16 plans with L >= 2.  0: P as
+   * BF16 hi + lo (two products, P's rounding below 2^-16 relative);
+   * 1 (default; PLAIN and MIXED precision only, SPLIT keeps hi + lo): one FP16
+   * product of P (one FP16 value) and an FP16 copy A s of the
+   * input (s a power of two from ||A||_F that keeps every entry below 32768;
+   * written after the Gram, in the workspace, which then grows by 2 bytes per
+   * input element).  FP16 keeps 3 more mantissa bits than BF16, so P's
+   * rounding costs about 2^-11 times its largest entries instead of 2^-8.
+   * Set it before sizing the workspace; get returns whether the plan uses it. */
+  IFNSO_OPT_APPLY_F16 = 15
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };
@@ -239,7 +249,10 @@ size_t ifnso_workspace_bytes(const ifnso_plan* plan, const ifnso_batch_desc* bat
  * caller; it must not be used by another call that runs concurrently.  The
  * call is asynchronous on `stream` and may be captured in a CUDA graph once
  * it has run outside capture with the same batch, outputs and workspace (the
- * first call uploads the launch metadata). */
+ * first call uploads the launch metadata).  A workspace holds the metadata of
+ * the plan that used it last: after another plan's call through it, this
+ * plan's next call uploads its own again, but a graph captured before does
+ * not, so a captured call needs a workspace no other plan uses. */
 ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch,
                                  const ifnso_coeffs* coeffs, void* const* out,
                                  void* workspace, size_t workspace_bytes, ifnso_stream_t stream);
@@ -370,7 +383,10 @@ ifnso_status ifnso_host_timeline(ifnso_plan* plan, double* ms_out, int32_t max_g
  * identity weight 1 + sum w_l, [4] two FP32 reciprocals and two 32-bit words
  * (status bits, max |A_ij|), [6] ||D_1^2||_F^2 = tr(D_1^4) when the proposal
  * network ran (its third feature), [7] 1.0 where that network's fallback head
- * chose the fixed coefficients, else 0.0.  BF16 plans keep these symmetric matrices on their 256 x 256
+ * chose the fixed coefficients, else 0.0; 7 = the FP16 copy A s of
+ * IFNSO_OPT_APPLY_F16 (M's shape, ld = its row pitch).  With that option, D
+ * buffer hi of the final parity holds P as one FP16 value after the last
+ * squaring.  BF16 plans keep these symmetric matrices on their 256 x 256
  * blocks on and above the diagonal only: element (i, j) with
  * i / 256 > j / 256 is the one at (j, i); the memory below is unspecified. */
 ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc* batch,

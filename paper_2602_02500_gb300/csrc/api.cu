@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -40,6 +41,7 @@ struct ifnso_plan {
   int gram_e4m3 = 0;     // Gram from a scaled E4M3 copy of A
   int small = 0;         // IFNSO_OPT_SMALL_MATRICES: 0 auto, 1 on-chip path where eligible, 2 tiled passes
   int small_tuned = 0;   // the autotuner's choice for eligible batches (0: not measured, 1 on chip, 2 tiled)
+  int apply_f16 = 1;     // IFNSO_OPT_APPLY_F16
   bool tuned = false;    // ifnso_plan_autotune chose cg_kind
   int cg_kind[4] = {1, 2, 1, 1};  // MMA mode per pass kind (Gram, split squaring, plain squaring, product)
   int num_sms = 0;
@@ -183,6 +185,8 @@ struct Prec {
   int k_split;  // squarings 1..k_split use split operands
   int p_split;  // P = hi + lo for the final product
   int mode;     // resolved IFNSO_PREC_*
+  int p_f16;    // the final product in FP16: P as one FP16 value times the FP16 copy A s
+  int chip_p_split;  // P = hi + lo in the on-chip path's product (it has no FP16 form)
 };
 
 struct Layout {
@@ -254,7 +258,7 @@ ifnso_status read_batch(const ifnso_plan* plan, const ifnso_batch_desc* b, std::
 // seven squarings tolerate plain FP16 operands -- and whether P is split for
 // the final product.
 Prec resolve_prec(const ifnso_plan* p) {
-  Prec r{0, 0, 0, IFNSO_PREC_PLAIN};
+  Prec r{0, 0, 0, IFNSO_PREC_PLAIN, 0, 0};
   if (p->dtype != IFNSO_BF16) return r;
   int mode = p->precision;
   const int L = p->L;
@@ -266,6 +270,13 @@ Prec resolve_prec(const ifnso_plan* p) {
   } else if (mode == IFNSO_PREC_MIXED) {
     r.k_split = p->split_squarings >= 0 ? std::min(p->split_squarings, L - 1) : std::max(0, L - 8);
     r.p_split = 1;
+  }
+  r.chip_p_split = r.p_split;
+  // (SPLIT's longer chains have larger coefficients, and P's FP16 rounding,
+  // about 2^-11 of its largest entries, then exceeds the BF16 plans' budget)
+  if (p->apply_f16 && L >= 2 && mode != IFNSO_PREC_SPLIT) {
+    r.p_f16 = 1;
+    r.p_split = 0;
   }
   r.ws_lo = r.p_split || r.k_split > 0;
   return r;
@@ -364,7 +375,7 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
   Layout ly;
   ly.count = static_cast<int>(shp.size());
   ly.L = plan->L;
-  ly.prec = ns ? Prec{0, 0, 0, IFNSO_PREC_PLAIN} : resolve_prec(plan);
+  ly.prec = ns ? Prec{0, 0, 0, IFNSO_PREC_PLAIN, 0, 0} : resolve_prec(plan);
   ly.split = ly.prec.ws_lo;
   ly.f32 = plan->dtype == IFNSO_F32;
   ly.e4m3 = (!ns && !ly.f32 && plan->gram_e4m3) ? 1 : 0;
@@ -433,6 +444,7 @@ Layout make_layout(const ifnso_plan* plan, const std::vector<Shape>& shp, int ns
         for (int b = 0; b < 4; ++b)
           if (ly.split || (b & 1) == 0) off = a1k(off + hp2 * 2);
         if (ly.e4m3) off = a1k(off + static_cast<size_t>(shp[i].h) * round_up(shp[i].w, 16));  // A s, E4M3
+        if (ly.prec.p_f16) off = a1k(off + static_cast<size_t>(shp[i].rows) * round_up(shp[i].cols, 8) * 2);  // M s, FP16
       }
     } else {
       const size_t xld = static_cast<size_t>(round_up(shp[i].cols, 8));
@@ -478,8 +490,13 @@ MatInfo mat_info(const Layout& ly, const ifnso_batch_desc* b, void* const* out, 
         }
       }
       if (ly.e4m3) {
-        mi.a8 = p;
+        mi.a8 = static_cast<uint8_t*>(p);
         mi.a8ld = round_up(s.w, 16);
+        p += a1k(static_cast<size_t>(s.h) * mi.a8ld);
+      }
+      if (ly.prec.p_f16) {
+        mi.a16 = p;
+        mi.a16ld = round_up(s.cols, 8);
       }
     }
   } else {
@@ -509,7 +526,7 @@ uint64_t batch_sig(const ifnso_plan* plan, const ifnso_batch_desc* b, void* cons
                    const ifnso_coeffs* cf, const double* poly, int degree, int steps, int kind) {
   uint64_t h = 1469598103934665603ull;
   const Prec pr = resolve_prec(plan);
-  int opts[8] = {plan->L, pr.mode, pr.k_split, pr.p_split, plan->scale, plan->dtype, kind, steps};
+  int opts[9] = {plan->L, pr.mode, pr.k_split, pr.p_split, plan->scale, plan->dtype, kind, steps, pr.p_f16};
   h = fnv(h, opts, sizeof(opts));
   h = fnv(h, &ws, sizeof(ws));
   h = fnv(h, &b->count, sizeof(b->count));
@@ -698,22 +715,27 @@ ifnso_status build_ifnso_meta(const Layout& ly, const ifnso_batch_desc* b, void*
     // apply: A operand P (BF16 hi/lo in D buffer (L-1) % 2), B operand the input
     TcProblem& a = pr[ly.pi_apply + i];
     const int fb = (ly.L - 1) % 2;
-    // P is symmetric and stored on its upper blocks
-    if (!map_k(&a.mapA[0], bf16_t(), mi.d[2 * fb], hp, hp, hp) ||
-        !map_mn(&a.mapT[0], bf16_t(), mi.d[2 * fb], hp, hp, hp))
+    // P is symmetric and stored on its upper blocks; the FP16 product reads P
+    // as one FP16 value and, in place of the input, its FP16 copy M s
+    const bool f16 = ly.prec.p_f16 != 0;
+    const CUtensorMapDataType pt = f16 ? f16_t() : bf16_t();
+    if (!map_k(&a.mapA[0], pt, mi.d[2 * fb], hp, hp, hp) || !map_mn(&a.mapT[0], pt, mi.d[2 * fb], hp, hp, hp))
       return fail(IFNSO_ERR_CUDA, "tensor map (P hi)");
-    if (ly.split && (!map_k(&a.mapA[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp) ||
-                     !map_mn(&a.mapT[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp)))
+    if (!f16 && ly.split &&
+        (!map_k(&a.mapA[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp) ||
+         !map_mn(&a.mapT[1], bf16_t(), mi.d[2 * fb + 1], hp, hp, hp)))
       return fail(IFNSO_ERR_CUDA, "tensor map (P lo)");
     a.sym = kSymA;
+    const void* bsrc = f16 ? mi.a16 : mi.in;
+    const int64_t bld = f16 ? mi.a16ld : s.ld;
     if (!s.trans) {
       // Y = P A: B(n, k) = A[k][n], contiguous along n
-      ok = map_mn(&a.mapB[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+      ok = map_mn(&a.mapB[0], pt, bsrc, s.cols, s.rows, bld);
       a.b_mn = 1;
       a.out_trans = 0;
     } else {
       // out = M P: computed as (P M^T)^T, B(n, k) = M[n][k], tile stored transposed
-      ok = map_k(&a.mapB[0], bf16_t(), mi.in, s.cols, s.rows, s.ld);
+      ok = map_k(&a.mapB[0], pt, bsrc, s.cols, s.rows, bld);
       a.b_mn = 0;
       a.out_trans = 1;
     }
@@ -1107,6 +1129,29 @@ ifnso_status ensure_copy_streams(ifnso_plan* plan, int groups) {
   return IFNSO_OK;
 }
 
+// Which plan last uploaded metadata into each workspace, with its signature:
+// a plan re-uploads when another plan's call has used the same workspace
+// since its own last upload (its cached signature alone would not show it).
+std::mutex g_ws_mu;
+std::unordered_map<const void*, std::pair<const ifnso_plan*, uint64_t>> g_ws_owner;
+
+bool ws_current(const void* ws, const ifnso_plan* plan, uint64_t sig) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto it = g_ws_owner.find(ws);
+  return it != g_ws_owner.end() && it->second.first == plan && it->second.second == sig;
+}
+
+void ws_claim(const void* ws, const ifnso_plan* plan, uint64_t sig) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  g_ws_owner[ws] = {plan, sig};
+}
+
+void ws_forget(const ifnso_plan* plan) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  for (auto it = g_ws_owner.begin(); it != g_ws_owner.end();)
+    it = it->second.first == plan ? g_ws_owner.erase(it) : std::next(it);
+}
+
 // Build and upload the metadata of an IFNSO call unless the cached copy
 // already describes it (item lists grouped by gb).
 ifnso_status upload_ifnso_meta(ifnso_plan* plan, const Layout& ly, const ifnso_batch_desc* batch, void* const* out,
@@ -1114,7 +1159,7 @@ ifnso_status upload_ifnso_meta(ifnso_plan* plan, const Layout& ly, const ifnso_b
                                cudaStream_t stream, bool on_chip = false) {
   const int groups = static_cast<int>(gb.size()) - 1;
   const uint64_t sig = batch_sig(plan, batch, out, ws, coeffs, nullptr, 0, 0, (on_chip ? 2000000 : 1000) + groups);
-  if (plan->sig_valid && plan->sig == sig) return IFNSO_OK;
+  if (plan->sig_valid && plan->sig == sig && ws_current(ws, plan, sig)) return IFNSO_OK;
   ifnso_status st;
   if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
   uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
@@ -1130,6 +1175,7 @@ ifnso_status upload_ifnso_meta(ifnso_plan* plan, const Layout& ly, const ifnso_b
   plan->sig = sig;
   plan->sig_valid = true;
   plan->groups = groups;
+  ws_claim(ws, plan, sig);
   return IFNSO_OK;
 }
 
@@ -1240,7 +1286,7 @@ cudaError_t launch_on_chip(const Run& r, int first, int count, const int32_t* d_
   p.first = first;
   p.L = ly.L;
   p.k_split = ly.prec.k_split;
-  p.p_split = ly.prec.p_split;
+  p.p_split = ly.prec.chip_p_split;
   p.frob = r.plan->scale == IFNSO_SCALE_FROB;
   p.wait_ms = static_cast<uint32_t>(r.plan->wait_ms);
   return launch_small(p, count, r.stream);
@@ -1302,6 +1348,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   const int n = ly.count;
   const Prec& pc = ly.prec;
   p.p_split = pc.p_split;
+  p.p_f16 = pc.p_f16;
   p.wait_ms = static_cast<uint32_t>(plan->wait_ms);
   // automatic: the autotuned mode of each pass kind, else MMAs of the CTA pair
   // for the split squarings (three products per stage hide the pair's
@@ -1351,6 +1398,10 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   // with fixed coefficients it also starts P = c_0 I - w_1 D_1
   const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
   IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream, 0, net ? 0 : 1), "prep");
+  if (pc.p_f16) {
+    // the FP16 copy M s that the final product reads (s from tr T_0)
+    IFNSO_CUDA(launch_cast_f16(d_mats, count, scal, std::max(1, 16 * plan->num_sms / count), stream), "FP16 copy");
+  }
   IFNSO_CUDA(mark_pass(false), "timing event");
   if (stop(1)) return IFNSO_OK;
   for (int j = 1; j <= L - 1; ++j) {
@@ -1400,7 +1451,8 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.update = r.update ? 1 : 0;
   p.lr = r.lr;
   p.cta_group = cta_group(kApply);
-  IFNSO_CUDA(tc_launch(EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream), "apply pass");
+  IFNSO_CUDA(tc_launch(pc.p_f16 ? EPI_APPLY_F16 : EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream),
+             "apply pass");
   IFNSO_CUDA(mark_pass(false), "timing event");
   return IFNSO_OK;
 }
@@ -1556,6 +1608,11 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       if (value < 0 || value > 2) return fail(IFNSO_ERR_INVALID_ARG, "small matrices %lld (0, 1 or 2)", (long long)value);
       plan->small = static_cast<int>(value);
       return IFNSO_OK;  // the metadata holds both paths' views
+    case IFNSO_OPT_APPLY_F16:
+      if (value != 0 && value != 1) return fail(IFNSO_ERR_INVALID_ARG, "FP16 product %lld (0 or 1)", (long long)value);
+      plan->apply_f16 = static_cast<int>(value);
+      plan->sig_valid = false;
+      return IFNSO_OK;
     case IFNSO_OPT_CTA_GROUP_KINDS: {
       if (value == 0) {
         plan->tuned = false;
@@ -1596,6 +1653,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_HOST_STREAMS: *value = plan->host_streams; return IFNSO_OK;
     case IFNSO_OPT_SMALL_MATRICES: *value = plan->small; return IFNSO_OK;
     case IFNSO_OPT_SMALL_TUNED: *value = plan->small_tuned; return IFNSO_OK;
+    case IFNSO_OPT_APPLY_F16: *value = resolve_prec(plan).p_f16; return IFNSO_OK;
     case IFNSO_OPT_CTA_GROUP_KINDS: {
       int64_t v = 0;
       if (plan->tuned)
@@ -1609,6 +1667,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
 
 ifnso_status ifnso_plan_destroy(ifnso_plan* plan) {
   if (!plan) return IFNSO_OK;
+  ws_forget(plan);
   for (auto* list : {&plan->ev_calls, &plan->ev_graph})
     for (auto& c : *list)
       for (cudaEvent_t e : c) cudaEventDestroy(e);
@@ -1904,7 +1963,7 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
   if ((st = check_ws(ly, workspace, workspace_bytes)) != IFNSO_OK) return st;
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   const uint64_t sig = batch_sig(plan, batch, out, workspace, nullptr, poly, degree, steps, 2);
-  if (!plan->sig_valid || plan->sig != sig) {
+  if (!plan->sig_valid || plan->sig != sig || !ws_current(ws, plan, sig)) {
     if ((st = ensure_meta_host(plan, ly.meta_bytes, stream)) != IFNSO_OK) return st;
     uint8_t* meta = static_cast<uint8_t*>(plan->meta_host);
     if ((st = build_ns_meta(ly, batch, out, ws, meta)) != IFNSO_OK) return st;
@@ -1912,6 +1971,7 @@ ifnso_status ns_iterate(ifnso_plan* plan, const ifnso_batch_desc* batch, const d
     IFNSO_CUDA(cudaMemcpyAsync(ws, meta, ly.meta_bytes, cudaMemcpyHostToDevice, stream), "metadata upload");
     plan->sig = sig;
     plan->sig_valid = true;
+    ws_claim(ws, plan, sig);
   }
   const int n = ly.count;
   MatInfo* d_mats = reinterpret_cast<MatInfo*>(ws + ly.off_mats);
@@ -2084,6 +2144,9 @@ ifnso_status ifnso_workspace_view(const ifnso_plan* plan, const ifnso_batch_desc
   } else if (which == 6) {
     *ptr = static_cast<uint8_t*>(workspace) + ly.off_scal + static_cast<size_t>(index) * sizeof(MatScalars);
     *ld = sizeof(MatScalars) / sizeof(double);
+  } else if (which == 7) {
+    *ptr = mi.a16;
+    *ld = mi.a16ld;
   }
   else return fail(IFNSO_ERR_INVALID_ARG, "which = %d", which);
   if (!*ptr) return fail(IFNSO_ERR_INVALID_ARG, "buffer %d is not used by this plan", which);

@@ -28,7 +28,19 @@ enum EpiKind : int {
   EPI_SQR_FOLD = 7,  // EPI_SQR with -2 D_l folded into the MMAs (chosen by TcParams::fold_d)
   EPI_APPLY_UPDATE = 8,  // EPI_APPLY whose result updates the weights: W -= lr s Y (TcParams::update)
   EPI_SQR_NORM = 9,      // ||D_1^2||_F^2 into MatScalars::spare[0], nothing stored (Gelfand q = 2)
+  EPI_APPLY_F16 = 10,    // EPI_APPLY from FP16 operands: P (one FP16 value) and the scaled FP16 copy A s
+  EPI_APPLY_UPDATE_F16 = 11,  // EPI_APPLY_UPDATE from the same FP16 operands
 };
+
+// Power-of-two scale s of the FP16 copy A s read by the FP16 product, from
+// tr T_0 = ||A||_F^2: max |A_ij| s <= ||A||_F s <= 32768 < 65504 (the largest
+// FP16 value), and s within 2^-60..2^60; 1 for a zero or non-finite norm.
+__device__ __forceinline__ float f16_copy_scale(double trace) {
+  if (!(trace > 0.0) || !(trace < 1e300)) return 1.f;
+  int e = static_cast<int>(floor(log2(32768.0 / sqrt(trace))));
+  e = e < -60 ? -60 : (e > 60 ? 60 : e);
+  return exp2f(static_cast<float>(e));
+}
 
 // Per-matrix scalars kept in the workspace (64 bytes).
 struct MatScalars {
@@ -137,6 +149,7 @@ struct TcParams {
   int32_t fold_d;      // EPI_SQR: the MMAs also add -2 D_l (an identity product), so the
                        // accumulator holds D_l^2 - 2 D_l = -D_{l+1} and the epilogue
                        // does not read D_l (passes whose P update has no D_l term)
+  int32_t p_f16;       // EPI_SQR final pass: store P as one FP16 value (for EPI_APPLY_F16)
   int32_t update;      // EPI_APPLY: out0 holds the weights W (M's shape, also read through
                        // aux0): W <- W - lr sqrt(max(1, rows / cols)) Y instead of Y
   float lr;            // the step size of that update
@@ -162,6 +175,8 @@ struct MatInfo {
   int64_t xld;
   uint8_t* a8;             // E4M3 Gram: A s (h x w, K-major, leading dimension a8ld bytes)
   int64_t a8ld;
+  void* a16;               // FP16 product: M s (M's layout, leading dimension a16ld elements)
+  int64_t a16ld;
 };
 
 // One matrix of the on-chip path for h <= 128 (small.cu): the whole of
@@ -239,6 +254,8 @@ cudaError_t launch_gelfand(int count, MatScalars* scal, cudaStream_t s);
 // E4M3 Gram: max |A_ij| into MatScalars::amax, then the scaled E4M3 copy of
 // A (M or M^T, K-major) into MatInfo::a8.
 cudaError_t launch_amax(const MatInfo* d_mats, int count, MatScalars* scal, int grid_x, cudaStream_t s);
+// FP16 product: the FP16 copy M s of every input (s = f16_copy_scale(tr T_0)).
+cudaError_t launch_cast_f16(const MatInfo* d_mats, int count, const MatScalars* scal, int grid_x, cudaStream_t s);
 cudaError_t launch_cast_e4m3(const MatInfo* d_mats, int count, int max_h, int max_w, MatScalars* scal,
                              cudaStream_t s);
 

@@ -139,6 +139,41 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 // (each thread 4 consecutive values, one 32-bit store); a tall one goes
 // through a 128 x 33 tile so that both its reads and its writes are along
 // rows of their matrices.
+// The FP16 copy M s of matrix blockIdx.y in M's own layout (an elementwise
+// cast: the product reads it through the same view as the BF16 input), 8
+// values per thread and step; rows of M are 16-byte aligned (the input's TMA
+// views require it).  BF16 values scaled by a power of two convert exactly
+// while they stay within the FP16 normal range.
+__global__ void __launch_bounds__(256) k_cast_f16(const MatInfo* mats, const MatScalars* scal) {
+  const MatInfo& mi = mats[blockIdx.y];
+  if (mi.on_chip || !mi.a16) return;
+  const float s = f16_copy_scale(scal[blockIdx.y].trace);
+  const int64_t vpr = (mi.cols + 7) / 8;  // 8-value pieces per row
+  const int64_t n = mi.rows * vpr;
+  const __nv_bfloat16* M = static_cast<const __nv_bfloat16*>(mi.in);
+  __half* D = static_cast<__half*>(mi.a16);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = i / vpr, c = (i - r * vpr) * 8;
+    const __nv_bfloat16* src = M + r * mi.ld + c;
+    __half* dst = D + r * mi.a16ld + c;
+    if (c + 8 <= mi.cols) {
+      const uint4 u = *reinterpret_cast<const uint4*>(src);
+      const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&u);
+      uint4 o;
+      __half2* h = reinterpret_cast<__half2*>(&o);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float2 f = __bfloat1622float2(e[t]);
+        h[t] = __floats2half2_rn(f.x * s, f.y * s);
+      }
+      *reinterpret_cast<uint4*>(dst) = o;
+    } else {
+      for (int64_t t = 0; c + t < mi.cols; ++t) dst[t] = __float2half_rn(__bfloat162float(src[t]) * s);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_cast_e4m3(const MatInfo* mats, const MatScalars* scal) {
   __shared__ float tile[128][33];
   const MatInfo& mi = mats[blockIdx.z];
@@ -543,6 +578,13 @@ cudaError_t launch_cast_e4m3(const MatInfo* d_mats, int count, int max_h, int ma
                              cudaStream_t s) {
   if (count == 0) return cudaSuccess;
   k_cast_e4m3<<<dim3((max_w + 127) / 128, (max_h + 31) / 32, count), 256, 0, s>>>(d_mats, scal);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f16(const MatInfo* d_mats, int count, const MatScalars* scal, int grid_x, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_cast_f16<<<dim3(grid_x, count), 256, 0, s>>>(d_mats, scal);
   count_launch();
   return cudaGetLastError();
 }

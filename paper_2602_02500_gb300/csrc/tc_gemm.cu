@@ -408,7 +408,7 @@ __device__ __forceinline__ void epilogue_load(const TcParams& p, const TcProblem
   } else if constexpr (EPI == EPI_NS_SQR) {
     blk_load<__nv_bfloat16>(in.a, static_cast<const __nv_bfloat16*>(pr.aux0) + static_cast<int64_t>(r0) * pr.ld_aux + c0,
                             pr.ld_aux);
-  } else if constexpr (EPI == EPI_NS_APPLY || EPI == EPI_APPLY_UPDATE) {
+  } else if constexpr (EPI == EPI_NS_APPLY || EPI == EPI_APPLY_UPDATE || EPI == EPI_APPLY_UPDATE_F16) {
     // X (NS) or the weights W (update): M's layout, read where the result goes
     const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(pr.aux0);
     const bool vec = (pr.ld_aux & 7) == 0;
@@ -539,7 +539,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
         store_blk<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r0, c0, v, st);
       }
     } else {
-      if (p.p_split) {
+      if (p.p_f16) {
+        // P for the FP16 product: one FP16 value
+        store_blk<__half>(static_cast<__half*>(pr.out0), pr.ld_out, r0, c0, pv, st);
+      } else if (p.p_split) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const float hi = __bfloat162float(__float2bfloat16_rn(pv[j]));
@@ -552,8 +555,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
         store_blk<__nv_bfloat16>(static_cast<__nv_bfloat16*>(pr.out0), pr.ld_out, r0, c0, pv, st);
       }
     }
-  } else if constexpr (EPI == EPI_APPLY) {
-    const float s = p.scal[pr.mat].inv_s;
+  } else if constexpr (EPI == EPI_APPLY || EPI == EPI_APPLY_F16) {
+    // (the FP16 product multiplies the copy A s: divide by s as well)
+    const float s = EPI == EPI_APPLY_F16 ? p.scal[pr.mat].inv_s / f16_copy_scale(p.scal[pr.mat].trace)
+                                         : p.scal[pr.mat].inv_s;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] *= s;
     store_out_bf16(pr, r0, c0, v, st);
@@ -579,16 +584,19 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(ka, x[j], kb * v[j]);
     store_out_bf16(pr, r0, c0, v, st);
-  } else if constexpr (EPI == EPI_APPLY_UPDATE) {
+  } else if constexpr (EPI == EPI_APPLY_UPDATE || EPI == EPI_APPLY_UPDATE_F16) {
     // W <- W - lr s Y with Y = Y' A / sqrt(o) and Muon's shape factor
-    // s = sqrt(max(1, rows / cols)) of the weight matrix (M's shape)
+    // s = sqrt(max(1, rows / cols)) of the weight matrix (M's shape); the FP16
+    // product multiplies the scaled copy of A, so it also divides by that scale
     float x[32];
     if (!pr.out_trans)
       blk_unpack<__nv_bfloat16, false>(in.a, st, x);
     else
       blk_unpack<__nv_bfloat16, true>(in.a, st, x);
     const float shape = sqrtf(fmaxf(1.f, static_cast<float>(pr.rows_out) / static_cast<float>(pr.cols_out)));
-    const float kb = -p.lr * shape * p.scal[pr.mat].inv_s;
+    const float inv_s = EPI == EPI_APPLY_UPDATE_F16 ? p.scal[pr.mat].inv_s / f16_copy_scale(p.scal[pr.mat].trace)
+                                                    : p.scal[pr.mat].inv_s;
+    const float kb = -p.lr * shape * inv_s;
 #pragma unroll
     for (int j = 0; j < 32; ++j) v[j] = fmaf(kb, v[j], x[j]);
     store_out_bf16(pr, r0, c0, v, st);
@@ -604,7 +612,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   constexpr int S = C::stages;
   // D_l are FP16, the E4M3 Gram's operands E4M3 (format code 0 of its kind), all else BF16
   constexpr bool kSqr = (EPI == EPI_SQR || EPI == EPI_SQR_FOLD || EPI == EPI_SQR_NORM);
-  constexpr uint32_t kIsBf16 = (kSqr || EPI == EPI_GRAM_F8) ? 0u : 1u;
+  constexpr uint32_t kIsBf16 =
+      (kSqr || EPI == EPI_GRAM_F8 || EPI == EPI_APPLY_F16 || EPI == EPI_APPLY_UPDATE_F16) ? 0u : 1u;
   constexpr bool kF8 = (EPI == EPI_GRAM_F8);
   constexpr int kBKe = kF8 ? 2 * BK : BK;  // elements per 128-byte K block
 
@@ -1022,6 +1031,9 @@ cudaError_t dispatch(int epi, int na, const TcParams& p, int max_clusters, cudaS
       }
       if (na == 2) return launch_one<2, 1, EPI_APPLY, CG>(p, max_clusters, s);
       return launch_one<1, 1, EPI_APPLY, CG>(p, max_clusters, s);
+    case EPI_APPLY_F16:
+      if (p.update) return launch_one<1, 1, EPI_APPLY_UPDATE_F16, CG>(p, max_clusters, s);
+      return launch_one<1, 1, EPI_APPLY_F16, CG>(p, max_clusters, s);
     case EPI_NS_GRAM:
       return launch_one<1, 1, EPI_NS_GRAM, CG>(p, max_clusters, s);
     case EPI_NS_SQR:

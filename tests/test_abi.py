@@ -72,8 +72,10 @@ def test_workspace_sizes(F):
     F.ifnso_plan_set(p, F.IFNSO_OPT_PRECISION, F.IFNSO_PREC_PLAIN)
     plain = F.ifnso_workspace_bytes(p, C.byref(d))
     hp2 = 2048 * 2048
-    assert 3 * 12 * hp2 <= split < 3 * 12 * hp2 + (4 << 20)
-    assert 3 * 8 * hp2 <= plain < 3 * 8 * hp2 + (4 << 20)
+    # plus the FP16 copy of every input for the FP16 final product (on by default)
+    a16 = 2 * (2048 * 2048 + 2048 * 5632 + 5632 * 2048)
+    assert 3 * 12 * hp2 + a16 <= split < 3 * 12 * hp2 + a16 + (4 << 20)
+    assert 3 * 8 * hp2 + a16 <= plain < 3 * 8 * hp2 + a16 + (4 << 20)
     v = C.c_int64()
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_PRECISION, C.byref(v)) == 0 and v.value == F.IFNSO_PREC_PLAIN
     F.ifnso_plan_destroy(p)
@@ -120,6 +122,31 @@ def test_cta_group_option(F):
     assert F.ifnso_plan_set(p, F.IFNSO_OPT_CTA_GROUP, 2) == 0
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_CTA_GROUP, C.byref(v)) == 0 and v.value == 2
     F.ifnso_plan_destroy(p)
+
+
+def test_apply_f16_option(F):
+    # on by default for BF16 plans with L >= 2 (L = 1 and FP32 plans keep their
+    # products); only 0 and 1; the workspace holds the FP16 copy of the input
+    # (2 bytes per element, rows padded to 8) only when it is on
+    st, p = _plan(F, 256, 512, 14)
+    v = C.c_int64()
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_APPLY_F16, C.byref(v)) == 0 and v.value == 1
+    for bad in (2, -1):
+        assert F.ifnso_plan_set(p, F.IFNSO_OPT_APPLY_F16, bad) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_APPLY_F16, 0) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_APPLY_F16, C.byref(v)) == 0 and v.value == 0
+    d, keep = _fake_batch(F, [(256, 504)])
+    before = F.ifnso_workspace_bytes(p, C.byref(d))
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_APPLY_F16, 1) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_APPLY_F16, C.byref(v)) == 0 and v.value == 1
+    after = F.ifnso_workspace_bytes(p, C.byref(d))
+    assert before > 0 and after >= before + 256 * 504 * 2
+    F.ifnso_plan_destroy(p)
+    for L in (1, 16):  # L = 1 has no squarings; L = 16 is SPLIT precision
+        st, p = _plan(F, 256, 512, L)
+        assert F.ifnso_plan_set(p, F.IFNSO_OPT_APPLY_F16, 1) == 0
+        assert F.ifnso_plan_get(p, F.IFNSO_OPT_APPLY_F16, C.byref(v)) == 0 and v.value == 0
+        F.ifnso_plan_destroy(p)
 
 
 def test_host_entry_argument_checks(F):
