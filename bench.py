@@ -18,6 +18,7 @@ own copy of the list (weak scaling); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -814,6 +815,14 @@ def main():
         Events between the steps (recorded without a synchronize) give each step's time."""
         barrier()
         torch.cuda.synchronize()
+        gc.collect()
+        gc.disable()  # no collector pause inside the timed region
+        try:
+            return _timed_steps(step, k, name)
+        finally:
+            gc.enable()
+
+    def _timed_steps(step, k, name):
         if flush is None:
             evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
             evs[0].record(stream)
@@ -936,31 +945,6 @@ def main():
                 "pass_ms_per_step": per_step, "pass_sum_ms": float(sum(per_step)),
                 "pass_sum_over_step": float(sum(per_step)) / ms_step}
 
-    # 5-step quintic Newton-Schulz on the same list
-    nsplan = F.Plan(hmax, wmax, dtype, L=1)
-    nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
-    if dtype == "bf16" and plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS):
-        # the baseline runs its passes in the modes the autotuner chose for IFNSO's passes of the same shape
-        nsplan.set(F.IFNSO_OPT_CTA_GROUP_KINDS, plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS))
-    nsplan.set(F.IFNSO_OPT_TIMING, 1)
-    nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
-    zs = [torch.empty(x.shape, dtype=x.dtype, device=device) for x in xs]
-    for _ in range(max(args.warmup, 3)):
-        nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
-    torch.cuda.synchronize()
-    ns_step, _ = make_step(lambda: nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws))
-    ns_step()
-    torch.cuda.synchronize()
-    ns_ms = timed_steps(ns_step, args.steps)
-    ns_pass, _ = averaged_pass_times(nsplan, ns_step, args.steps)
-    ns_value = whole_job_rate(world, n, args.steps, ns_ms)
-    ns_on_chip = dtype == "bf16" and hmax <= 128
-    ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
-    quality = None
-    if rank == 0 and not args.no_quality:
-        quality = polar_quality(torch, shapes, xs, {"ifnso": ys, "ns5": zs})
-    del nsws, zs
-
     # end to end through the C ABI with host buffers: ifnso_orthogonalize_host
     # uploads the inputs, runs the passes and downloads the results, group by
     # group on overlapping streams
@@ -1026,21 +1010,54 @@ def main():
                             "ms": [[round(float(v), 3) for v in row] for row in tl]}}
         plan.pass_times()
 
+    # 5-step quintic Newton-Schulz on the same list
+    nsplan = F.Plan(hmax, wmax, dtype, L=1)
+    nsplan.set(F.IFNSO_OPT_CTA_GROUP, args.cta_group)
+    if dtype == "bf16" and plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS):
+        # the baseline runs its passes in the modes the autotuner chose for IFNSO's passes of the same shape
+        nsplan.set(F.IFNSO_OPT_CTA_GROUP_KINDS, plan.get(F.IFNSO_OPT_CTA_GROUP_KINDS))
+    nsplan.set(F.IFNSO_OPT_TIMING, 1)
+    nsws = F.Workspace(nsplan.ns_workspace_bytes(batch), device=device)
+    zs = [torch.empty(x.shape, dtype=x.dtype, device=device) for x in xs]
+    for _ in range(max(args.warmup, 3)):
+        nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws)
+    torch.cuda.synchronize()
+    ns_step, _ = make_step(lambda: nsplan.ns_iterate(batch, MUON_ABC, 5, zs, ws=nsws))
+    ns_step()
+    torch.cuda.synchronize()
+    ns_ms = timed_steps(ns_step, args.steps)
+    ns_pass, _ = averaged_pass_times(nsplan, ns_step, args.steps)
+    ns_value = whole_job_rate(world, n, args.steps, ns_ms)
+    ns_on_chip = dtype == "bf16" and hmax <= 128
+    ns_tflops = world * sum(flops_ns5(h, w) for h, w in hw) * args.steps / (ns_ms / 1000.0) / 1e12
+    quality = None
+    if rank == 0 and not args.no_quality:
+        quality = polar_quality(torch, shapes, xs, {"ifnso": ys, "ns5": zs})
+    del nsws, zs
+
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sample, cores = cpu_oracle_sample(wl, shapes, L)
         cpu = {"value": v, "unit": "matrices/s", "cores": cores, "kind": "oracle", "sample": sample}
 
+    if dtype != "bf16":
+        product_label = ""
+    elif plan.get(F.IFNSO_OPT_APPLY_F16):
+        product_label = "; product: P in FP16 times an FP16 copy of A scaled by a power of two"
+    else:
+        product_label = "; product: P as BF16 hi+lo" if mode != F.IFNSO_PREC_PLAIN else "; product: P in BF16"
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload + ": " + wl["desc"], "L": L,
-                       "precision": {F.IFNSO_PREC_PLAIN: "plain FP16 squarings, BF16 P",
-                                     F.IFNSO_PREC_SPLIT: "split FP16 hi+lo squarings, BF16 hi+lo P",
+                       "precision": {F.IFNSO_PREC_PLAIN: "plain FP16 squarings",
+                                     F.IFNSO_PREC_SPLIT: "split FP16 hi+lo squarings",
                                      F.IFNSO_PREC_MIXED: f"mixed: first {k_split} squarings split FP16 hi+lo, "
-                                                         f"last {L - 1 - k_split} plain FP16, BF16 hi+lo P"}.get(mode),
+                                                         f"last {L - 1 - k_split} plain FP16"}.get(mode, "")
+                                    + product_label,
                        "matrices_per_gpu": n, "parallelism": f"dp{world} (independent lists per GPU)",
                        "l2": ("inputs larger than L2 (no flush)" if flush is None else
                               "inputs smaller than twice L2: a 512 MB buffer is written before every step, "
