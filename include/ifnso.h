@@ -157,7 +157,14 @@ typedef enum {
    * input element).  FP16 keeps 3 more mantissa bits than BF16, so P's
    * rounding costs about 2^-11 times its largest entries instead of 2^-8.
    * Set it before sizing the workspace; get returns whether the plan uses it. */
-  IFNSO_OPT_APPLY_F16 = 15
+  IFNSO_OPT_APPLY_F16 = 15,
+  /* Read only: where the plan's last call wrote the FP16 copy of
+   * IFNSO_OPT_APPLY_F16 (its last group, for ifnso_orthogonalize_host): the
+   * number of squarings whose extra warps wrote it while they ran (the split
+   * ones, or every squaring when fewer than three are split), or 0 when a
+   * kernel of its own wrote it (batches too small to fill the GPU, or whose
+   * squarings are too short to hide the copy) or no copy was needed. */
+  IFNSO_OPT_FP16_COPY_HOSTS = 16
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };

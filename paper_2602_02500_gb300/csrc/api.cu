@@ -42,6 +42,7 @@ struct ifnso_plan {
   int small = 0;         // IFNSO_OPT_SMALL_MATRICES: 0 auto, 1 on-chip path where eligible, 2 tiled passes
   int small_tuned = 0;   // the autotuner's choice for eligible batches (0: not measured, 1 on chip, 2 tiled)
   int apply_f16 = 1;     // IFNSO_OPT_APPLY_F16
+  int copy_hosts = 0;    // IFNSO_OPT_FP16_COPY_HOSTS of the last call
   bool tuned = false;    // ifnso_plan_autotune chose cg_kind
   int cg_kind[4] = {1, 2, 1, 1};  // MMA mode per pass kind (Gram, split squaring, plain squaring, product)
   int num_sms = 0;
@@ -1398,10 +1399,33 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   // with fixed coefficients it also starts P = c_0 I - w_1 D_1
   const int prep_lo = L == 1 ? pc.p_split : (pc.k_split >= 1 ? 1 : 0);
   IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream, 0, net ? 0 : 1), "prep");
+  // The FP16 copy M s that the final product reads (s from tr T_0) is written
+  // by the side warps of the squarings that the tensor pipe bounds -- the
+  // split ones, or every squaring when fewer than three are split -- with the
+  // matrices shared out among them in order; or by its own HBM-bound kernel
+  // here when those passes would not hide it: a grid short of the GPU, a
+  // matrix of 2^31 pieces or more, or passes too short for the copy
+  // (estimated from its reads at 0.5 TB/s against the host passes' products
+  // at 1.6 PFLOP/s, with a margin of 0.6).
+  int side_hosts = 0;
   if (pc.p_f16) {
-    // the FP16 copy M s that the final product reads (s from tr T_0)
-    IFNSO_CUDA(launch_cast_f16(d_mats, count, scal, std::max(1, 16 * plan->num_sms / count), stream), "FP16 copy");
+    const int hosts = pc.k_split >= 3 ? pc.k_split : L - 1;
+    double rd = 0.0, fl = 0.0;
+    bool fits = 2 * grid_for(plan, n_sym) >= plan->num_sms;
+    for (int i = first; i < first + count; ++i) {
+      const Shape& s = ly.shp[i];
+      if (r.on_chip && s.h <= kSmallH) continue;
+      rd += 2.0 * static_cast<double>(s.rows) * static_cast<double>(s.cols);
+      fits = fits && static_cast<uint64_t>(s.rows) * static_cast<uint64_t>((s.cols + 7) / 8) < (1ull << 31);
+      const double nb = static_cast<double>(s.hpad / 256);
+      fl += nb * (nb + 1.0) / 2.0 * 2.0 * 256.0 * 256.0 * static_cast<double>(s.hpad);
+    }
+    const int prods = pc.k_split >= 3 ? 3 : 1;
+    if (fits && hosts >= 1 && rd / hosts / 0.5e12 < 0.6 * prods * fl / 1.6e15) side_hosts = hosts;
+    if (!side_hosts)
+      IFNSO_CUDA(launch_cast_f16(d_mats, count, scal, std::max(1, 16 * plan->num_sms / count), stream), "FP16 copy");
   }
+  plan->copy_hosts = side_hosts;
   IFNSO_CUDA(mark_pass(false), "timing event");
   if (stop(1)) return IFNSO_OK;
   for (int j = 1; j <= L - 1; ++j) {
@@ -1431,6 +1455,18 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     // passes whose P update has no D_l term take 2 D_l - D_l^2 from the MMAs
     // (the feature pass needs D_l^2 itself)
     p.fold_d = ((p.p_mode == 0 || p.p_mode == 3) && !p.feat) ? 1 : 0;
+    if (j <= side_hosts) {
+      // this squaring's share of the FP16 copies: matrices [c0, c1) of the range
+      const int c0 = static_cast<int>(static_cast<int64_t>(count) * (j - 1) / side_hosts);
+      const int c1 = static_cast<int>(static_cast<int64_t>(count) * j / side_hosts);
+      p.side_mats = d_mats + c0;
+      p.side_scal = scal + c0;
+      p.side_count = c1 - c0;
+    } else {
+      p.side_mats = nullptr;
+      p.side_scal = nullptr;
+      p.side_count = 0;
+    }
     IFNSO_CUDA(tc_launch(EPI_SQR, split ? 2 : 1, split ? 2 : 1, p, grid_for(plan, n_sym), stream), "squaring pass");
     if (net && j == 1) {
       IFNSO_CUDA(mlp_infer(net->prm, net->K, net->wfix, net->scale, net->stats, d_mats, scal, count,
@@ -1441,6 +1477,9 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     IFNSO_CUDA(mark_pass(false), "timing event");
     if (stop(1 + j)) return IFNSO_OK;
   }
+  p.side_mats = nullptr;
+  p.side_scal = nullptr;
+  p.side_count = 0;
   p.probs = probs + ly.pi_apply;
   p.items = app;
   p.n_items = static_cast<int32_t>(n_app);
@@ -1653,6 +1692,7 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_HOST_STREAMS: *value = plan->host_streams; return IFNSO_OK;
     case IFNSO_OPT_SMALL_MATRICES: *value = plan->small; return IFNSO_OK;
     case IFNSO_OPT_SMALL_TUNED: *value = plan->small_tuned; return IFNSO_OK;
+    case IFNSO_OPT_FP16_COPY_HOSTS: *value = plan->copy_hosts; return IFNSO_OK;
     case IFNSO_OPT_APPLY_F16: *value = resolve_prec(plan).p_f16; return IFNSO_OK;
     case IFNSO_OPT_CTA_GROUP_KINDS: {
       int64_t v = 0;

@@ -18,7 +18,7 @@
 //           odd CTA's TMA loads complete on the even CTA's stage barrier,
 //           which the even CTA arms with the bytes of both.
 //
-// Warp roles (320 threads):
+// Warp roles (384 threads):
 //   warp 0      TMA producer: K blocks of 64 of every operand source into a
 //               ring of shared-memory stages (128-byte swizzle).
 //   warp 1      TMEM owner (512 columns = two 128 x 256 FP32 accumulators)
@@ -28,6 +28,10 @@
 //               tcgen05.ld of the accumulator, fused elementwise math of the
 //               pass, stores to global memory (16-bit results and T_0 through
 //               the bulk-copy engine).
+//   warps 10,11 side work that shares no data with the pass: while the
+//               squarings run, the FP16 copies of the inputs that the FP16
+//               product reads (an HBM-bound job that would otherwise be a
+//               pass of its own between the tensor-bound ones).
 // The two accumulators let the epilogue of tile t overlap the main loop of
 // tile t + 1.  Symmetric results (T_0, D_l, P) are computed and stored on
 // the upper 256 x 256 blocks only; where a pass reads one as an operand, the
@@ -53,8 +57,10 @@ namespace ifnso {
 
 namespace {
 
-constexpr int kEpiWarps = 8;                  // two per TMEM lane quadrant, 128 columns each
-constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr int kEpiWarps = 8;   // two per TMEM lane quadrant, 128 columns each
+constexpr int kSideWarps = 2;  // side work of the squarings (TcParams::side_mats)
+// producer warp, MMA warp, epilogue warps, side-work warps
+constexpr int kThreads = 64 + 32 * kEpiWarps + 32 * kSideWarps;
 constexpr uint32_t kTileA = BM * BK * 2;  // 16 KB: 128 rows x 64 K of 16-bit values
 constexpr uint32_t kTmemCols = 512;
 constexpr int kStageLd = 33;                               // padded row of a transpose buffer
@@ -603,6 +609,67 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
   }
 }
 
+// ---------------------------------------------------------------- side work
+//
+// The FP16 copy M s of matrices side_mats[0 .. side_count) (s =
+// f16_copy_scale(tr T_0), known once the Gram has run), in M's own layout:
+// the same values as the standalone cast kernel writes.  The side warps of
+// all CTAs stride over the 8-value pieces of each matrix (rows 16-byte
+// aligned, as the input's TMA views require), U pieces per lane in flight:
+// 16-byte streaming loads, then 16-byte streaming stores (neither the input
+// nor the copy is read again before the product, so they should not evict
+// the pass's operands from L2); a row's ragged end goes value by value.  A
+// BF16 value times a power of two converts to FP16 exactly while it stays in
+// FP16's normal range.  The host sends a matrix here only when its piece
+// count is below 2^31.
+__device__ __forceinline__ void side_cast_f16(const TcParams& p, int t) {
+  constexpr int U = 8;
+  const uint32_t stride = gridDim.x * (32u * kSideWarps);
+  for (int m = 0; m < p.side_count; ++m) {
+    const MatInfo& mi = p.side_mats[m];
+    if (mi.on_chip || !mi.a16) continue;
+    const float s = f16_copy_scale(p.side_scal[m].trace);
+    const uint32_t cols = static_cast<uint32_t>(mi.cols);
+    const uint32_t vpr = (cols + 7u) / 8u;  // pieces per row
+    const uint32_t n = static_cast<uint32_t>(mi.rows) * vpr;
+    const __nv_bfloat16* M = static_cast<const __nv_bfloat16*>(mi.in);
+    __half* D = static_cast<__half*>(mi.a16);
+    for (uint32_t i0 = blockIdx.x * (32u * kSideWarps) + t; i0 < n; i0 += U * stride) {
+      uint4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = i0 + u * stride;
+        v[u] = make_uint4(0u, 0u, 0u, 0u);
+        if (i < n) {
+          const uint32_t r = i / vpr, c = (i - r * vpr) * 8u;
+          if (c + 8u <= cols) v[u] = __ldcs(reinterpret_cast<const uint4*>(M + r * mi.ld + c));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = i0 + u * stride;
+        if (i >= n) break;
+        const uint32_t r = i / vpr, c = (i - r * vpr) * 8u;
+        const __nv_bfloat16* src = M + r * mi.ld + c;
+        __half* dst = D + r * mi.a16ld + c;
+        if (c + 8u <= cols) {
+          const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
+          uint4 o;
+          __half2* h = reinterpret_cast<__half2*>(&o);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(e[k]);
+            h[k] = __floats2half2_rn(f.x * s, f.y * s);
+          }
+          __stcs(reinterpret_cast<uint4*>(dst), o);
+        } else {
+          for (uint32_t k = 0; c + k < cols; ++k) dst[k] = __float2half_rn(__bfloat162float(src[k]) * s);
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernel
 
 template <int NA, int NB, int EPI, int CG>
@@ -883,6 +950,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
       umma_commit<CG>(drain_bar);
       mbar_wait_bounded(drain_bar, 0, tmo);
     }
+  } else if (warp >= 2 + kEpiWarps) {
+    // -------------------------------------------------- side work (warps 10, 11)
+    if (p.side_mats) side_cast_f16(p, threadIdx.x - 32 * (2 + kEpiWarps));
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
     float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256 + kIdBytes) + (warp - 2) * 32 * kStageLd;

@@ -45,6 +45,7 @@ IFNSO_OPT_SMALL_MATRICES = 12
 IFNSO_OPT_SMALL_TUNED = 13
 IFNSO_OPT_CTA_GROUP_KINDS = 14
 IFNSO_OPT_APPLY_F16 = 15
+IFNSO_OPT_FP16_COPY_HOSTS = 16
 IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT, IFNSO_PREC_MIXED = 0, 1, 2, 3
 IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB, IFNSO_SCALE_GELFAND2 = 0, 1, 2
 IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4

@@ -142,6 +142,9 @@ def test_apply_f16_option(F):
     after = F.ifnso_workspace_bytes(p, C.byref(d))
     assert before > 0 and after >= before + 256 * 504 * 2
     F.ifnso_plan_destroy(p)
+    # where the last call wrote the copy: read only, 0 before any call
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_FP16_COPY_HOSTS, C.byref(v)) == 0 and v.value == 0
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_FP16_COPY_HOSTS, 6) == F.IFNSO_ERR_INVALID_ARG
     for L in (1, 16):  # L = 1 has no squarings; L = 16 is SPLIT precision
         st, p = _plan(F, 256, 512, L)
         assert F.ifnso_plan_set(p, F.IFNSO_OPT_APPLY_F16, 1) == 0

@@ -72,6 +72,7 @@ def test_f16_copy_is_the_scaled_rounded_input():
     mats = [synth.gaussian(70, 256, 520), synth.gaussian(71, 600, 200), 1e4 * synth.gaussian(72, 128, 300),
             1e-6 * synth.gaussian(73, 260, 260)]
     plan, b, xs, ys, w, st = run(F, mats, 6, 1)
+    assert plan.get(F.IFNSO_OPT_FP16_COPY_HOSTS) == 0  # too few tiles to fill the GPU: the copy kernel
     for i, x in enumerate(xs):
         A = to_np(x)
         want, s = f16_copy(A)
@@ -80,6 +81,38 @@ def test_f16_copy_is_the_scaled_rounded_input():
         got = F.tensor_at(ptr, (r, ld), torch.float16, plan._last_ws.buf)[:, :c].cpu().numpy()
         assert np.array_equal(got.view(np.uint16), want.view(np.uint16)), i
         assert rel(ys[i], O.ifnso_alg1(A, w)) < TOL
+
+
+@pytest.mark.parametrize("L,shapes,hosts", [
+    # six split squarings carry the copies: wide with a ragged row end, tall, ragged square
+    (14, [(2048, 2048)] * 3 + [(2048, 5630), (5632, 2040), (1530, 1536)], 6),
+    # no split squaring: all five squarings carry them (square shapes, whose copies are short)
+    (6, [(2048, 2048)] * 5 + [(2040, 2044)], 5),
+])
+def test_f16_copy_written_by_the_squarings(L, shapes, hosts):
+    """Batches that fill the GPU have the FP16 copies written by the side
+    warps of the squarings: the copy matches its definition bit for bit on
+    every matrix (one of them scaled by 1e-4, so that s is not the same for
+    all), and sampled outputs match the oracle."""
+    import torch
+
+    F = lib()
+    mats = [synth.gaussian(140 + i, r, c) for i, (r, c) in enumerate(shapes)]
+    mats[1] = 1e-4 * mats[1]
+    plan, b, xs, ys, w, st = run(F, mats, L, 1)
+    assert np.all(st == 0)
+    assert plan.get(F.IFNSO_OPT_FP16_COPY_HOSTS) == hosts
+    for i, x in enumerate(xs):
+        A = to_np(x)
+        want, s = f16_copy(A)
+        ptr, ld = plan.workspace_view(b, i, 7)
+        r, c = A.shape
+        got = F.tensor_at(ptr, (r, ld), torch.float16, plan._last_ws.buf)[:, :c].cpu().numpy()
+        assert np.array_equal(got.view(np.uint16), want.view(np.uint16)), i
+    for i in (1, len(xs) - 3, len(xs) - 1):
+        err = rel(ys[i], O.ifnso_alg1(to_np(xs[i]), w))
+        print(f"L={L} {tuple(xs[i].shape)}: {err:.2e}")
+        assert err < TOL, (i, err)
 
 
 def test_f16_product_zero_input_and_frobenius_scale():
