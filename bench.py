@@ -1041,6 +1041,9 @@ def main():
         v, sample, cores = cpu_oracle_sample(wl, shapes, L)
         cpu = {"value": v, "unit": "matrices/s", "cores": cores, "kind": "oracle", "sample": sample}
 
+    lim = plan.get(F.IFNSO_OPT_STAGE_LIMITS)
+    stage_limits = {k: ((lim >> (4 * i)) & 15) or "whole ring"
+                    for i, k in enumerate(["gram", "split_squaring", "plain_squaring", "product", "final_squaring"])}
     if dtype != "bf16":
         product_label = ""
     elif plan.get(F.IFNSO_OPT_APPLY_F16):
@@ -1070,6 +1073,7 @@ def main():
                                 1: "per-CTA tcgen05 MMAs, each CTA loading its whole B tile",
                                 2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group]),
                        "autotuned": tuned is not None,
+                       "stage_limits": stage_limits,
                        "small_matrices": ({1: "on-chip path (one CTA per matrix, all of Algorithm 1 in one launch)",
                                            2: "tiled passes"}.get(plan.get(F.IFNSO_OPT_SMALL_TUNED),
                                                                   "not applicable (a matrix has h > 128)")

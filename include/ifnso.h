@@ -148,15 +148,17 @@ typedef enum {
    * its squaring S^2 and its product in the Gram's, the plain squarings' and
    * the product's modes. */
   IFNSO_OPT_CTA_GROUP_KINDS = 14,
-  /* The final product Y = P A / sqrt(o) of BF16 plans with L >= 2.  0: P as
-   * BF16 hi + lo (two products, P's rounding below 2^-16 relative);
-   * 1 (default; PLAIN and MIXED precision only, SPLIT keeps hi + lo): one FP16
-   * product of P (one FP16 value) and an FP16 copy A s of the
-   * input (s a power of two from ||A||_F that keeps every entry below 32768;
-   * written after the Gram, in the workspace, which then grows by 2 bytes per
-   * input element).  FP16 keeps 3 more mantissa bits than BF16, so P's
-   * rounding costs about 2^-11 times its largest entries instead of 2^-8.
-   * Set it before sizing the workspace; get returns whether the plan uses it. */
+  /* The final product Y = P A / sqrt(o) of MIXED-precision BF16 plans (AUTO
+   * for 5 <= L <= 14), whose P is otherwise BF16 hi + lo (two products, P's
+   * rounding below 2^-16 relative).  1 (default): one FP16 product of P (one
+   * FP16 value) and an FP16 copy A s of the input (s a power of two from
+   * ||A||_F that keeps every entry below 32768; written after the Gram, in
+   * the workspace, which then grows by 2 bytes per input element).  FP16
+   * keeps 3 more mantissa bits than BF16, so P's rounding costs about 2^-11
+   * times its largest entries.  0: BF16 hi + lo.  PLAIN plans keep their one
+   * BF16 product of P and SPLIT plans (larger coefficients) hi + lo whatever
+   * the value.  Set it before sizing the workspace; get returns whether the
+   * plan uses it. */
   IFNSO_OPT_APPLY_F16 = 15,
   /* Read only: where the plan's last call wrote the FP16 copy of
    * IFNSO_OPT_APPLY_F16 (its last group, for ifnso_orthogonalize_host): the
@@ -164,7 +166,18 @@ typedef enum {
    * ones, or every squaring when fewer than three are split), or 0 when a
    * kernel of its own wrote it (batches too small to fill the GPU, or whose
    * squarings are too short to hide the copy) or no copy was needed. */
-  IFNSO_OPT_FP16_COPY_HOSTS = 16
+  IFNSO_OPT_FP16_COPY_HOSTS = 16,
+  /* How many stages of its ring of operand buffers each kind of tensor-core
+   * pass cycles through, packed 4 bits per kind (bits 0-3 the Gram, 4-7 the
+   * split squarings, 8-11 the plain squarings, 12-15 the product, 16-19 the
+   * final squaring, which reads P in its epilogue); 0 is the whole ring (up
+   * to 6 stages, as many as shared memory holds), 2..15 a limit (a limit at or
+   * above the ring's depth changes nothing).  A shallower ring leaves the
+   * shared memory it does not allocate to the L1 cache and has fewer operand
+   * bytes in flight, which can speed up a pass whose epilogue loads or stores
+   * compete with them.  ifnso_plan_autotune chooses among the whole ring, 4 and 3 per kind
+   * (get returns its choice); set overrides it; the default is 0. */
+  IFNSO_OPT_STAGE_LIMITS = 17
 } ifnso_option;
 
 enum { IFNSO_PREC_AUTO = 0, IFNSO_PREC_PLAIN = 1, IFNSO_PREC_SPLIT = 2, IFNSO_PREC_MIXED = 3 };
@@ -291,7 +304,11 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
  * kind, the faster mode.  The kinds are the Gram, the split squarings, the
  * plain squarings and the final product.  Later calls with
  * IFNSO_OPT_CTA_GROUP = 0 (the default) use those modes.  `chosen` (host,
- * 4 entries, or NULL) receives them in that order.  When every matrix of the
+ * 4 entries, or NULL) receives them in that order.  In those modes it then
+ * times the whole ring of operand stages, 4 and 3 stages for every pass
+ * (1 + reps calls each) and keeps per kind, the final squaring counted
+ * apart, the depth that is fastest by more than 2%
+ * (IFNSO_OPT_STAGE_LIMITS).  When every matrix of the
  * batch has h <= 128 and the on-chip path applies to the call
  * (IFNSO_OPT_SMALL_MATRICES), it then also times that path (1 + reps calls)
  * against the tiled passes in their chosen modes and keeps the faster for

@@ -24,6 +24,8 @@ using namespace ifnso;
 namespace {
 // pass kinds of the tensor-core path, as ifnso_plan_autotune reports them
 constexpr int kGram = 0, kSplit = 1, kPlain = 2, kApply = 3, kKinds = 4;
+// stage-depth kinds: the four above and the final squaring (which reads P in its epilogue)
+constexpr int kFinal = 4, kDepthKinds = 5;
 }  // namespace
 
 struct ifnso_plan {
@@ -45,6 +47,7 @@ struct ifnso_plan {
   int copy_hosts = 0;    // IFNSO_OPT_FP16_COPY_HOSTS of the last call
   bool tuned = false;    // ifnso_plan_autotune chose cg_kind
   int cg_kind[4] = {1, 2, 1, 1};  // MMA mode per pass kind (Gram, split squaring, plain squaring, product)
+  int stage_lim[kDepthKinds] = {0, 0, 0, 0, 0};  // IFNSO_OPT_STAGE_LIMITS (0: the whole ring)
   int num_sms = 0;
   // metadata of the last batch (pinned host copy, uploaded into the workspace)
   uint64_t sig = 0;
@@ -273,9 +276,12 @@ Prec resolve_prec(const ifnso_plan* p) {
     r.p_split = 1;
   }
   r.chip_p_split = r.p_split;
+  // The FP16 product replaces MIXED plans' two products of P hi + lo by one.
   // (SPLIT's longer chains have larger coefficients, and P's FP16 rounding,
-  // about 2^-11 of its largest entries, then exceeds the BF16 plans' budget)
-  if (p->apply_f16 && L >= 2 && mode != IFNSO_PREC_SPLIT) {
+  // about 2^-11 of its largest entries, then exceeds the BF16 plans' budget;
+  // PLAIN plans already take one BF16 product of P, and the copy of the
+  // input would only add its HBM traffic.)
+  if (p->apply_f16 && L >= 2 && mode == IFNSO_PREC_MIXED) {
     r.p_f16 = 1;
     r.p_split = 0;
   }
@@ -1360,6 +1366,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     return kind == kSplit ? 2 : 1;
   };
   p.cta_group = cta_group(kGram);
+  p.max_stages = plan->stage_lim[kGram];
   p.probs = probs + ly.pi_gram;
   p.items = sym;
   p.n_items = static_cast<int32_t>(n_sym);
@@ -1392,6 +1399,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, 0, 0, stream, 1), "Gelfand prep");
     p.probs = probs + ly.pi_sqr;  // squaring 1 reads D buffer 0
     p.cta_group = cta_group(kPlain);
+    p.max_stages = 0;
     IFNSO_CUDA(tc_launch(EPI_SQR_NORM, 1, 1, p, grid_for(plan, n_sym), stream), "Gelfand norm pass");
     IFNSO_CUDA(launch_gelfand(count, scal, stream), "Gelfand scale");
   }
@@ -1402,12 +1410,14 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   // The FP16 copy M s that the final product reads (s from tr T_0) is written
   // by the side warps of the squarings that the tensor pipe bounds -- the
   // split ones, or every squaring when fewer than three are split -- with the
-  // matrices shared out among them in order; or by its own HBM-bound kernel
+  // matrices shared out among them in order, in shares of about equal bytes;
+  // or by its own HBM-bound kernel
   // here when those passes would not hide it: a grid short of the GPU, a
   // matrix of 2^31 pieces or more, or passes too short for the copy
   // (estimated from its reads at 0.5 TB/s against the host passes' products
   // at 1.6 PFLOP/s, with a margin of 0.6).
   int side_hosts = 0;
+  std::vector<int> side_cut;  // host j copies matrices [side_cut[j - 1], side_cut[j])
   if (pc.p_f16) {
     const int hosts = pc.k_split >= 3 ? pc.k_split : L - 1;
     double rd = 0.0, fl = 0.0;
@@ -1422,6 +1432,16 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     }
     const int prods = pc.k_split >= 3 ? 3 : 1;
     if (fits && hosts >= 1 && rd / hosts / 0.5e12 < 0.6 * prods * fl / 1.6e15) side_hosts = hosts;
+    // host j's share: the matrices whose copies' cumulative bytes cross (j - 1) / hosts of the total
+    side_cut.assign(1, 0);
+    double acc = 0.0;
+    for (int i = 0; i < count && side_hosts; ++i) {
+      const Shape& s = ly.shp[first + i];
+      if (!(r.on_chip && s.h <= kSmallH)) acc += 2.0 * static_cast<double>(s.rows) * static_cast<double>(s.cols);
+      while (static_cast<int>(side_cut.size()) < side_hosts && acc >= rd * side_cut.size() / side_hosts)
+        side_cut.push_back(i + 1);
+    }
+    while (static_cast<int>(side_cut.size()) <= side_hosts) side_cut.push_back(count);
     if (!side_hosts)
       IFNSO_CUDA(launch_cast_f16(d_mats, count, scal, std::max(1, 16 * plan->num_sms / count), stream), "FP16 copy");
   }
@@ -1439,6 +1459,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     p.read_lo = split;
     p.write_lo = (j + 1 <= pc.k_split) ? 1 : 0;
     p.cta_group = cta_group(split ? kSplit : kPlain);
+    p.max_stages = plan->stage_lim[j == L - 1 ? kFinal : (split ? kSplit : kPlain)];
     if (!net) {
       // every squaring folds -2 D_j into its MMAs and adds its own term
       // -w_{j+1} D_{j+1}, from the FP32 accumulator, to P (started by prep);
@@ -1457,8 +1478,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     p.fold_d = ((p.p_mode == 0 || p.p_mode == 3) && !p.feat) ? 1 : 0;
     if (j <= side_hosts) {
       // this squaring's share of the FP16 copies: matrices [c0, c1) of the range
-      const int c0 = static_cast<int>(static_cast<int64_t>(count) * (j - 1) / side_hosts);
-      const int c1 = static_cast<int>(static_cast<int64_t>(count) * j / side_hosts);
+      const int c0 = side_cut[j - 1], c1 = side_cut[j];
       p.side_mats = d_mats + c0;
       p.side_scal = scal + c0;
       p.side_count = c1 - c0;
@@ -1490,6 +1510,7 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   p.update = r.update ? 1 : 0;
   p.lr = r.lr;
   p.cta_group = cta_group(kApply);
+  p.max_stages = plan->stage_lim[kApply];
   IFNSO_CUDA(tc_launch(pc.p_f16 ? EPI_APPLY_F16 : EPI_APPLY, pc.p_split ? 2 : 1, 1, p, grid_for(plan, n_app), stream),
              "apply pass");
   IFNSO_CUDA(mark_pass(false), "timing event");
@@ -1652,6 +1673,17 @@ ifnso_status ifnso_plan_set(ifnso_plan* plan, ifnso_option option, int64_t value
       plan->apply_f16 = static_cast<int>(value);
       plan->sig_valid = false;
       return IFNSO_OK;
+    case IFNSO_OPT_STAGE_LIMITS: {
+      int m[kDepthKinds];
+      for (int k = 0; k < kDepthKinds; ++k) {
+        m[k] = static_cast<int>((value >> (4 * k)) & 15);
+        if (m[k] == 1) return fail(IFNSO_ERR_INVALID_ARG, "stage limits %lld (0 or 2..15 per kind)", (long long)value);
+      }
+      if (value < 0 || (value >> (4 * kDepthKinds)))
+        return fail(IFNSO_ERR_INVALID_ARG, "stage limits %lld (5 kinds of 4 bits)", (long long)value);
+      for (int k = 0; k < kDepthKinds; ++k) plan->stage_lim[k] = m[k];
+      return IFNSO_OK;
+    }
     case IFNSO_OPT_CTA_GROUP_KINDS: {
       if (value == 0) {
         plan->tuned = false;
@@ -1693,6 +1725,12 @@ ifnso_status ifnso_plan_get(const ifnso_plan* plan, ifnso_option option, int64_t
     case IFNSO_OPT_SMALL_MATRICES: *value = plan->small; return IFNSO_OK;
     case IFNSO_OPT_SMALL_TUNED: *value = plan->small_tuned; return IFNSO_OK;
     case IFNSO_OPT_FP16_COPY_HOSTS: *value = plan->copy_hosts; return IFNSO_OK;
+    case IFNSO_OPT_STAGE_LIMITS: {
+      int64_t v = 0;
+      for (int k = 0; k < kDepthKinds; ++k) v |= static_cast<int64_t>(plan->stage_lim[k]) << (4 * k);
+      *value = v;
+      return IFNSO_OK;
+    }
     case IFNSO_OPT_APPLY_F16: *value = resolve_prec(plan).p_f16; return IFNSO_OK;
     case IFNSO_OPT_CTA_GROUP_KINDS: {
       int64_t v = 0;
@@ -1825,6 +1863,11 @@ ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch
   };
   const int saved_cg = plan->cta_group, saved_stop = plan->stop_after, saved_small = plan->small;
   const bool saved_timing = plan->timing, saved_tuned = plan->tuned;
+  int saved_lim[kDepthKinds];
+  for (int k = 0; k < kDepthKinds; ++k) {
+    saved_lim[k] = plan->stage_lim[k];
+    plan->stage_lim[k] = 0;  // the MMA modes are compared with the whole ring
+  }
   plan->stop_after = -1;
   plan->timing = true;
   plan->tuned = false;
@@ -1851,10 +1894,53 @@ ifnso_status ifnso_plan_autotune(ifnso_plan* plan, const ifnso_batch_desc* batch
     plan->timing = saved_timing;
     plan->tuned = saved_tuned;
     plan->small = saved_small;
+    for (int k = 0; k < kDepthKinds; ++k) plan->stage_lim[k] = saved_lim[k];
     return st;
   }
   for (int k = 0; k < kKinds; ++k) plan->cg_kind[k] = ms[2][k] < ms[1][k] ? 2 : 1;
   plan->tuned = true;
+  // The depth of the operand ring per pass kind, in the chosen modes: the
+  // whole ring, 4 or 3 stages (fewer operand bytes in flight leave L2 to the
+  // loads and stores of epilogues like the final squaring's P read).  A
+  // shallower ring must win by 2%.
+  {
+    auto depth_of = [&](int pass) {
+      if (pass == L && L >= 2) return kFinal;
+      return kind_of(pass);
+    };
+    const int cands[3] = {0, 4, 3};
+    double best[kDepthKinds] = {};
+    int pick[kDepthKinds] = {};
+    plan->cta_group = 0;
+    for (int c = 0; c < 3 && st == IFNSO_OK; ++c) {
+      for (int k = 0; k < kDepthKinds; ++k) plan->stage_lim[k] = cands[c];
+      double t[kDepthKinds] = {};
+      for (int r = 0; r <= reps && st == IFNSO_OK; ++r) {
+        st = orthogonalize_locked(plan, batch, coeffs, out, workspace, workspace_bytes, stream);
+        if (st != IFNSO_OK) break;
+        int np = 0;
+        st = pass_times_locked(plan, pt.data(), static_cast<int>(pt.size()), &np, nullptr);
+        if (r == 0) continue;
+        for (int k = 0; k < np; ++k)
+          if (depth_of(k) >= 0) t[depth_of(k)] += pt[k];
+      }
+      for (int k = 0; k < kDepthKinds; ++k)
+        if (c == 0 || t[k] < 0.98 * best[k]) {
+          best[k] = t[k];
+          pick[k] = cands[c];
+        }
+    }
+    plan->cta_group = saved_cg;
+    // a limit at or above the kind's ring depth is the whole ring
+    const int fin_split = pc.k_split >= L - 1 ? 1 : 0;
+    const int na[kDepthKinds] = {1, 2, 1, pc.p_split ? 2 : 1, fin_split ? 2 : 1};
+    const int nb[kDepthKinds] = {1, 2, 1, 1, fin_split ? 2 : 1};
+    for (int k = 0; k < kDepthKinds; ++k) {
+      const int cg = plan->cg_kind[k == kFinal ? (fin_split ? kSplit : kPlain) : k];
+      if (pick[k] >= tc_ring_stages(na[k], nb[k], cg)) pick[k] = 0;
+    }
+    for (int k = 0; k < kDepthKinds; ++k) plan->stage_lim[k] = st == IFNSO_OK ? pick[k] : saved_lim[k];
+  }
   // the shape bucket h <= 128: the on-chip path against the tiled passes (in their tuned modes)
   {
     std::vector<Shape> shp;

@@ -152,6 +152,9 @@ struct TcParams {
                        // accumulator holds D_l^2 - 2 D_l = -D_{l+1} and the epilogue
                        // does not read D_l (passes whose P update has no D_l term)
   int32_t p_f16;       // EPI_SQR final pass: store P as one FP16 value (for EPI_APPLY_F16)
+  int32_t max_stages;  // 0: the whole ring of operand stages; else the stages this pass uses
+                       // (fewer operand bytes in flight, for passes whose epilogue loads
+                       // or stores compete with them in L2)
   int32_t update;      // EPI_APPLY: out0 holds the weights W (M's shape, also read through
                        // aux0): W <- W - lr sqrt(max(1, rows / cols)) Y instead of Y
   float lr;            // the step size of that update
@@ -242,6 +245,9 @@ struct SmNsParams {
 // Launches clusters of two CTAs (at most max_clusters, at most one per item;
 // items are pairs of tiles, see WorkItem), in the MMA mode p.cta_group.
 cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s);
+// Depth of the operand ring of the tensor-core pass with na x nb operand
+// sources in MMA mode cg (TcParams::max_stages at or above it changes nothing).
+int tc_ring_stages(int na, int nb, int cg);
 int tc_smem_bytes(int na, int nb, int cta_group);
 // One CTA per matrix first .. first + count - 1 (every one with h <= 128).
 cudaError_t launch_small(const SmParams& p, int count, cudaStream_t s);

@@ -75,8 +75,13 @@ struct Cfg {
   static constexpr uint32_t stage_bytes = NA * kTileA + NB * tile_b;
   static constexpr int stages_fit = static_cast<int>((200u * 1024u) / stage_bytes);
   static constexpr int stages = stages_fit > 6 ? 6 : stages_fit;
-  // tiles + 1 KB alignment slack + barriers / flags + identity tile + epilogue transpose buffers
-  static constexpr uint32_t smem = stages * stage_bytes + 1024 + 256 + kIdBytes + kStageBytes;
+  // tiles + 1 KB alignment slack + barriers / flags + identity tile + epilogue transpose buffers,
+  // for a ring of sr stages (a launch may use fewer than `stages`: TcParams::max_stages)
+  static constexpr uint32_t smem_for(int sr) { return sr * stage_bytes + 1024 + 256 + kIdBytes + kStageBytes; }
+  static constexpr uint32_t smem = smem_for(stages);
+  __host__ __device__ static int ring(int max_stages) {
+    return (max_stages > 0 && max_stages < stages) ? max_stages : stages;
+  }
 };
 
 // Number of products per K step: every (A source, B source) pair except
@@ -676,7 +681,9 @@ template <int NA, int NB, int EPI, int CG>
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
   using C = Cfg<NA, NB, CG>;
   using PR = Products<NA, NB>;
-  constexpr int S = C::stages;
+  // stages of the ring this pass allocates and cycles through (the same in
+  // both CTAs of a pair); the shared memory it leaves unallocated goes to L1
+  const int SR = C::ring(p.max_stages);
   // D_l are FP16, the E4M3 Gram's operands E4M3 (format code 0 of its kind), all else BF16
   constexpr bool kSqr = (EPI == EPI_SQR || EPI == EPI_SQR_FOLD || EPI == EPI_SQR_NORM);
   constexpr uint32_t kIsBf16 =
@@ -688,14 +695,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base_ptr + S * C::stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base_ptr + SR * C::stage_bytes);
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
-  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * S + a); };
-  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * S + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  auto empty_bar = [&](int s) { return bar0 + 8u * (SR + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * SR + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * SR + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * SR + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * SR + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -708,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   const int ncl = static_cast<int>(cluster_count_x());
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < SR; ++s) {
       if constexpr (CG == 2) {
         // even CTA: armed with the bytes of both CTAs' copies (the odd CTA's
         // stage barriers are not used)
@@ -739,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
   // even CTA rows 0..7 (core matrix (0, 0)), the odd CTA rows 8..15 (core
   // matrix (0, 1) of its half).  Either way the tile is symmetric, as is
   // each of its core matrices.
-  const uint32_t id_tile = base + S * C::stage_bytes + 256;
+  const uint32_t id_tile = base + SR * C::stage_bytes + 256;
   if constexpr (EPI == EPI_SQR_FOLD) {
     if (warp == 2) {
       const int cm = lane >> 3, i = lane & 7;  // core matrix, row within it
@@ -748,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (diag && (i >> 1) == t) w[t] = (i & 1) ? 0xC0000000u : 0x0000C000u;  // -2.0 at column i
-      *reinterpret_cast<uint4*>(base_ptr + S * C::stage_bytes + 256 + 16 * lane) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(base_ptr + SR * C::stage_bytes + 256 + 16 * lane) = make_uint4(w[0], w[1], w[2], w[3]);
       fence_proxy_async_smem();
     }
   }
@@ -849,7 +856,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
             }
           }
           ++filled[stage];
-          if (++stage == S) {
+          if (++stage == SR) {
             stage = 0;
             phase ^= 1u;
           }
@@ -861,7 +868,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
         // even CTA's barriers count both CTAs' copies; the odd CTA's last copy
         // was issued a whole wait limit before it gave up)
         if (CG == 1 || crank == 0)
-          for (int s = 0; s < S; ++s)
+          for (int s = 0; s < SR; ++s)
             if (filled[s]) mbar_wait_bounded(full_bar(s), (filled[s] - 1u) & 1u, tmo);
       }
     }
@@ -936,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
           }
           // frees the stage once these MMAs have read it (CG 2: in both CTAs)
           umma_commit_pair<CG>(empty_bar(stage));
-          if (++stage == S) {
+          if (++stage == SR) {
             stage = 0;
             phase ^= 1u;
           }
@@ -955,7 +962,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(const __grid_const
     if (p.side_mats) side_cast_f16(p, threadIdx.x - 32 * (2 + kEpiWarps));
   } else {
     // -------------------------------------------------- epilogue (warps 2..9)
-    float* stage = reinterpret_cast<float*>(base_ptr + S * C::stage_bytes + 256 + kIdBytes) + (warp - 2) * 32 * kStageLd;
+    float* stage = reinterpret_cast<float*>(base_ptr + SR * C::stage_bytes + 256 + kIdBytes) + (warp - 2) * 32 * kStageLd;
     const int q = warp & 3;            // TMEM lane quadrant this warp may access
     const int half = (warp - 2) >> 2;  // which 128 of the tile's 256 columns
     int local = 0;
@@ -1069,7 +1076,7 @@ cudaError_t launch_one(const TcParams& p, int max_clusters, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(2 * clusters, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = C::smem;
+  cfg.dynamicSmemBytes = C::smem_for(C::ring(p.max_stages));
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -1123,6 +1130,11 @@ int tc_smem_bytes(int na, int nb, int cta_group) {
   if (na == 2 && nb == 2) return pair ? Cfg<2, 2, 2>::smem : Cfg<2, 2, 1>::smem;
   if (na == 2 && nb == 1) return pair ? Cfg<2, 1, 2>::smem : Cfg<2, 1, 1>::smem;
   return -1;
+}
+
+int tc_ring_stages(int na, int nb, int cg) {
+  if (cg == 2) return na == 2 ? (nb == 2 ? Cfg<2, 2, 2>::stages : Cfg<2, 1, 2>::stages) : Cfg<1, 1, 2>::stages;
+  return na == 2 ? (nb == 2 ? Cfg<2, 2, 1>::stages : Cfg<2, 1, 1>::stages) : Cfg<1, 1, 1>::stages;
 }
 
 cudaError_t tc_launch(int epi, int na, int nb, const TcParams& p, int max_clusters, cudaStream_t s) {

@@ -46,6 +46,7 @@ IFNSO_OPT_SMALL_TUNED = 13
 IFNSO_OPT_CTA_GROUP_KINDS = 14
 IFNSO_OPT_APPLY_F16 = 15
 IFNSO_OPT_FP16_COPY_HOSTS = 16
+IFNSO_OPT_STAGE_LIMITS = 17
 IFNSO_PREC_AUTO, IFNSO_PREC_PLAIN, IFNSO_PREC_SPLIT, IFNSO_PREC_MIXED = 0, 1, 2, 3
 IFNSO_SCALE_GRAM, IFNSO_SCALE_FROB, IFNSO_SCALE_GELFAND2 = 0, 1, 2
 IFNSO_DEV_ZERO_INPUT, IFNSO_DEV_NONFINITE, IFNSO_DEV_TIMEOUT = 1, 2, 4
@@ -306,7 +307,9 @@ class Plan:
 
     def autotune(self, batch, coeffs, outs, reps=3, ws=None, stream=None):
         """Time per-CTA and CTA-pair MMAs on this batch and keep the faster per
-        pass kind; returns the modes (Gram, split squaring, plain squaring, product)."""
+        pass kind, then the depth of the operand ring per kind
+        (IFNSO_OPT_STAGE_LIMITS); returns the modes (Gram, split squaring,
+        plain squaring, product)."""
         cf = self._coeffs(batch, coeffs)
         need = self.workspace_bytes(batch)
         if ws is None:

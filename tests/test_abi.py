@@ -72,10 +72,11 @@ def test_workspace_sizes(F):
     F.ifnso_plan_set(p, F.IFNSO_OPT_PRECISION, F.IFNSO_PREC_PLAIN)
     plain = F.ifnso_workspace_bytes(p, C.byref(d))
     hp2 = 2048 * 2048
-    # plus the FP16 copy of every input for the FP16 final product (on by default)
+    # the MIXED plan (L = 14) also holds the FP16 copy of every input for its
+    # FP16 final product (on by default); PLAIN plans take one BF16 product
     a16 = 2 * (2048 * 2048 + 2048 * 5632 + 5632 * 2048)
     assert 3 * 12 * hp2 + a16 <= split < 3 * 12 * hp2 + a16 + (4 << 20)
-    assert 3 * 8 * hp2 + a16 <= plain < 3 * 8 * hp2 + a16 + (4 << 20)
+    assert 3 * 8 * hp2 <= plain < 3 * 8 * hp2 + (4 << 20)
     v = C.c_int64()
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_PRECISION, C.byref(v)) == 0 and v.value == F.IFNSO_PREC_PLAIN
     F.ifnso_plan_destroy(p)
@@ -125,9 +126,9 @@ def test_cta_group_option(F):
 
 
 def test_apply_f16_option(F):
-    # on by default for BF16 plans with L >= 2 (L = 1 and FP32 plans keep their
-    # products); only 0 and 1; the workspace holds the FP16 copy of the input
-    # (2 bytes per element, rows padded to 8) only when it is on
+    # on by default for MIXED-precision BF16 plans (AUTO for 5 <= L <= 14; the
+    # others keep their products); only 0 and 1; the workspace holds the FP16
+    # copy of the input (2 bytes per element, rows padded to 8) only when it is on
     st, p = _plan(F, 256, 512, 14)
     v = C.c_int64()
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_APPLY_F16, C.byref(v)) == 0 and v.value == 1
@@ -145,11 +146,27 @@ def test_apply_f16_option(F):
     # where the last call wrote the copy: read only, 0 before any call
     assert F.ifnso_plan_get(p, F.IFNSO_OPT_FP16_COPY_HOSTS, C.byref(v)) == 0 and v.value == 0
     assert F.ifnso_plan_set(p, F.IFNSO_OPT_FP16_COPY_HOSTS, 6) == F.IFNSO_ERR_INVALID_ARG
-    for L in (1, 16):  # L = 1 has no squarings; L = 16 is SPLIT precision
+    for L in (1, 4, 16):  # L = 1 has no squarings; L = 4 is PLAIN (one BF16 P), L = 16 SPLIT
         st, p = _plan(F, 256, 512, L)
         assert F.ifnso_plan_set(p, F.IFNSO_OPT_APPLY_F16, 1) == 0
         assert F.ifnso_plan_get(p, F.IFNSO_OPT_APPLY_F16, C.byref(v)) == 0 and v.value == 0
         F.ifnso_plan_destroy(p)
+
+
+def test_stage_limits_option(F):
+    # 4 bits per pass kind (Gram, split, plain, product, final squaring); 0 is
+    # the whole ring, 1 and anything beyond 20 bits are rejected
+    st, p = _plan(F, 256, 512, 14)
+    v = C.c_int64()
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_STAGE_LIMITS, C.byref(v)) == 0 and v.value == 0
+    packed = 3 << 16 | 3 << 12 | 4 << 8
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_STAGE_LIMITS, packed) == 0
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_STAGE_LIMITS, C.byref(v)) == 0 and v.value == packed
+    for bad in (1, 1 << 8, 1 << 20, -1):
+        assert F.ifnso_plan_set(p, F.IFNSO_OPT_STAGE_LIMITS, bad) == F.IFNSO_ERR_INVALID_ARG
+    assert F.ifnso_plan_get(p, F.IFNSO_OPT_STAGE_LIMITS, C.byref(v)) == 0 and v.value == packed
+    assert F.ifnso_plan_set(p, F.IFNSO_OPT_STAGE_LIMITS, 0) == 0
+    F.ifnso_plan_destroy(p)
 
 
 def test_host_entry_argument_checks(F):

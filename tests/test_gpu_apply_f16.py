@@ -50,7 +50,8 @@ def run(F, mats, L, f16, cta_group=None, scale=None):
 SHAPES = [(256, 512), (392, 136), (200, 328), (512, 512), (130, 260), (700, 1030), (1, 64)]
 
 
-@pytest.mark.parametrize("L,cg", [(14, 1), (14, 2), (6, 1), (2, 1)])  # (SPLIT, L >= 15, keeps hi + lo)
+# MIXED plans (AUTO for 5 <= L <= 14); SPLIT (L >= 15) keeps hi + lo and PLAIN (L <= 4) one BF16 P
+@pytest.mark.parametrize("L,cg", [(14, 1), (14, 2), (6, 1), (5, 1)])
 def test_f16_product_matches_oracle(L, cg):
     F = lib()
     mats = [synth.gaussian(60 + i, r, c) for i, (r, c) in enumerate(SHAPES)]

@@ -142,6 +142,64 @@ def test_bf16_cta_groups(shape, L, precision):
     assert rel(out[1], out[2]) < 1e-3
 
 
+@pytest.mark.parametrize("cg", [1, 2])
+def test_bf16_stage_limits_give_identical_results(cg):
+    """The depth of the operand ring changes when stages are loaded, not what
+    the MMAs add in which order: every pass kind limited to 2 or 3 stages
+    gives the whole ring's outputs bit for bit (L = 14 mixed: Gram, split,
+    plain and final squarings, FP16 product), and they match the oracle."""
+    import torch
+
+    F = lib()
+    mats = [synth.gaussian(150 + i, *s) for i, s in enumerate([(512, 768), (768, 512), (300, 900), (1024, 1024)])]
+    xs = [to_dev(m, "bf16") for m in mats]
+    b = F.Batch(xs)
+    w = coeffs(14)
+    outs = []
+    for lim in (0, 2, 3):
+        plan = F.Plan(1024, 1024, "bf16", L=14)
+        plan.set(F.IFNSO_OPT_CTA_GROUP, cg)
+        plan.set(F.IFNSO_OPT_SMALL_MATRICES, 2)
+        plan.set(F.IFNSO_OPT_STAGE_LIMITS, sum(lim << (4 * k) for k in range(5)))
+        ys = [torch.full(x.shape, float("nan"), dtype=x.dtype, device="cuda") for x in xs]
+        plan.orthogonalize(b, np.r_[1.0, w], ys)
+        torch.cuda.synchronize()
+        st, _, _ = plan.device_status(len(xs))
+        assert np.all(st == 0)
+        outs.append([to_np(y) for y in ys])
+    for o in outs[1:]:
+        for y0, y in zip(outs[0], o):
+            assert np.array_equal(y0, y)
+    for x, y in zip(xs, outs[0]):
+        assert rel(y, O.ifnso_alg1(to_np(x), w)) < TOL["bf16"]
+
+
+def test_autotune_chooses_stage_limits():
+    """The autotuner keeps a depth per pass kind (0, 4 or 3 in each nibble)
+    and the call with its choice gives the whole ring's outputs bit for bit."""
+    import torch
+
+    F = lib()
+    mats = [synth.gaussian(160 + i, 1024, 2048) for i in range(6)]
+    xs = [to_dev(m, "bf16") for m in mats]
+    b = F.Batch(xs)
+    w = np.r_[1.0, coeffs(14)]
+    ref = [torch.empty_like(x) for x in xs]
+    p0 = F.Plan(1024, 2048, "bf16", L=14)
+    p0.orthogonalize(b, w, ref)
+    plan = F.Plan(1024, 2048, "bf16", L=14)
+    ys = [torch.empty_like(x) for x in xs]
+    plan.autotune(b, w, ys, reps=1)
+    lim = plan.get(F.IFNSO_OPT_STAGE_LIMITS)
+    assert all(((lim >> (4 * k)) & 15) in (0, 3, 4) for k in range(5)) and lim >> 20 == 0
+    ys = [torch.full(x.shape, float("nan"), dtype=x.dtype, device="cuda") for x in xs]
+    plan.set(F.IFNSO_OPT_CTA_GROUP_KINDS, 0)  # the untuned MMA modes, as p0, with the tuned depths
+    plan.orthogonalize(b, w, ys)
+    torch.cuda.synchronize()
+    for y0, y in zip(ref, ys):
+        assert np.array_equal(to_np(y0), to_np(y))
+
+
 @pytest.mark.parametrize("L,precision", [(14, "mixed"), (14, "plain"), (16, "mixed")])
 def test_bf16_folded_squarings_stay_accurate(L, precision):
     """Every other squaring folds -2 D_l into its MMAs, which rounds the two
