@@ -289,7 +289,11 @@ ifnso_status ifnso_orthogonalize(ifnso_plan* plan, const ifnso_batch_desc* batch
  * copy stream of the plan, the downloads on another, and each group's passes
  * start as soon as its inputs have arrived, so the call costs about the
  * larger of the copies and the passes rather than their sum.  Host buffers
- * must be page-locked for the copies to overlap anything.  Asynchronous:
+ * must be page-locked for the copies to overlap anything.  On hosts with
+ * 64 KB base pages (Grace), buffers carved from one mapping backed by
+ * transparent huge pages and registered once kept the copies at full speed,
+ * where buffers page-locked one by one after another large process had
+ * freed its memory intermittently copied at about a tenth of it.  Asynchronous:
  * everything the call does is ordered after earlier work on `stream` and
  * before later work on it; the host buffers must stay untouched until then.
  * Per-pass timing events (IFNSO_OPT_TIMING) and IFNSO_OPT_STOP_AFTER do not

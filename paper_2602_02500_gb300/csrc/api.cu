@@ -1409,15 +1409,14 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   IFNSO_CUDA(launch_prep(d_mats, count, r.hpad_max, scal, coef, L, prep_lo, 0, stream, 0, net ? 0 : 1), "prep");
   // The FP16 copy M s that the final product reads (s from tr T_0) is written
   // by the side warps of the squarings that the tensor pipe bounds -- the
-  // split ones, or every squaring when fewer than three are split -- with the
-  // matrices shared out among them in order, in shares of about equal bytes;
-  // or by its own HBM-bound kernel
+  // split ones, or every squaring when fewer than three are split -- each
+  // writing an equal part of the copies' pieces, matrix after matrix; or by
+  // its own HBM-bound kernel
   // here when those passes would not hide it: a grid short of the GPU, a
   // matrix of 2^31 pieces or more, or passes too short for the copy
   // (estimated from its reads at 0.5 TB/s against the host passes' products
   // at 1.6 PFLOP/s, with a margin of 0.6).
   int side_hosts = 0;
-  std::vector<int> side_cut;  // host j copies matrices [side_cut[j - 1], side_cut[j])
   if (pc.p_f16) {
     const int hosts = pc.k_split >= 3 ? pc.k_split : L - 1;
     double rd = 0.0, fl = 0.0;
@@ -1432,16 +1431,6 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     }
     const int prods = pc.k_split >= 3 ? 3 : 1;
     if (fits && hosts >= 1 && rd / hosts / 0.5e12 < 0.6 * prods * fl / 1.6e15) side_hosts = hosts;
-    // host j's share: the matrices whose copies' cumulative bytes cross (j - 1) / hosts of the total
-    side_cut.assign(1, 0);
-    double acc = 0.0;
-    for (int i = 0; i < count && side_hosts; ++i) {
-      const Shape& s = ly.shp[first + i];
-      if (!(r.on_chip && s.h <= kSmallH)) acc += 2.0 * static_cast<double>(s.rows) * static_cast<double>(s.cols);
-      while (static_cast<int>(side_cut.size()) < side_hosts && acc >= rd * side_cut.size() / side_hosts)
-        side_cut.push_back(i + 1);
-    }
-    while (static_cast<int>(side_cut.size()) <= side_hosts) side_cut.push_back(count);
     if (!side_hosts)
       IFNSO_CUDA(launch_cast_f16(d_mats, count, scal, std::max(1, 16 * plan->num_sms / count), stream), "FP16 copy");
   }
@@ -1477,11 +1466,12 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
     // (the feature pass needs D_l^2 itself)
     p.fold_d = ((p.p_mode == 0 || p.p_mode == 3) && !p.feat) ? 1 : 0;
     if (j <= side_hosts) {
-      // this squaring's share of the FP16 copies: matrices [c0, c1) of the range
-      const int c0 = side_cut[j - 1], c1 = side_cut[j];
-      p.side_mats = d_mats + c0;
-      p.side_scal = scal + c0;
-      p.side_count = c1 - c0;
+      // this squaring's part of the FP16 copies
+      p.side_mats = d_mats;
+      p.side_scal = scal;
+      p.side_count = count;
+      p.side_part = j - 1;
+      p.side_parts = side_hosts;
     } else {
       p.side_mats = nullptr;
       p.side_scal = nullptr;

@@ -158,12 +158,15 @@ struct TcParams {
   int32_t update;      // EPI_APPLY: out0 holds the weights W (M's shape, also read through
                        // aux0): W <- W - lr sqrt(max(1, rows / cols)) Y instead of Y
   float lr;            // the step size of that update
-  // Side work of a squaring pass: the FP16 copies M s of side_mats[0 .. side_count)
-  // for the FP16 product, written by extra warps of every CTA while the pass
-  // runs (side_scal: their scalar records; side_mats nullptr: no side work)
+  // Side work of a squaring pass: part side_part of side_parts equal parts of
+  // the FP16 copies M s of side_mats[0 .. side_count) (the copies' 8-value
+  // pieces, matrix after matrix) for the FP16 product, written by extra warps
+  // of every CTA while the pass runs (side_scal: their scalar records;
+  // side_mats nullptr: no side work)
   const MatInfo* side_mats;
   const MatScalars* side_scal;
   int32_t side_count;
+  int32_t side_part, side_parts;
   MatScalars* scal;
   CoefTable coef;
   float ns_a, ns_b, ns_c, ns_bcoef;

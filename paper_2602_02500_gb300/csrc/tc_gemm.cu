@@ -616,10 +616,13 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
 
 // ---------------------------------------------------------------- side work
 //
-// The FP16 copy M s of matrices side_mats[0 .. side_count) (s =
+// The FP16 copy M s of the matrices side_mats[0 .. side_count) (s =
 // f16_copy_scale(tr T_0), known once the Gram has run), in M's own layout:
-// the same values as the standalone cast kernel writes.  The side warps of
-// all CTAs stride over the 8-value pieces of each matrix (rows 16-byte
+// the same values as the standalone cast kernel writes.  The copies' 8-value
+// pieces, taken matrix after matrix, are cut into side_parts equal parts and
+// this pass writes part side_part, so that a batch of a few large matrices
+// spreads over the host passes as evenly as one of many small ones.  The
+// side warps of all CTAs stride over the part's pieces (rows 16-byte
 // aligned, as the input's TMA views require), U pieces per lane in flight:
 // 16-byte streaming loads, then 16-byte streaming stores (neither the input
 // nor the copy is read again before the product, so they should not evict
@@ -627,51 +630,66 @@ __device__ __forceinline__ void epilogue_chunk(const TcParams& p, const TcProble
 // BF16 value times a power of two converts to FP16 exactly while it stays in
 // FP16's normal range.  The host sends a matrix here only when its piece
 // count is below 2^31.
+__device__ __forceinline__ uint32_t side_pieces(const MatInfo& mi) {
+  if (mi.on_chip || !mi.a16) return 0u;
+  return static_cast<uint32_t>(mi.rows) * static_cast<uint32_t>((mi.cols + 7) / 8);
+}
+
 __device__ __forceinline__ void side_cast_f16(const TcParams& p, int t) {
   constexpr int U = 8;
   const uint32_t stride = gridDim.x * (32u * kSideWarps);
-  for (int m = 0; m < p.side_count; ++m) {
+  uint64_t total = 0;
+  for (int m = 0; m < p.side_count; ++m) total += side_pieces(p.side_mats[m]);
+  const uint64_t lo = total * static_cast<uint64_t>(p.side_part) / static_cast<uint64_t>(p.side_parts);
+  const uint64_t hi = total * static_cast<uint64_t>(p.side_part + 1) / static_cast<uint64_t>(p.side_parts);
+  uint64_t off = 0;
+  for (int m = 0; m < p.side_count && off < hi; ++m) {
     const MatInfo& mi = p.side_mats[m];
-    if (mi.on_chip || !mi.a16) continue;
-    const float s = f16_copy_scale(p.side_scal[m].trace);
-    const uint32_t cols = static_cast<uint32_t>(mi.cols);
-    const uint32_t vpr = (cols + 7u) / 8u;  // pieces per row
-    const uint32_t n = static_cast<uint32_t>(mi.rows) * vpr;
-    const __nv_bfloat16* M = static_cast<const __nv_bfloat16*>(mi.in);
-    __half* D = static_cast<__half*>(mi.a16);
-    for (uint32_t i0 = blockIdx.x * (32u * kSideWarps) + t; i0 < n; i0 += U * stride) {
-      uint4 v[U];
+    const uint32_t n = side_pieces(mi);
+    const uint64_t a = lo > off ? lo : off, b = hi < off + n ? hi : off + n;
+    if (a < b) {
+      // pieces [i_lo, i_hi) of matrix m
+      const uint32_t i_lo = static_cast<uint32_t>(a - off), i_hi = static_cast<uint32_t>(b - off);
+      const float s = f16_copy_scale(p.side_scal[m].trace);
+      const uint32_t cols = static_cast<uint32_t>(mi.cols);
+      const uint32_t vpr = (cols + 7u) / 8u;  // pieces per row
+      const __nv_bfloat16* M = static_cast<const __nv_bfloat16*>(mi.in);
+      __half* D = static_cast<__half*>(mi.a16);
+      for (uint32_t i0 = i_lo + blockIdx.x * (32u * kSideWarps) + t; i0 < i_hi; i0 += U * stride) {
+        uint4 v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t i = i0 + u * stride;
-        v[u] = make_uint4(0u, 0u, 0u, 0u);
-        if (i < n) {
-          const uint32_t r = i / vpr, c = (i - r * vpr) * 8u;
-          if (c + 8u <= cols) v[u] = __ldcs(reinterpret_cast<const uint4*>(M + r * mi.ld + c));
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t i = i0 + u * stride;
-        if (i >= n) break;
-        const uint32_t r = i / vpr, c = (i - r * vpr) * 8u;
-        const __nv_bfloat16* src = M + r * mi.ld + c;
-        __half* dst = D + r * mi.a16ld + c;
-        if (c + 8u <= cols) {
-          const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
-          uint4 o;
-          __half2* h = reinterpret_cast<__half2*>(&o);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float2 f = __bfloat1622float2(e[k]);
-            h[k] = __floats2half2_rn(f.x * s, f.y * s);
+        for (int u = 0; u < U; ++u) {
+          const uint32_t i = i0 + u * stride;
+          v[u] = make_uint4(0u, 0u, 0u, 0u);
+          if (i < i_hi) {
+            const uint32_t r = i / vpr, c = (i - r * vpr) * 8u;
+            if (c + 8u <= cols) v[u] = __ldcs(reinterpret_cast<const uint4*>(M + r * mi.ld + c));
           }
-          __stcs(reinterpret_cast<uint4*>(dst), o);
-        } else {
-          for (uint32_t k = 0; c + k < cols; ++k) dst[k] = __float2half_rn(__bfloat162float(src[k]) * s);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t i = i0 + u * stride;
+          if (i >= i_hi) break;
+          const uint32_t r = i / vpr, c = (i - r * vpr) * 8u;
+          const __nv_bfloat16* src = M + r * mi.ld + c;
+          __half* dst = D + r * mi.a16ld + c;
+          if (c + 8u <= cols) {
+            const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v[u]);
+            uint4 o;
+            __half2* h = reinterpret_cast<__half2*>(&o);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float2 f = __bfloat1622float2(e[k]);
+              h[k] = __floats2half2_rn(f.x * s, f.y * s);
+            }
+            __stcs(reinterpret_cast<uint4*>(dst), o);
+          } else {
+            for (uint32_t k = 0; c + k < cols; ++k) dst[k] = __float2half_rn(__bfloat162float(src[k]) * s);
+          }
         }
       }
     }
+    off += n;
   }
 }
 
