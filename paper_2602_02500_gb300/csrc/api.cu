@@ -1410,12 +1410,11 @@ ifnso_status run_tc(const Run& r, int first, int count, size_t sym0, size_t sym1
   // The FP16 copy M s that the final product reads (s from tr T_0) is written
   // by the side warps of the squarings that the tensor pipe bounds -- the
   // split ones, or every squaring when fewer than three are split -- each
-  // writing an equal part of the copies' pieces, matrix after matrix; or by
-  // its own HBM-bound kernel
-  // here when those passes would not hide it: a grid short of the GPU, a
-  // matrix of 2^31 pieces or more, or passes too short for the copy
-  // (estimated from its reads at 0.5 TB/s against the host passes' products
-  // at 1.6 PFLOP/s, with a margin of 0.6).
+  // writing an equal part of the copies' pieces, matrix after matrix.  Its
+  // own HBM-bound kernel writes it here instead when those passes would not
+  // hide it: a grid short of the GPU, a matrix of 2^31 pieces or more, or
+  // passes too short for the copy (estimated from its reads at 0.5 TB/s
+  // against the host passes' products at 1.6 PFLOP/s, with a margin of 0.6).
   int side_hosts = 0;
   if (pc.p_f16) {
     const int hosts = pc.k_split >= 3 ? pc.k_split : L - 1;
