@@ -153,7 +153,8 @@ typedef enum {
    * rounding below 2^-16 relative).  1 (default): one FP16 product of P (one
    * FP16 value) and an FP16 copy A s of the input (s a power of two from
    * ||A||_F that keeps every entry below 32768; written after the Gram, in
-   * the workspace, which then grows by 2 bytes per input element).  FP16
+   * the workspace, which then grows by 2 bytes per input element; see
+   * IFNSO_OPT_FP16_COPY_HOSTS for which kernels write it).  FP16
    * keeps 3 more mantissa bits than BF16, so P's rounding costs about 2^-11
    * times its largest entries.  0: BF16 hi + lo.  PLAIN plans keep their one
    * BF16 product of P and SPLIT plans (larger coefficients) hi + lo whatever
@@ -175,8 +176,9 @@ typedef enum {
    * above the ring's depth changes nothing).  A shallower ring leaves the
    * shared memory it does not allocate to the L1 cache and has fewer operand
    * bytes in flight, which can speed up a pass whose epilogue loads or stores
-   * compete with them.  ifnso_plan_autotune chooses among the whole ring, 4 and 3 per kind
-   * (get returns its choice); set overrides it; the default is 0. */
+   * compete with them.  ifnso_plan_autotune chooses among the whole ring, 4
+   * and 3 per kind (get returns its choice); set overrides it; the default is
+   * 0.  Results do not depend on it. */
   IFNSO_OPT_STAGE_LIMITS = 17
 } ifnso_option;
 
