@@ -879,6 +879,10 @@ def main():
     time.sleep(0.3)
     n0 = F.launch_count()
     ms_total = timed_steps(ifnso_step, args.steps, "ifnso")
+    # where the timed step's FP16 copy of the inputs was written (set when the step was enqueued)
+    hosts = plan.get(F.IFNSO_OPT_FP16_COPY_HOSTS) if dtype == "bf16" else 0
+    fp16_copy = (f"written by the side warps of {hosts} squarings" if hosts else
+                 "written by its own kernel" if plan.get(F.IFNSO_OPT_APPLY_F16) else "not used")
     launches = ifnso_launches * args.steps if ifnso_launches is not None else F.launch_count() - n0
     clk = clocks.stop()
     ms_step = ms_total / args.steps
@@ -1110,6 +1114,7 @@ def main():
                                 2: "tcgen05 MMAs of the CTA pair (M = 256)"}[args.cta_group]),
                        "autotuned": tuned is not None,
                        "stage_limits": stage_limits,
+                       "fp16_copy": fp16_copy,
                        "small_matrices": ({1: "on-chip path (one CTA per matrix, all of Algorithm 1 in one launch)",
                                            2: "tiled passes"}.get(plan.get(F.IFNSO_OPT_SMALL_TUNED),
                                                                   "not applicable (a matrix has h > 128)")

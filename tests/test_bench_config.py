@@ -84,3 +84,16 @@ def test_committed_traffic_counters_belong_to_the_kernel_source():
     for k, b in per.items():
         alg = 168 * upper * b
         assert 0.85 * alg <= t["muon_1b:" + k] <= 1.15 * alg, (k, t["muon_1b:" + k], alg)
+
+
+def test_bench_names_exist_in_the_binding():
+    """Every F.<name> that bench.py uses (most of it runs only on a GPU) is
+    defined by the binding, so a misspelt option or call fails here first."""
+    import re
+
+    from paper_2602_02500_gb300 import ifnso as F
+
+    with open(os.path.join(ROOT, "bench.py")) as f:
+        names = set(re.findall(r"\bF\.([A-Za-z_][A-Za-z0-9_]*)", f.read()))
+    assert names
+    assert [n for n in sorted(names) if not hasattr(F, n)] == []
